@@ -1,0 +1,635 @@
+/*
+ * tmd_oracle.c -- plain, serial CPU oracle for TPC track-model encoding and
+ * decoding (arXiv:2411.02206, Sec. 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
+ * only the test suite, the smoke check and the CPU-baseline leg of the bench
+ * load it.  It shares no source, header, table or helper with the CUDA
+ * library; both are written independently from the same format definition.
+ *
+ * What it computes (Sec. 3):
+ *   - track-model encoding: each attached cluster after the first of its track
+ *     is stored as the residual of its quantised pad/time to the prediction of
+ *     the track model, which is updated with the cluster after each step;
+ *   - unattached-cluster encoding: per (sector,row) the clusters are sorted by
+ *     position (time, then pad) and stored as differences to the preceding one;
+ *   - track-model decoding: the exact inverse of both, producing the native
+ *     cluster list grouped by (sector,row), attached clusters first in
+ *     (track, cluster) order, then the unattached clusters in stored order.
+ *
+ * The paper does not give the track model (it is in the cited CTD2019
+ * proceedings, not available here).  The model below is this project's
+ * reading: a linear Kalman filter in the sector-local frame, with a parabola
+ * (y, dy/dx, d2y/dx2) for the bending plane and a line (t, dt/dx) for drift
+ * time.  Every floating-point operation is binary32, round-to-nearest-even,
+ * performed in the order written; this file must be compiled with
+ * -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define O_NSEC 36
+#define O_NROW 152
+#define O_NBIN (O_NSEC * O_NROW)
+
+/* status bits of a decoded frame */
+#define O_ST_COUNT 1u   /* counts inconsistent: sum of nCl, nCl == 0, sum of nUnatt */
+#define O_ST_ROW 2u     /* a row >= 152 or a sector >= 36 */
+#define O_ST_TIME 4u    /* a decoded time >= 2^24 (does not fit the native record) */
+
+/* ------------------------------------------------------------------------ */
+/* Geometry of the synthetic TPC.                                           */
+/* Row r lies on the plane x = 85 + r cm of its sector's local frame; it    */
+/* holds nPads(r) = 66 + floor(72 r / 151) pads spanning +-x tan(10 deg).   */
+/* Sector s (0..17 on the A side, 18..35 on the C side) is centred at the   */
+/* azimuth (s mod 18) * 20 deg + 10 deg.                                   */
+/* ------------------------------------------------------------------------ */
+static float g_x[O_NROW];      /* row plane x [cm] */
+static float g_w[O_NROW];      /* pad width [cm] */
+static float g_invw[O_NROW];   /* 1 / pad width */
+static float g_halfnp[O_NROW]; /* nPads / 2 */
+static int g_np[O_NROW];
+static float g_cos[18], g_sin[18]; /* cos, sin of k * 20 deg */
+static int g_geo_ready = 0;
+
+/* exact sin/cos of an integer number of degrees (multiple of 20) by reduction
+ * to a reference angle in [0, 90), so that 0 and 180 deg give exact zeros */
+static void o_sincos_deg(int a, double* s, double* c) {
+  int q = ((a % 360) + 360) % 360;
+  double ss = 1.0, sc = 1.0;
+  if (q > 180) { q = 360 - q; ss = -1.0; }
+  if (q > 90) { q = 180 - q; sc = -1.0; }
+  double r = (double)q * (3.14159265358979323846 / 180.0);
+  *s = ss * (q == 0 ? 0.0 : sin(r));
+  *c = sc * (q == 0 ? 1.0 : cos(r));
+}
+
+static void o_geo_init(void) {
+  if (g_geo_ready) return;
+  const float tan10 = 0.17632698f; /* binary32 nearest tan(10 deg) */
+  for (int r = 0; r < O_NROW; r++) {
+    int np = 66 + (72 * r) / 151;
+    float x = 85.0f + (float)r;
+    float w = (2.0f * x * tan10) / (float)np;
+    g_np[r] = np;
+    g_x[r] = x;
+    g_w[r] = w;
+    g_invw[r] = 1.0f / w;
+    g_halfnp[r] = 0.5f * (float)np;
+  }
+  for (int k = 0; k < 18; k++) {
+    double s, c;
+    o_sincos_deg(20 * k, &s, &c);
+    g_cos[k] = (float)c;
+    g_sin[k] = (float)s;
+  }
+  g_geo_ready = 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Track model parameters.                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  float sy2;  /* measurement variance of y [cm^2] */
+  float st2;  /* measurement variance of t [bin^2] */
+  float qty;  /* process noise of dy/dx per cm of |dx| */
+  float qtt;  /* process noise of dt/dx per cm of |dx| */
+  float cty0; /* seed variance of dy/dx */
+  float cc0;  /* seed variance of d2y/dx2 [cm^-2] */
+  float ctt0; /* seed variance of dt/dx [bin^2/cm^2] */
+  float syr;  /* variance of y after a sector or leg change [cm^2] */
+  float kc;   /* |d2y/dx2| per unit q/pT [cm^-1 per (GeV/c)^-1] */
+} OModel;
+
+static const OModel O_DEFAULT_MODEL = {0.01f, 0.04f, 1.0e-6f, 4.0e-6f, 0.01f,
+                                       1.0e-8f, 4.0f, 0.25f, 0.0015f};
+
+/* Track state: sector-local frame, reference plane x. */
+typedef struct {
+  float x;
+  float y, ty, c;               /* y-block: parabola */
+  float c00, c01, c02, c11, c12, c22; /* y-block covariance (upper triangle) */
+  float t, tt;                  /* t-block: line in drift time */
+  float d00, d01, d11;          /* t-block covariance */
+  int row, sec;
+} OState;
+
+/* Quantisation: clamp to [lo, hi] (a NaN goes to lo), then floor(v + 0.5). */
+static uint32_t o_quant(float v, float lo, float hi) {
+  if (!(v >= lo)) v = lo;
+  if (v > hi) v = hi;
+  return (uint32_t)floorf(v + 0.5f);
+}
+#define O_PAD_HI 65535.0f
+#define O_TIME_HI 8388607.0f
+
+/* pad code (1/64 pad) -> y [cm] on row r */
+static float o_pad_to_y(uint32_t padq, int r) {
+  return ((float)padq * 0.015625f - g_halfnp[r]) * g_w[r];
+}
+/* time code (1/32 bin) -> t [bin] */
+static float o_time_to_t(uint32_t timeq) { return (float)timeq * 0.03125f; }
+
+/* q/pT code -> q/pT [(GeV/c)^-1] */
+static float o_qpt(uint8_t qpta) { return ((float)qpta - 127.5f) * 0.078125f; }
+
+/* Seed from the first cluster of the track (stored absolute in the header). */
+static void o_seed(const OModel* m, OState* s, uint8_t qpta, int row, int sec,
+                   uint32_t padq, uint32_t timeq) {
+  float qpt = o_qpt(qpta);
+  s->row = row;
+  s->sec = sec;
+  s->x = g_x[row];
+  s->y = o_pad_to_y(padq, row);
+  s->c = (-m->kc) * qpt;
+  /* slope of the parabola through the origin and the first cluster */
+  s->ty = s->y / s->x + (s->c * s->x) * 0.5f;
+  s->c00 = m->sy2; s->c01 = 0.0f; s->c02 = 0.0f;
+  s->c11 = m->cty0; s->c12 = 0.0f; s->c22 = m->cc0;
+  s->t = o_time_to_t(timeq);
+  s->tt = 0.0f;
+  s->d00 = m->st2; s->d01 = 0.0f; s->d11 = m->ctt0;
+}
+
+static void o_reset_ycov(const OModel* m, OState* s) {
+  s->c00 = m->syr; s->c01 = 0.0f; s->c02 = 0.0f;
+  s->c11 = m->cty0; s->c12 = 0.0f; s->c22 = m->cc0;
+}
+
+/* A new leg: the track turns back in x.  The x-parametrised slope and
+ * curvature change sign, as does dt/dx; the y-block restarts its uncertainty. */
+static void o_leg_change(const OModel* m, OState* s) {
+  s->ty = -s->ty;
+  s->c = -s->c;
+  s->tt = -s->tt;
+  s->d01 = -s->d01;
+  o_reset_ycov(m, s);
+}
+
+/* Move the state into the frame of sector nsec: rotate the point, slope and
+ * curvature of the parabola by k * 20 deg; crossing to the other side of the
+ * central membrane reverses dt/dx. */
+static void o_sector_change(const OModel* m, OState* s, int nsec) {
+  int k = ((nsec % 18) - (s->sec % 18) + 18) % 18;
+  float ca = g_cos[k], sa = g_sin[k];
+  float a = ca + s->ty * sa;
+  float b = s->ty * ca - sa;
+  if (!(a >= 1.0e-3f || a <= -1.0e-3f)) a = (a < 0.0f) ? -1.0e-3f : 1.0e-3f;
+  float nx = s->x * ca + s->y * sa;
+  float ny = s->y * ca - s->x * sa;
+  s->ty = b / a;
+  s->c = s->c / ((a * a) * a);
+  s->x = nx;
+  s->y = ny;
+  if ((s->sec < 18) != (nsec < 18)) {
+    s->tt = -s->tt;
+    s->d01 = -s->d01;
+  }
+  s->sec = nsec;
+  o_reset_ycov(m, s);
+}
+
+/* Propagate the state to the plane of row r (linear model, F = [[1,dx,dx^2/2],
+ * [0,1,dx],[0,0,1]] for the y-block and [[1,dx],[0,1]] for the t-block). */
+static void o_propagate(const OModel* m, OState* s, int r) {
+  float dx = g_x[r] - s->x;
+  float adx = fabsf(dx);
+  float h = (0.5f * s->c) * dx;
+  s->y = s->y + dx * (s->ty + h);
+  s->ty = s->ty + s->c * dx;
+  s->t = s->t + s->tt * dx;
+  s->x = g_x[r];
+  s->row = r;
+  /* y-block: C' = F C F^T + diag(0, qty |dx|, 0) */
+  float h2 = (0.5f * dx) * dx;
+  float a0 = (s->c00 + dx * s->c01) + h2 * s->c02;
+  float a1 = (s->c01 + dx * s->c11) + h2 * s->c12;
+  float a2 = (s->c02 + dx * s->c12) + h2 * s->c22;
+  float b1 = s->c11 + dx * s->c12;
+  float b2 = s->c12 + dx * s->c22;
+  s->c00 = (a0 + dx * a1) + h2 * a2;
+  s->c01 = a1 + dx * a2;
+  s->c02 = a2;
+  s->c11 = (b1 + dx * b2) + m->qty * adx;
+  s->c12 = b2;
+  /* c22 unchanged */
+  /* t-block: D' = G D G^T + diag(0, qtt |dx|) */
+  float e0 = s->d00 + dx * s->d01;
+  float e1 = s->d01 + dx * s->d11;
+  s->d00 = e0 + dx * e1;
+  s->d01 = e1;
+  s->d11 = s->d11 + m->qtt * adx;
+}
+
+/* Kalman update of both blocks with a measured (y, t). */
+static void o_update(const OModel* m, OState* s, float ym, float tm) {
+  float inv = 1.0f / (s->c00 + m->sy2);
+  float k0 = s->c00 * inv, k1 = s->c01 * inv, k2 = s->c02 * inv;
+  float r = ym - s->y;
+  s->y = s->y + k0 * r;
+  s->ty = s->ty + k1 * r;
+  s->c = s->c + k2 * r;
+  float c00 = s->c00, c01 = s->c01, c02 = s->c02;
+  s->c00 = c00 - k0 * c00;
+  s->c01 = c01 - k0 * c01;
+  s->c02 = c02 - k0 * c02;
+  s->c11 = s->c11 - k1 * c01;
+  s->c12 = s->c12 - k1 * c02;
+  s->c22 = s->c22 - k2 * c02;
+  float invt = 1.0f / (s->d00 + m->st2);
+  float g0 = s->d00 * invt, g1 = s->d01 * invt;
+  float rt = tm - s->t;
+  s->t = s->t + g0 * rt;
+  s->tt = s->tt + g1 * rt;
+  float d00 = s->d00, d01 = s->d01;
+  s->d00 = d00 - g0 * d00;
+  s->d01 = d01 - g0 * d01;
+  s->d11 = s->d11 - g1 * d01;
+}
+
+/* Apply the key step (row difference, sector/leg difference) of one cluster,
+ * propagate to its row and return the quantised prediction.  Returns 0, or
+ * O_ST_ROW if the row left the detector (it is then clamped to 151). */
+static uint32_t o_step_predict(const OModel* m, OState* s, uint8_t row_diff,
+                               uint8_t slice_leg_diff, uint32_t* pred_padq,
+                               uint32_t* pred_timeq, float* pred_y, float* pred_t) {
+  uint32_t st = 0;
+  int leg = slice_leg_diff / O_NSEC;
+  int sd = slice_leg_diff % O_NSEC;
+  int row = (s->row + row_diff) & 255;
+  if (row >= O_NROW) { st |= O_ST_ROW; row = O_NROW - 1; }
+  if (leg != 0) o_leg_change(m, s);
+  if (sd != 0) o_sector_change(m, s, (s->sec + sd) % O_NSEC);
+  o_propagate(m, s, row);
+  float pp = s->y * g_invw[row] + g_halfnp[row];
+  *pred_padq = o_quant(pp * 64.0f, 0.0f, O_PAD_HI);
+  *pred_timeq = o_quant(s->t * 32.0f, 0.0f, O_TIME_HI);
+  if (pred_y) *pred_y = s->y;
+  if (pred_t) *pred_t = s->t;
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compressed frame (entropy-decoded CTF) and native output.               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t n_tracks, n_attached, n_unattached;
+  /* per track: the first cluster stored absolute, plus q/pT and length */
+  const uint8_t* qpt;
+  const uint8_t* row;
+  const uint8_t* slice;
+  const uint16_t* pad;
+  const uint32_t* time;
+  const uint16_t* ncl;
+  /* per attached cluster, track order (n_attached entries) */
+  const uint16_t* qtot_a;
+  const uint16_t* qmax_a;
+  const uint8_t* flags_a;
+  const uint8_t* sigma_pad_a;
+  const uint8_t* sigma_time_a;
+  /* per attached cluster after the first of its track (n_attached - n_tracks) */
+  const uint8_t* row_diff;
+  const uint8_t* slice_leg_diff;
+  const uint16_t* pad_res;
+  const uint32_t* time_res;
+  /* per (sector,row) bin, bin = sector * 152 + row */
+  const uint32_t* n_unatt;
+  /* per unattached cluster, bin order then stored order */
+  const uint16_t* pad_diff_u;
+  const uint32_t* time_diff_u;
+  const uint16_t* qtot_u;
+  const uint16_t* qmax_u;
+  const uint8_t* flags_u;
+  const uint8_t* sigma_pad_u;
+  const uint8_t* sigma_time_u;
+} OFrame;
+
+/* Native record, 12 bytes little-endian:
+ *   u32 time (low 24 bits) | flags << 24;  u16 pad;  u8 sigmaTime;  u8 sigmaPad;
+ *   u16 qMax;  u16 qTot. */
+static void o_put_record(uint8_t* dst, uint32_t timeq, uint8_t flags, uint16_t padq,
+                         uint8_t sig_time, uint8_t sig_pad, uint16_t qmax, uint16_t qtot) {
+  uint32_t w0 = (timeq & 0xFFFFFFu) | ((uint32_t)flags << 24);
+  dst[0] = (uint8_t)w0; dst[1] = (uint8_t)(w0 >> 8);
+  dst[2] = (uint8_t)(w0 >> 16); dst[3] = (uint8_t)(w0 >> 24);
+  dst[4] = (uint8_t)padq; dst[5] = (uint8_t)(padq >> 8);
+  dst[6] = sig_time; dst[7] = sig_pad;
+  dst[8] = (uint8_t)qmax; dst[9] = (uint8_t)(qmax >> 8);
+  dst[10] = (uint8_t)qtot; dst[11] = (uint8_t)(qtot >> 8);
+}
+
+/* Walk the keys (row, sector) of every attached cluster, track by track.
+ * bins[j] receives sector * 152 + row of cluster j.  Returns status bits. */
+static uint32_t o_attached_bins(const OFrame* f, const uint32_t* tstart, uint16_t* bins) {
+  uint32_t st = 0;
+  for (uint32_t t = 0; t < f->n_tracks; t++) {
+    uint32_t j0 = tstart[t], n = f->ncl[t];
+    int row = f->row[t], sec = f->slice[t];
+    if (row >= O_NROW) { st |= O_ST_ROW; row = O_NROW - 1; }
+    if (sec >= O_NSEC) { st |= O_ST_ROW; sec = O_NSEC - 1; }
+    bins[j0] = (uint16_t)(sec * O_NROW + row);
+    for (uint32_t k = 1; k < n; k++) {
+      uint32_t d = j0 - t + k - 1;
+      row = (row + f->row_diff[d]) & 255;
+      if (row >= O_NROW) { st |= O_ST_ROW; row = O_NROW - 1; }
+      sec = (sec + f->slice_leg_diff[d] % O_NSEC) % O_NSEC;
+      bins[j0 + k] = (uint16_t)(sec * O_NROW + row);
+    }
+  }
+  return st;
+}
+
+/* Decode one frame.
+ * native:    (n_attached + n_unattached) * 12 bytes
+ * row_start: 5473 entries; row_start[b] is the first record of bin b
+ * att_count: 5472 entries (may be NULL); attached records of bin b
+ * status:    out, O_ST_* bits.  On O_ST_COUNT nothing else is written.
+ * Returns 0, or -1 on allocation failure. */
+int tmd_oracle_decode(const OFrame* f, uint8_t* native, uint32_t* row_start,
+                      uint32_t* att_count, uint32_t* status) {
+  o_geo_init();
+  const OModel* m = &O_DEFAULT_MODEL;
+  uint32_t st = 0;
+  /* counts */
+  uint64_t sum = 0;
+  for (uint32_t t = 0; t < f->n_tracks; t++) {
+    if (f->ncl[t] == 0) st |= O_ST_COUNT;
+    sum += f->ncl[t];
+  }
+  if (sum != f->n_attached) st |= O_ST_COUNT;
+  uint64_t sumu = 0;
+  for (int b = 0; b < O_NBIN; b++) sumu += f->n_unatt[b];
+  if (sumu != f->n_unattached) st |= O_ST_COUNT;
+  if (st & O_ST_COUNT) { *status = st; return 0; }
+
+  uint32_t* tstart = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)f->n_tracks + 1));
+  uint16_t* bins = (uint16_t*)malloc(sizeof(uint16_t) * ((size_t)f->n_attached + 1));
+  uint32_t* cursor = (uint32_t*)malloc(sizeof(uint32_t) * O_NBIN);
+  uint32_t* attc = (uint32_t*)calloc(O_NBIN, sizeof(uint32_t));
+  if (!tstart || !bins || !cursor || !attc) {
+    free(tstart); free(bins); free(cursor); free(attc);
+    return -1;
+  }
+  tstart[0] = 0;
+  for (uint32_t t = 0; t < f->n_tracks; t++) tstart[t + 1] = tstart[t] + f->ncl[t];
+
+  /* row offsets: attached count + unattached count per bin, exclusive scan */
+  st |= o_attached_bins(f, tstart, bins);
+  for (uint32_t j = 0; j < f->n_attached; j++) attc[bins[j]]++;
+  uint32_t acc = 0;
+  for (int b = 0; b < O_NBIN; b++) {
+    row_start[b] = acc;
+    cursor[b] = acc;
+    acc += attc[b] + f->n_unatt[b];
+  }
+  row_start[O_NBIN] = acc;
+  if (att_count) memcpy(att_count, attc, sizeof(uint32_t) * O_NBIN);
+
+  /* attached clusters: tracks in order, clusters in order */
+  for (uint32_t t = 0; t < f->n_tracks; t++) {
+    uint32_t j0 = tstart[t], n = f->ncl[t];
+    int row0 = f->row[t] < O_NROW ? f->row[t] : O_NROW - 1;
+    int sec0 = f->slice[t] < O_NSEC ? f->slice[t] : O_NSEC - 1;
+    OState s;
+    o_seed(m, &s, f->qpt[t], row0, sec0, f->pad[t], f->time[t]);
+    uint32_t padq = f->pad[t], timeq = f->time[t];
+    for (uint32_t k = 0; k < n; k++) {
+      uint32_t j = j0 + k;
+      if (k > 0) {
+        uint32_t d = j0 - t + k - 1, ppad, ptime;
+        st |= o_step_predict(m, &s, f->row_diff[d], f->slice_leg_diff[d], &ppad, &ptime,
+                             NULL, NULL);
+        padq = (ppad + f->pad_res[d]) & 0xFFFFu;
+        timeq = ptime + f->time_res[d];
+        o_update(m, &s, o_pad_to_y(padq, s.row), o_time_to_t(timeq));
+      }
+      if (timeq > 0xFFFFFFu) st |= O_ST_TIME;
+      uint32_t b = bins[j];
+      o_put_record(native + (size_t)12 * cursor[b]++, timeq, f->flags_a[j], (uint16_t)padq,
+                   f->sigma_time_a[j], f->sigma_pad_a[j], f->qmax_a[j], f->qtot_a[j]);
+    }
+  }
+
+  /* unattached clusters: per bin, running sums of the stored differences */
+  uint64_t u = 0;
+  for (int b = 0; b < O_NBIN; b++) {
+    uint32_t padq = 0, timeq = 0;
+    for (uint32_t i = 0; i < f->n_unatt[b]; i++, u++) {
+      padq = (padq + f->pad_diff_u[u]) & 0xFFFFu;
+      timeq = timeq + f->time_diff_u[u];
+      if (timeq > 0xFFFFFFu) st |= O_ST_TIME;
+      o_put_record(native + (size_t)12 * cursor[b]++, timeq, f->flags_u[u], (uint16_t)padq,
+                   f->sigma_time_u[u], f->sigma_pad_u[u], f->qmax_u[u], f->qtot_u[u]);
+    }
+  }
+  free(tstart); free(bins); free(cursor); free(attc);
+  *status = st;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Encoder (the synchronous side of Sec. 3), used to build test frames     */
+/* whose decoded result is known: the quantised truth itself.              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t n_tracks, n_attached, n_unattached;
+  const uint8_t* qpt;  /* per track */
+  const uint16_t* ncl; /* per track */
+  /* per attached cluster, track order */
+  const uint8_t* row;
+  const uint8_t* sector;
+  const uint8_t* leg; /* leg index along the track, non-decreasing */
+  const uint16_t* pad;
+  const uint32_t* time;
+  const uint16_t* qtot_a;
+  const uint16_t* qmax_a;
+  const uint8_t* flags_a;
+  const uint8_t* sigma_pad_a;
+  const uint8_t* sigma_time_a;
+  /* unattached clusters, any order */
+  const uint8_t* row_u;
+  const uint8_t* sector_u;
+  const uint16_t* pad_u;
+  const uint32_t* time_u;
+  const uint16_t* qtot_u;
+  const uint16_t* qmax_u;
+  const uint8_t* flags_u;
+  const uint8_t* sigma_pad_u;
+  const uint8_t* sigma_time_u;
+} OTruth;
+
+/* Writable compressed frame: same fields as OFrame. */
+typedef struct {
+  uint8_t* qpt; uint8_t* row; uint8_t* slice; uint16_t* pad; uint32_t* time; uint16_t* ncl;
+  uint16_t* qtot_a; uint16_t* qmax_a; uint8_t* flags_a; uint8_t* sigma_pad_a; uint8_t* sigma_time_a;
+  uint8_t* row_diff; uint8_t* slice_leg_diff; uint16_t* pad_res; uint32_t* time_res;
+  uint32_t* n_unatt;
+  uint16_t* pad_diff_u; uint32_t* time_diff_u; uint16_t* qtot_u; uint16_t* qmax_u;
+  uint8_t* flags_u; uint8_t* sigma_pad_u; uint8_t* sigma_time_u;
+} OFrameOut;
+
+/* unattached sort key: (time, pad), ties by input index (stable) */
+static const OTruth* g_sort_truth;
+static int o_cmp_unatt(const void* pa, const void* pb) {
+  uint32_t a = *(const uint32_t*)pa, b = *(const uint32_t*)pb;
+  const OTruth* T = g_sort_truth;
+  if (T->time_u[a] != T->time_u[b]) return T->time_u[a] < T->time_u[b] ? -1 : 1;
+  if (T->pad_u[a] != T->pad_u[b]) return T->pad_u[a] < T->pad_u[b] ? -1 : 1;
+  return a < b ? -1 : (a > b);
+}
+
+/* Encode a truth frame.  Returns 0, -1 on allocation failure, -2 on invalid
+ * truth (row >= 152, sector >= 36, nCl == 0, inconsistent counts, decreasing
+ * leg index). */
+int tmd_oracle_encode(const OTruth* T, OFrameOut* o) {
+  o_geo_init();
+  const OModel* m = &O_DEFAULT_MODEL;
+  uint64_t sum = 0;
+  for (uint32_t t = 0; t < T->n_tracks; t++) {
+    if (T->ncl[t] == 0) return -2;
+    sum += T->ncl[t];
+  }
+  if (sum != T->n_attached) return -2;
+  for (uint32_t j = 0; j < T->n_attached; j++)
+    if (T->row[j] >= O_NROW || T->sector[j] >= O_NSEC) return -2;
+  for (uint32_t i = 0; i < T->n_unattached; i++)
+    if (T->row_u[i] >= O_NROW || T->sector_u[i] >= O_NSEC) return -2;
+
+  uint32_t j0 = 0;
+  for (uint32_t t = 0; t < T->n_tracks; t++) {
+    uint32_t n = T->ncl[t];
+    for (uint32_t k = 1; k < n; k++)
+      if (T->leg[j0 + k] < T->leg[j0 + k - 1]) return -2;
+    o->qpt[t] = T->qpt[t];
+    o->row[t] = T->row[j0];
+    o->slice[t] = T->sector[j0];
+    o->pad[t] = T->pad[j0];
+    o->time[t] = T->time[j0];
+    o->ncl[t] = (uint16_t)n;
+    OState s;
+    o_seed(m, &s, T->qpt[t], T->row[j0], T->sector[j0], T->pad[j0], T->time[j0]);
+    for (uint32_t k = 1; k < n; k++) {
+      uint32_t j = j0 + k, d = j0 - t + k - 1, ppad, ptime;
+      int legd = T->leg[j] != T->leg[j - 1] ? 1 : 0;
+      int secd = ((int)T->sector[j] - (int)T->sector[j - 1] + O_NSEC) % O_NSEC;
+      o->row_diff[d] = (uint8_t)((T->row[j] - T->row[j - 1]) & 255);
+      o->slice_leg_diff[d] = (uint8_t)(legd * O_NSEC + secd);
+      o_step_predict(m, &s, o->row_diff[d], o->slice_leg_diff[d], &ppad, &ptime, NULL, NULL);
+      o->pad_res[d] = (uint16_t)((T->pad[j] - ppad) & 0xFFFFu);
+      o->time_res[d] = T->time[j] - ptime;
+      o_update(m, &s, o_pad_to_y(T->pad[j], s.row), o_time_to_t(T->time[j]));
+    }
+    j0 += n;
+  }
+  memcpy(o->qtot_a, T->qtot_a, 2u * T->n_attached);
+  memcpy(o->qmax_a, T->qmax_a, 2u * T->n_attached);
+  memcpy(o->flags_a, T->flags_a, T->n_attached);
+  memcpy(o->sigma_pad_a, T->sigma_pad_a, T->n_attached);
+  memcpy(o->sigma_time_a, T->sigma_time_a, T->n_attached);
+
+  /* unattached: group by bin (stable), sort each bin by (time, pad), store
+   * differences to the preceding cluster (the first to zero) */
+  uint32_t nu = T->n_unattached;
+  uint32_t* idx = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)nu + 1));
+  uint32_t* start = (uint32_t*)calloc(O_NBIN + 1, sizeof(uint32_t));
+  uint32_t* cur = (uint32_t*)malloc(sizeof(uint32_t) * O_NBIN);
+  if (!idx || !start || !cur) { free(idx); free(start); free(cur); return -1; }
+  for (uint32_t i = 0; i < nu; i++) start[T->sector_u[i] * O_NROW + T->row_u[i] + 1]++;
+  for (int b = 0; b < O_NBIN; b++) {
+    o->n_unatt[b] = start[b + 1];
+    start[b + 1] += start[b];
+    cur[b] = start[b];
+  }
+  for (uint32_t i = 0; i < nu; i++) idx[cur[T->sector_u[i] * O_NROW + T->row_u[i]]++] = i;
+  g_sort_truth = T;
+  for (int b = 0; b < O_NBIN; b++)
+    qsort(idx + start[b], start[b + 1] - start[b], sizeof(uint32_t), o_cmp_unatt);
+  for (int b = 0; b < O_NBIN; b++) {
+    uint32_t ppad = 0, ptime = 0;
+    for (uint32_t p = start[b]; p < start[b + 1]; p++) {
+      uint32_t i = idx[p];
+      o->pad_diff_u[p] = (uint16_t)((T->pad_u[i] - ppad) & 0xFFFFu);
+      o->time_diff_u[p] = T->time_u[i] - ptime;
+      ppad = T->pad_u[i];
+      ptime = T->time_u[i];
+      o->qtot_u[p] = T->qtot_u[i];
+      o->qmax_u[p] = T->qmax_u[i];
+      o->flags_u[p] = T->flags_u[i];
+      o->sigma_pad_u[p] = T->sigma_pad_u[i];
+      o->sigma_time_u[p] = T->sigma_time_u[i];
+    }
+  }
+  free(idx); free(start); free(cur);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Introspection for the tests that pin the model.                         */
+/* ------------------------------------------------------------------------ */
+
+/* Run the track model along one track with known measurements (the encoder's
+ * view).  model: 9 floats in OModel order, or NULL for the default model.
+ * For every cluster k the arrays receive: pred_y/pred_t the propagated state
+ * before the update (k = 0: the seed), pred_padq/pred_timeq the quantised
+ * prediction (k = 0: the stored header values), state (17 floats per k) the
+ * state after the update: x y ty c c00 c01 c02 c11 c12 c22 t tt d00 d01 d11
+ * row sec.  Returns status bits. */
+uint32_t tmd_oracle_track_trace(const float* model, uint8_t qpta, uint32_t n,
+                                const uint8_t* row, const uint8_t* sector, const uint8_t* leg,
+                                const uint16_t* pad, const uint32_t* time, float* pred_y,
+                                float* pred_t, uint32_t* pred_padq, uint32_t* pred_timeq,
+                                float* state) {
+  o_geo_init();
+  OModel mm = O_DEFAULT_MODEL;
+  if (model) memcpy(&mm, model, sizeof(OModel));
+  uint32_t st = 0;
+  OState s;
+  if (n == 0) return 0;
+  o_seed(&mm, &s, qpta, row[0], sector[0], pad[0], time[0]);
+  for (uint32_t k = 0; k < n; k++) {
+    if (k == 0) {
+      pred_y[0] = s.y; pred_t[0] = s.t;
+      pred_padq[0] = pad[0]; pred_timeq[0] = time[0];
+    } else {
+      uint8_t rd = (uint8_t)((row[k] - row[k - 1]) & 255);
+      int legd = leg[k] != leg[k - 1] ? 1 : 0;
+      int secd = ((int)sector[k] - (int)sector[k - 1] + O_NSEC) % O_NSEC;
+      st |= o_step_predict(&mm, &s, rd, (uint8_t)(legd * O_NSEC + secd), &pred_padq[k],
+                           &pred_timeq[k], &pred_y[k], &pred_t[k]);
+      o_update(&mm, &s, o_pad_to_y(pad[k], s.row), o_time_to_t(time[k]));
+    }
+    float* o = state + 17 * (size_t)k;
+    o[0] = s.x; o[1] = s.y; o[2] = s.ty; o[3] = s.c;
+    o[4] = s.c00; o[5] = s.c01; o[6] = s.c02; o[7] = s.c11; o[8] = s.c12; o[9] = s.c22;
+    o[10] = s.t; o[11] = s.tt; o[12] = s.d00; o[13] = s.d01; o[14] = s.d11;
+    o[15] = (float)s.row; o[16] = (float)s.sec;
+  }
+  return st;
+}
+
+/* Apply one sector change to a given state (x, y, ty, c) and report the
+ * rotated (x, y, ty, c). */
+void tmd_oracle_rotate(int from_sec, int to_sec, const float* in4, float* out4) {
+  o_geo_init();
+  OState s;
+  memset(&s, 0, sizeof(s));
+  s.x = in4[0]; s.y = in4[1]; s.ty = in4[2]; s.c = in4[3]; s.sec = from_sec;
+  o_sector_change(&O_DEFAULT_MODEL, &s, to_sec);
+  out4[0] = s.x; out4[1] = s.y; out4[2] = s.ty; out4[3] = s.c;
+}
+
+uint32_t tmd_oracle_quant(float v, float lo, float hi) { return o_quant(v, lo, hi); }
+
+/* Geometry tables: x[152], w[152], invw[152], np[152], cos[18], sin[18]. */
+void tmd_oracle_geometry(float* x, float* w, float* invw, int32_t* np, float* cs, float* sn) {
+  o_geo_init();
+  for (int r = 0; r < O_NROW; r++) { x[r] = g_x[r]; w[r] = g_w[r]; invw[r] = g_invw[r]; np[r] = g_np[r]; }
+  for (int k = 0; k < 18; k++) { cs[k] = g_cos[k]; sn[k] = g_sin[k]; }
+}
+
+/* Default model parameters (9 floats, OModel order). */
+void tmd_oracle_default_model(float* out9) { memcpy(out9, &O_DEFAULT_MODEL, sizeof(OModel)); }
