@@ -1,0 +1,214 @@
+/*
+ * tmd.h -- C-ABI of the GB300 TPC track-model decoder (libtmd.so).
+ *
+ * What it computes (arXiv:2411.02206, Sec. 3, "TPC track-model decoding on
+ * GPU"): after entropy decoding, a compressed time frame stores the clusters
+ * attached to tracks as residuals to the track model and the unattached
+ * clusters, sorted by position within each (sector,row), as differences to
+ * the preceding cluster.  Decoding restores the absolute coordinates and
+ * writes the native cluster list grouped by (sector,row).
+ *
+ * Conventions
+ *   - Bins: bin = sector * 152 + row, 36 sectors x 152 pad rows = 5472 bins.
+ *   - Codes: pad in 1/64 pad (u16), time in 1/32 time bin (u32).
+ *   - Residuals and differences are modular: pad mod 2^16, time mod 2^32.
+ *   - Native record (12 bytes, little endian): u32 (time & 0xFFFFFF) |
+ *     flags << 24; u16 pad; u8 sigmaTime; u8 sigmaPad; u16 qMax; u16 qTot.
+ *     Within a bin: the attached clusters in (track, cluster) order, then the
+ *     unattached clusters in stored order.
+ *   - All pointers in tmd_frame_in / tmd_frame_out are device pointers unless
+ *     the entry point says otherwise.  The caller owns every buffer it passes.
+ *   - Every entry point returns TMD_OK (0) or a negative TMD_ERR_* code and
+ *     never throws; tmd_last_error_string() describes the last failure.
+ *   - A handle is used by one host thread at a time, except tmd_submit /
+ *     tmd_poll / tmd_release, which lock internally.
+ */
+#ifndef TMD_H
+#define TMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TMD_NSEC 36
+#define TMD_NROW 152
+#define TMD_NBIN 5472
+#define TMD_REC_BYTES 12
+
+/* return codes */
+#define TMD_OK 0
+#define TMD_PENDING 1        /* tmd_poll: not finished within the timeout */
+#define TMD_ERR_ARG (-1)     /* invalid argument: null/misaligned pointer, bad size */
+#define TMD_ERR_CORRUPT (-2) /* the frame's status word has error bits (host-side checks) */
+#define TMD_ERR_BUDGET (-3)  /* a frame can never fit the serving memory budget */
+#define TMD_ERR_TIMEOUT (-4) /* a bounded wait ran out */
+#define TMD_ERR_CUDA (-5)    /* a CUDA runtime call failed */
+#define TMD_ERR_NOMEM (-6)   /* device or host allocation failed */
+#define TMD_ERR_STATE (-7)   /* unknown request id, request already released, ... */
+
+/* bits of the device-written status word of a decoded frame */
+#define TMD_STATUS_COUNT 1u   /* sum of nCl != n_attached, some nCl == 0, or
+                                 sum of n_unatt != n_unattached: nothing decoded */
+#define TMD_STATUS_ROW 2u     /* a row >= 152 or a header sector >= 36 was met */
+#define TMD_STATUS_TIME 4u    /* a decoded time code >= 2^24 (truncated in the record) */
+#define TMD_STATUS_TIMEOUT 8u /* a bounded wait inside a kernel ran out */
+#define TMD_STATUS_LIMIT 16u  /* the frame breaks a decoder limit (record not written) */
+
+typedef struct tmd_handle tmd_handle;
+
+typedef struct tmd_config {
+  int device;                /* CUDA device ordinal */
+  uint64_t mem_budget_bytes; /* serving: device bytes for resident frames (0: 120 GB) */
+  uint32_t max_slots;        /* serving: frames resident at once (0: 256) */
+  const char* autotune_cache;/* path of the autotune cache (JSON), or NULL */
+  uint32_t flags;            /* reserved, 0 */
+} tmd_config;
+
+/* A compressed frame: SoA streams after entropy decoding.  Lengths:
+ *   per track:                       n_tracks
+ *   per attached cluster:            n_attached       (sum of ncl)
+ *   per attached cluster after the
+ *   first of its track:              n_attached - n_tracks
+ *   per bin:                         5472
+ *   per unattached cluster:          n_unattached     (sum of n_unatt)
+ * pad_diff_u and time_diff_u must be 16-byte aligned; other arrays need their
+ * natural alignment.  A pointer whose length is 0 may be NULL. */
+typedef struct tmd_frame_in {
+  uint32_t n_tracks, n_attached, n_unattached;
+  /* per track: q/pT code (q/pT = (code - 127.5) * 5/64 (GeV/c)^-1) and the
+   * first cluster stored absolute */
+  const uint8_t* qpt;
+  const uint8_t* row;
+  const uint8_t* slice;
+  const uint16_t* pad;
+  const uint32_t* time;
+  const uint16_t* ncl;
+  /* per attached cluster (the first of each track included) */
+  const uint16_t* qtot_a;
+  const uint16_t* qmax_a;
+  const uint8_t* flags_a;
+  const uint8_t* sigma_pad_a;
+  const uint8_t* sigma_time_a;
+  /* per attached cluster after the first of its track */
+  const uint8_t* row_diff;       /* row - previous row, mod 256 */
+  const uint8_t* slice_leg_diff; /* 36 * (new leg ? 1 : 0) + (sector - prev) mod 36 */
+  const uint16_t* pad_res;       /* pad code - predicted pad code, mod 2^16 */
+  const uint32_t* time_res;      /* time code - predicted time code, mod 2^32 */
+  /* per bin */
+  const uint32_t* n_unatt;
+  /* per unattached cluster, bins in order, clusters in stored order */
+  const uint16_t* pad_diff_u;  /* pad - previous pad of the bin (first: - 0), mod 2^16 */
+  const uint32_t* time_diff_u; /* time - previous time of the bin, mod 2^32 */
+  const uint16_t* qtot_u;
+  const uint16_t* qmax_u;
+  const uint8_t* flags_u;
+  const uint8_t* sigma_pad_u;
+  const uint8_t* sigma_time_u;
+} tmd_frame_in;
+
+/* Decoder output.  native: (n_attached + n_unattached) * 12 bytes, 4-byte
+ * aligned.  row_start: 5473 entries, row_start[b] = first record of bin b,
+ * row_start[5472] = total.  att_count: 5472 entries or NULL: attached records
+ * of bin b (they come first in the bin).  status: one u32 (TMD_STATUS_*). */
+typedef struct tmd_frame_out {
+  uint8_t* native;
+  uint32_t* row_start;
+  uint32_t* att_count;
+  uint32_t* status;
+} tmd_frame_out;
+
+/* Encoder input: the attached clusters of a frame as quantised truth, in
+ * (track, cluster) order, with the leg index of every cluster (a change of
+ * leg index starts a new leg). */
+typedef struct tmd_truth_in {
+  uint32_t n_tracks, n_attached;
+  const uint8_t* qpt;  /* per track */
+  const uint16_t* ncl; /* per track */
+  const uint8_t* row;  /* per attached cluster */
+  const uint8_t* sector;
+  const uint8_t* leg;
+  const uint16_t* pad;
+  const uint32_t* time;
+} tmd_truth_in;
+
+/* Encoder output: the track headers and the attached residual streams of a
+ * compressed frame (lengths as in tmd_frame_in).  The charge, sigma and flag
+ * streams of the truth are already in compressed form and are not copied. */
+typedef struct tmd_track_out {
+  uint8_t* qpt;
+  uint8_t* row;
+  uint8_t* slice;
+  uint16_t* pad;
+  uint32_t* time;
+  uint16_t* ncl;
+  uint8_t* row_diff;
+  uint8_t* slice_leg_diff;
+  uint16_t* pad_res;
+  uint32_t* time_res;
+  uint32_t* status; /* one u32 */
+} tmd_track_out;
+
+/* Create a decoder on cfg->device.  *out receives the handle. */
+int tmd_create(const tmd_config* cfg, tmd_handle** out);
+
+/* Drain or cancel in-flight served requests and free every buffer the handle
+ * owns.  The handle is invalid afterwards. */
+int tmd_destroy(tmd_handle* h);
+
+/* Text of the last error on this handle ("" if none); valid until the next call. */
+const char* tmd_last_error_string(const tmd_handle* h);
+
+/* Decode one frame (Sec. 3), asynchronously on `stream` (a cudaStream_t, or
+ * NULL for the legacy default stream).  Inputs and outputs are device
+ * buffers borrowed until the stream reaches the end of the decode.  The
+ * handle keeps scratch memory sized for the largest frame seen. */
+int tmd_decode_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out,
+                     void* stream);
+
+/* Decode n frames in one launch sequence (the same kernels run over the work
+ * items of all frames).  Results equal those of n tmd_decode_frame calls. */
+int tmd_decode_batch(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
+                     const tmd_frame_out* out, void* stream);
+
+/* Decode one frame given HOST buffers: the inputs are copied to handle-owned
+ * device memory, decoded, and native / row_start / att_count / status copied
+ * back to the host buffers in `out`.  Synchronous on return.  Pinned host
+ * memory gives the fastest copies. */
+int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out,
+                          void* stream);
+
+/* Track-model encoding of the attached clusters (the synchronous side of
+ * Sec. 3), device buffers, asynchronous on `stream`. */
+int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,
+                      void* stream);
+
+/* Serving.  tmd_submit copies the frame (device pointers) into memory the
+ * handle owns and queues it; frames are admitted while the memory budget and
+ * the slot table allow and are decoded in batches as they arrive.
+ * TMD_ERR_BUDGET if the frame can never fit the budget. */
+int tmd_submit(tmd_handle* h, const tmd_frame_in* in, uint64_t* req_id);
+
+/* Wait up to timeout_us for request req_id.  TMD_OK: *out receives device
+ * pointers owned by the handle until tmd_release; TMD_PENDING: not done yet. */
+int tmd_poll(tmd_handle* h, uint64_t req_id, uint32_t timeout_us, tmd_frame_out* out);
+
+/* Free the buffers of a finished request. */
+int tmd_release(tmd_handle* h, uint64_t req_id);
+
+/* Instrumentation.  While enabled, every kernel the handle launches is
+ * bracketed by CUDA events on its stream.  tmd_profile_read waits for the
+ * recorded launches, returns per kernel its name (32-byte slots in
+ * names_out), total device milliseconds and launch count, resets the
+ * counters, and sets *n_out to the number of kernels reported (<= max). */
+int tmd_profile_enable(tmd_handle* h, int on);
+int tmd_profile_read(tmd_handle* h, uint32_t max, char* names_out, double* ms_out,
+                     uint32_t* launches_out, uint32_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMD_H */

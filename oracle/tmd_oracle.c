@@ -115,7 +115,8 @@ typedef struct {
   float c00, c01, c02, c11, c12, c22; /* y-block covariance (upper triangle) */
   float t, tt;                  /* t-block: line in drift time */
   float d00, d01, d11;          /* t-block covariance */
-  int row, sec;
+  int raw_row;                  /* row walk: header row + row differences, mod 256 */
+  int row, sec;                 /* row used by the model: min(raw_row, 151) */
 } OState;
 
 /* Quantisation: clamp to [lo, hi] (a NaN goes to lo), then floor(v + 0.5). */
@@ -138,9 +139,11 @@ static float o_time_to_t(uint32_t timeq) { return (float)timeq * 0.03125f; }
 static float o_qpt(uint8_t qpta) { return ((float)qpta - 127.5f) * 0.078125f; }
 
 /* Seed from the first cluster of the track (stored absolute in the header). */
-static void o_seed(const OModel* m, OState* s, uint8_t qpta, int row, int sec,
+static void o_seed(const OModel* m, OState* s, uint8_t qpta, int raw_row, int sec,
                    uint32_t padq, uint32_t timeq) {
   float qpt = o_qpt(qpta);
+  int row = raw_row < O_NROW ? raw_row : O_NROW - 1;
+  s->raw_row = raw_row;
   s->row = row;
   s->sec = sec;
   s->x = g_x[row];
@@ -260,7 +263,8 @@ static uint32_t o_step_predict(const OModel* m, OState* s, uint8_t row_diff,
   uint32_t st = 0;
   int leg = slice_leg_diff / O_NSEC;
   int sd = slice_leg_diff % O_NSEC;
-  int row = (s->row + row_diff) & 255;
+  s->raw_row = (s->raw_row + row_diff) & 255;
+  int row = s->raw_row;
   if (row >= O_NROW) { st |= O_ST_ROW; row = O_NROW - 1; }
   if (leg != 0) o_leg_change(m, s);
   if (sd != 0) o_sector_change(m, s, (s->sec + sd) % O_NSEC);
@@ -328,13 +332,15 @@ static uint32_t o_attached_bins(const OFrame* f, const uint32_t* tstart, uint16_
   uint32_t st = 0;
   for (uint32_t t = 0; t < f->n_tracks; t++) {
     uint32_t j0 = tstart[t], n = f->ncl[t];
-    int row = f->row[t], sec = f->slice[t];
+    int raw = f->row[t], sec = f->slice[t];
+    int row = raw;
     if (row >= O_NROW) { st |= O_ST_ROW; row = O_NROW - 1; }
     if (sec >= O_NSEC) { st |= O_ST_ROW; sec = O_NSEC - 1; }
     bins[j0] = (uint16_t)(sec * O_NROW + row);
     for (uint32_t k = 1; k < n; k++) {
       uint32_t d = j0 - t + k - 1;
-      row = (row + f->row_diff[d]) & 255;
+      raw = (raw + f->row_diff[d]) & 255;
+      row = raw;
       if (row >= O_NROW) { st |= O_ST_ROW; row = O_NROW - 1; }
       sec = (sec + f->slice_leg_diff[d] % O_NSEC) % O_NSEC;
       bins[j0 + k] = (uint16_t)(sec * O_NROW + row);
@@ -392,10 +398,9 @@ int tmd_oracle_decode(const OFrame* f, uint8_t* native, uint32_t* row_start,
   /* attached clusters: tracks in order, clusters in order */
   for (uint32_t t = 0; t < f->n_tracks; t++) {
     uint32_t j0 = tstart[t], n = f->ncl[t];
-    int row0 = f->row[t] < O_NROW ? f->row[t] : O_NROW - 1;
     int sec0 = f->slice[t] < O_NSEC ? f->slice[t] : O_NSEC - 1;
     OState s;
-    o_seed(m, &s, f->qpt[t], row0, sec0, f->pad[t], f->time[t]);
+    o_seed(m, &s, f->qpt[t], f->row[t], sec0, f->pad[t], f->time[t]);
     uint32_t padq = f->pad[t], timeq = f->time[t];
     for (uint32_t k = 0; k < n; k++) {
       uint32_t j = j0 + k;

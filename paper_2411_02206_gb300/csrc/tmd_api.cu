@@ -1,0 +1,505 @@
+// tmd_api.cu -- C-ABI of the decoder: handle, scratch planning, launch chain.
+//
+// One call decodes a batch of frames (a single frame is a batch of one) with
+// the same kernel sequence; every kernel covers the work items of all frames
+// and finds its frame from a prefix table (tmd_internal.cuh).
+//
+//   k_zero_status -> k_track_scan1 -> k_frame_scan -> k_track_scan2   (a1)
+//   k_count_rank                                                       (a2)
+//   k_group_sum -> k_row_offsets -> k_tile_base                        (a3)
+//   k_track_decode                                                     (a4)
+//   k_unatt_decode                                                     (a5)
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tmd.h"
+#include "tmd_api_internal.h"
+#include "tmd_internal.cuh"
+
+using namespace tmd;
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+bool misaligned(const void* p, size_t a) { return ((uintptr_t)p) % a != 0; }
+
+}  // namespace
+
+int tmd_set_error(tmd_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+int tmd_cuda_check(tmd_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TMD_OK;
+  return tmd_set_error(h, TMD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    const int rc_ = tmd_cuda_check(h, (call), #call);                   \
+    if (rc_ != TMD_OK) return rc_;                                      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// validation and planning
+// ---------------------------------------------------------------------------
+int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out) {
+  if (!in || !out) return tmd_set_error(h, TMD_ERR_ARG, "null frame descriptor");
+  const uint64_t nt = in->n_tracks, na = in->n_attached, nu = in->n_unattached;
+  if (na < nt) return tmd_set_error(h, TMD_ERR_ARG, "n_attached < n_tracks");
+  if (na + nu >= 0xFFFFFFFFull)
+    return tmd_set_error(h, TMD_ERR_ARG, "frame larger than 2^32 - 1 clusters");
+  struct P { const void* p; uint64_t n; const char* name; };
+  const P ps[] = {
+      {in->qpt, nt, "qpt"}, {in->row, nt, "row"}, {in->slice, nt, "slice"}, {in->pad, nt, "pad"},
+      {in->time, nt, "time"}, {in->ncl, nt, "ncl"}, {in->qtot_a, na, "qtot_a"},
+      {in->qmax_a, na, "qmax_a"}, {in->flags_a, na, "flags_a"},
+      {in->sigma_pad_a, na, "sigma_pad_a"}, {in->sigma_time_a, na, "sigma_time_a"},
+      {in->row_diff, na - nt, "row_diff"}, {in->slice_leg_diff, na - nt, "slice_leg_diff"},
+      {in->pad_res, na - nt, "pad_res"}, {in->time_res, na - nt, "time_res"},
+      {in->n_unatt, 1, "n_unatt"}, {in->pad_diff_u, nu, "pad_diff_u"},
+      {in->time_diff_u, nu, "time_diff_u"}, {in->qtot_u, nu, "qtot_u"},
+      {in->qmax_u, nu, "qmax_u"}, {in->flags_u, nu, "flags_u"},
+      {in->sigma_pad_u, nu, "sigma_pad_u"}, {in->sigma_time_u, nu, "sigma_time_u"},
+      {out->row_start, 1, "row_start"}, {out->status, 1, "status"},
+      {out->native, na + nu, "native"}};
+  for (const P& p : ps)
+    if (p.n && !p.p) return tmd_set_error(h, TMD_ERR_ARG, "%s is NULL", p.name);
+  if (misaligned(in->pad_diff_u, 16) || misaligned(in->time_diff_u, 16))
+    return tmd_set_error(h, TMD_ERR_ARG, "pad_diff_u/time_diff_u must be 16-byte aligned");
+  if (misaligned(out->native, 4)) return tmd_set_error(h, TMD_ERR_ARG, "native must be 4-byte aligned");
+  if (misaligned(in->pad, 2) || misaligned(in->ncl, 2) || misaligned(in->qtot_a, 2) ||
+      misaligned(in->qmax_a, 2) || misaligned(in->pad_res, 2) || misaligned(in->qtot_u, 2) ||
+      misaligned(in->qmax_u, 2) || misaligned(in->time, 4) || misaligned(in->time_res, 4) ||
+      misaligned(in->n_unatt, 4) || misaligned(out->row_start, 4) ||
+      misaligned(out->att_count, 4) || misaligned(out->status, 4))
+    return tmd_set_error(h, TMD_ERR_ARG, "array not aligned to its element size");
+  return TMD_OK;
+}
+
+// Scratch layout of one frame.  The zeroed part of all frames is contiguous.
+struct FrameLayout {
+  uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
+  size_t z_heads, z_len, z_lb;                    // offsets in the zeroed part
+  size_t track_start, order, rank, tile_hist, group_sum, tile_base, unatt_start, blk_sum,
+      att_count;                                  // offsets in the plain part
+};
+
+static void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
+                       FrameLayout& L) {
+  L.n_tblocks = ceil_div(nt, kTrackBlk);
+  L.n_tiles = ceil_div(na, kTile);
+  L.n_groups = ceil_div(L.n_tiles, kGroup);
+  L.n_chunks = ceil_div(nu, kChunk);
+  auto z = [&](size_t bytes) { size_t o = zoff; zoff = align_up(zoff + bytes, 256); return o; };
+  auto p = [&](size_t bytes) { size_t o = poff; poff = align_up(poff + bytes, 256); return o; };
+  L.z_heads = z(((size_t)na / 32 + 32) * 4);
+  L.z_len = z((size_t)kLenBuckets * 4);
+  L.z_lb = z((size_t)L.n_chunks * 8 + 8);
+  L.track_start = p(((size_t)nt + 1) * 4);
+  L.order = p((size_t)nt * 4 + 4);
+  L.rank = p((size_t)na * 2 + 4);
+  L.tile_hist = p((size_t)L.n_tiles * kNBin * 2 + 4);
+  L.group_sum = p((size_t)L.n_groups * kNBin * 4 + 4);
+  L.tile_base = p((size_t)L.n_tiles * kNBin * 4 + 4);
+  L.unatt_start = p(((size_t)kNBin + 1) * 4);
+  L.blk_sum = p((size_t)L.n_tblocks * 4 + 4);
+  L.att_count = p((size_t)kNBin * 4);
+}
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+int tmd_handle::ensure_scratch(size_t bytes) {
+  if (bytes <= scratch_bytes) return TMD_OK;
+  tmd_handle* h = this;
+  if (scratch) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaFree(scratch));
+    scratch = nullptr;
+    scratch_bytes = 0;
+  }
+  const size_t want = align_up(bytes + bytes / 8, 1 << 20);
+  if (cudaMalloc(&scratch, want) != cudaSuccess) {
+    cudaGetLastError();
+    scratch = nullptr;
+    return tmd_set_error(h, TMD_ERR_NOMEM, "cudaMalloc of %zu bytes of scratch failed", want);
+  }
+  scratch_bytes = want;
+  return TMD_OK;
+}
+
+int tmd_handle::acquire_slot(size_t bytes, int& slot) {
+  tmd_handle* h = this;
+  slot = next_slot;
+  next_slot = (next_slot + 1) % kSlots;
+  Slot& s = slots[slot];
+  if (s.used) CK(cudaEventSynchronize(s.done));
+  if (bytes > s.bytes) {
+    if (s.host) cudaFreeHost(s.host);
+    if (s.dev) cudaFree(s.dev);
+    s.host = nullptr;
+    s.dev = nullptr;
+    s.bytes = 0;
+    const size_t want = align_up(bytes, 4096);
+    if (cudaMallocHost(&s.host, want) != cudaSuccess || cudaMalloc(&s.dev, want) != cudaSuccess) {
+      cudaGetLastError();
+      return tmd_set_error(h, TMD_ERR_NOMEM, "launch record allocation failed");
+    }
+    s.bytes = want;
+  }
+  if (!s.done) CK(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+  return TMD_OK;
+}
+
+tmd_handle::~tmd_handle() {
+  for (Slot& s : slots) {
+    if (s.used && s.done) cudaEventSynchronize(s.done);
+    if (s.host) cudaFreeHost(s.host);
+    if (s.dev) cudaFree(s.dev);
+    if (s.done) cudaEventDestroy(s.done);
+  }
+  if (scratch) cudaFree(scratch);
+  if (stage) cudaFree(stage);
+}
+
+extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
+  if (!cfg || !out) return TMD_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return TMD_ERR_ARG;
+  }
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return TMD_ERR_CUDA;
+  tmd_handle* h = new (std::nothrow) tmd_handle();
+  if (!h) return TMD_ERR_NOMEM;
+  h->device = cfg->device;
+  h->mem_budget = cfg->mem_budget_bytes ? cfg->mem_budget_bytes : (uint64_t)120 << 30;
+  h->max_slots = cfg->max_slots ? cfg->max_slots : 256;
+  if (cfg->autotune_cache) h->autotune_cache = cfg->autotune_cache;
+  int rc = TMD_OK;
+  if ((rc = tmd_cuda_check(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount,
+                                                    h->device), "sm count")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaFuncSetAttribute(k_count_rank,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kCountRankSmem), "smem attribute")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                  &h->occ_decode, k_track_decode, 256, 0), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                  &h->occ_unatt, k_unatt_decode, 256, 0), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                  &h->occ_encode, k_track_encode, 256, 0), "occupancy")) != TMD_OK) {
+    delete h;
+    return rc;
+  }
+  if (h->occ_decode < 1) h->occ_decode = 1;
+  if (h->occ_unatt < 1) h->occ_unatt = 1;
+  if (h->occ_encode < 1) h->occ_encode = 1;
+  *out = h;
+  return TMD_OK;
+}
+
+extern "C" int tmd_destroy(tmd_handle* h) {
+  if (!h) return TMD_ERR_ARG;
+  cudaSetDevice(h->device);
+  tmd_serve_shutdown(h);
+  delete h;
+  return TMD_OK;
+}
+
+extern "C" const char* tmd_last_error_string(const tmd_handle* h) {
+  return h ? h->err.c_str() : "null handle";
+}
+
+// ---------------------------------------------------------------------------
+// instrumentation
+// ---------------------------------------------------------------------------
+static const char* kKernelNames[kKNum] = {
+    "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_count_rank",
+    "k_group_sum", "k_row_offsets", "k_tile_base", "k_track_decode", "k_unatt_decode",
+    "k_track_encode"};
+
+cudaEvent_t TmdProfile::get() {
+  if (pool.empty()) {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t e = pool.back();
+  pool.pop_back();
+  return e;
+}
+
+void TmdProfile::drain(size_t keep) {
+  if (pending.size() <= keep) return;
+  const size_t n = pending.size() - keep;
+  cudaEventSynchronize(pending[n - 1].second.second);
+  for (size_t i = 0; i < n; i++) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, pending[i].second.first, pending[i].second.second) == cudaSuccess) {
+      ms[pending[i].first] += t;
+      launches[pending[i].first] += 1;
+    }
+    pool.push_back(pending[i].second.first);
+    pool.push_back(pending[i].second.second);
+  }
+  pending.erase(pending.begin(), pending.begin() + n);
+}
+
+TmdProfile::~TmdProfile() {
+  for (auto& p : pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+extern "C" int tmd_profile_enable(tmd_handle* h, int on) {
+  if (!h) return TMD_ERR_ARG;
+  h->prof.on = on != 0;
+  return TMD_OK;
+}
+
+extern "C" int tmd_profile_read(tmd_handle* h, uint32_t max, char* names_out, double* ms_out,
+                                uint32_t* launches_out, uint32_t* n_out) {
+  if (!h || !n_out) return TMD_ERR_ARG;
+  cudaSetDevice(h->device);
+  h->prof.drain(0);
+  uint32_t n = 0;
+  for (int k = 0; k < kKNum && n < max; k++) {
+    if (!h->prof.launches[k]) continue;
+    if (names_out) {
+      strncpy(names_out + 32 * n, kKernelNames[k], 31);
+      names_out[32 * n + 31] = 0;
+    }
+    if (ms_out) ms_out[n] = h->prof.ms[k];
+    if (launches_out) launches_out[n] = h->prof.launches[k];
+    n++;
+  }
+  for (int k = 0; k < kKNum; k++) {
+    h->prof.ms[k] = 0.0;
+    h->prof.launches[k] = 0;
+  }
+  *n_out = n;
+  return TMD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch chain
+// ---------------------------------------------------------------------------
+// Record uploaded per call: prefix tables, then FrameDev[n], then EncDev[n].
+struct RecordLayout {
+  size_t pre, frames, enc, counters_unused, bytes;
+};
+
+static RecordLayout record_layout(uint32_t n, bool enc) {
+  RecordLayout r;
+  r.pre = 0;
+  r.frames = align_up(5 * ((size_t)n + 1) * 4, 64);
+  r.enc = align_up(r.frames + (size_t)n * sizeof(FrameDev), 64);
+  r.bytes = align_up(r.enc + (enc ? (size_t)n * sizeof(EncDev) : 0), 64);
+  r.counters_unused = 0;
+  return r;
+}
+
+int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
+               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st) {
+  const bool encode = tin != nullptr;
+  CK(cudaSetDevice(h->device));
+  // plan every frame
+  std::vector<FrameLayout> L(nf);
+  size_t zoff = 256 + align_up((size_t)kNBin * 4, 256);  // counters + zero bins
+  size_t poff = 0;
+  for (uint32_t f = 0; f < nf; f++) {
+    const uint32_t nt = encode ? tin[f].n_tracks : in[f].n_tracks;
+    const uint32_t na = encode ? tin[f].n_attached : in[f].n_attached;
+    const uint32_t nu = encode ? 0u : in[f].n_unattached;
+    plan_frame(nt, na, nu, zoff, poff, L[f]);
+  }
+  const size_t zbytes = align_up(zoff, 256);
+  int rc = h->ensure_scratch(zbytes + poff);
+  if (rc != TMD_OK) return rc;
+  char* zb = static_cast<char*>(h->scratch);
+  char* pb = zb + zbytes;
+  const RecordLayout R = record_layout(nf, encode);
+  int slot = 0;
+  if ((rc = h->acquire_slot(R.bytes, slot)) != TMD_OK) return rc;
+  tmd_handle::Slot& S = h->slots[slot];
+  char* host = static_cast<char*>(S.host);
+  char* dev = static_cast<char*>(S.dev);
+  uint32_t* pre = reinterpret_cast<uint32_t*>(host + R.pre);
+  uint32_t* pre_tblk = pre;
+  uint32_t* pre_tile = pre + (nf + 1);
+  uint32_t* pre_grp = pre + 2 * (nf + 1);
+  uint32_t* pre_warp = pre + 3 * (nf + 1);
+  uint32_t* pre_chunk = pre + 4 * (nf + 1);
+  FrameDev* fd = reinterpret_cast<FrameDev*>(host + R.frames);
+  EncDev* ed = reinterpret_cast<EncDev*>(host + R.enc);
+  pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = 0;
+  uint32_t* zero_bins = reinterpret_cast<uint32_t*>(zb + 256);
+  for (uint32_t f = 0; f < nf; f++) {
+    FrameDev& F = fd[f];
+    memset(&F, 0, sizeof F);
+    const FrameLayout& l = L[f];
+    if (encode) {
+      const tmd_truth_in& T = tin[f];
+      F.n_tracks = T.n_tracks;
+      F.n_att = T.n_attached;
+      F.n_unatt = 0;
+      F.ncl = T.ncl;
+      F.n_unatt_bin = zero_bins;
+      F.status = tout[f].status;
+      EncDev& E = ed[f];
+      E.n_tracks = T.n_tracks; E.n_att = T.n_attached;
+      E.qpt = T.qpt; E.ncl = T.ncl; E.row = T.row; E.sector = T.sector; E.leg = T.leg;
+      E.pad = T.pad; E.time = T.time;
+      const tmd_track_out& O = tout[f];
+      E.o_qpt = O.qpt; E.o_row = O.row; E.o_slice = O.slice; E.o_pad = O.pad;
+      E.o_time = O.time; E.o_ncl = O.ncl; E.o_row_diff = O.row_diff;
+      E.o_sld = O.slice_leg_diff; E.o_pad_res = O.pad_res; E.o_time_res = O.time_res;
+    } else {
+      const tmd_frame_in& I = in[f];
+      const tmd_frame_out& O = out[f];
+      F.n_tracks = I.n_tracks; F.n_att = I.n_attached; F.n_unatt = I.n_unattached;
+      F.qpt = I.qpt; F.row = I.row; F.slice = I.slice; F.pad = I.pad; F.time = I.time;
+      F.ncl = I.ncl; F.qtot_a = I.qtot_a; F.qmax_a = I.qmax_a; F.flags_a = I.flags_a;
+      F.sigp_a = I.sigma_pad_a; F.sigt_a = I.sigma_time_a; F.row_diff = I.row_diff;
+      F.sld = I.slice_leg_diff; F.pad_res = I.pad_res; F.time_res = I.time_res;
+      F.n_unatt_bin = I.n_unatt; F.pad_diff_u = I.pad_diff_u; F.time_diff_u = I.time_diff_u;
+      F.qtot_u = I.qtot_u; F.qmax_u = I.qmax_u; F.flags_u = I.flags_u;
+      F.sigp_u = I.sigma_pad_u; F.sigt_u = I.sigma_time_u;
+      F.native = O.native; F.row_start = O.row_start; F.status = O.status;
+      F.att_count = O.att_count ? O.att_count : reinterpret_cast<uint32_t*>(pb + l.att_count);
+    }
+    F.n_tblocks = l.n_tblocks; F.n_tiles = l.n_tiles; F.n_groups = l.n_groups;
+    F.n_chunks = l.n_chunks;
+    F.heads = reinterpret_cast<uint32_t*>(zb + l.z_heads);
+    F.len_cursor = reinterpret_cast<uint32_t*>(zb + l.z_len);
+    F.lookback = reinterpret_cast<unsigned long long*>(zb + l.z_lb);
+    F.track_start = reinterpret_cast<uint32_t*>(pb + l.track_start);
+    F.order = reinterpret_cast<uint32_t*>(pb + l.order);
+    F.rank = reinterpret_cast<uint16_t*>(pb + l.rank);
+    F.tile_hist = reinterpret_cast<uint16_t*>(pb + l.tile_hist);
+    F.group_sum = reinterpret_cast<uint32_t*>(pb + l.group_sum);
+    F.tile_base = reinterpret_cast<uint32_t*>(pb + l.tile_base);
+    F.unatt_start = reinterpret_cast<uint32_t*>(pb + l.unatt_start);
+    F.blk_sum = reinterpret_cast<uint32_t*>(pb + l.blk_sum);
+    pre_tblk[f + 1] = pre_tblk[f] + l.n_tblocks;
+    pre_tile[f + 1] = pre_tile[f] + l.n_tiles;
+    pre_grp[f + 1] = pre_grp[f] + l.n_groups * kBinBlocks;
+    pre_warp[f + 1] = pre_warp[f] + ceil_div(F.n_tracks, 32);
+    pre_chunk[f + 1] = pre_chunk[f] + l.n_chunks;
+  }
+  PlanDev P;
+  const uint32_t* dpre = reinterpret_cast<const uint32_t*>(dev + R.pre);
+  P.n_frames = nf;
+  P.pre_tblk = dpre;
+  P.pre_tile = dpre + (nf + 1);
+  P.pre_grp = dpre + 2 * (nf + 1);
+  P.pre_warp = dpre + 3 * (nf + 1);
+  P.pre_chunk = dpre + 4 * (nf + 1);
+  P.counters = reinterpret_cast<uint32_t*>(zb);
+  const FrameDev* dframes = reinterpret_cast<const FrameDev*>(dev + R.frames);
+  const EncDev* denc = reinterpret_cast<const EncDev*>(dev + R.enc);
+
+  CK(cudaMemcpyAsync(dev, host, R.bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(zb, 0, zbytes, st));
+  TmdProfile& prof = h->prof;
+  auto timed = [&](int id, auto&& launch) {
+    if (!prof.on) {
+      launch();
+      return;
+    }
+    cudaEvent_t a = prof.get(), b = prof.get();
+    cudaEventRecord(a, st);
+    launch();
+    cudaEventRecord(b, st);
+    prof.pending.push_back({id, {a, b}});
+    if (prof.pending.size() >= 4096) prof.drain(2048);
+  };
+  timed(kKZeroStatus, [&] { k_zero_status<<<1, 256, 0, st>>>(dframes, nf); });
+  const uint32_t n_tblk = pre_tblk[nf], n_tile = pre_tile[nf], n_grp = pre_grp[nf];
+  const uint32_t n_warp = pre_warp[nf], n_chunk = pre_chunk[nf];
+  if (n_tblk) timed(kKTrackScan1, [&] { k_track_scan1<<<n_tblk, 256, 0, st>>>(dframes, P); });
+  timed(kKFrameScan, [&] { k_frame_scan<<<nf, 1024, 0, st>>>(dframes, P); });
+  if (n_tblk) timed(kKTrackScan2, [&] { k_track_scan2<<<n_tblk, 256, 0, st>>>(dframes, P); });
+  if (encode) {
+    if (n_warp) {
+      const uint32_t grid = std::min<uint32_t>(n_warp / 8 + 1, (uint32_t)(h->sms * h->occ_encode));
+      timed(kKTrackEncode, [&] { k_track_encode<<<grid, 256, 0, st>>>(denc, dframes, P, n_warp); });
+    }
+  } else {
+    if (n_tile)
+      timed(kKCountRank, [&] { k_count_rank<<<n_tile, 256, kCountRankSmem, st>>>(dframes, P); });
+    if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+    timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
+    if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+    if (n_warp) {
+      const uint32_t grid = std::min<uint32_t>(n_warp / 8 + 1, (uint32_t)(h->sms * h->occ_decode));
+      timed(kKTrackDecode, [&] { k_track_decode<<<grid, 256, 0, st>>>(dframes, P, n_warp); });
+    }
+    if (n_chunk) {
+      const uint32_t grid = std::min<uint32_t>(n_chunk, (uint32_t)(h->sms * h->occ_unatt));
+      timed(kKUnattDecode, [&] { k_unatt_decode<<<grid, 256, 0, st>>>(dframes, P, n_chunk); });
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(S.done, st));
+  S.used = true;
+  return TMD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+extern "C" int tmd_decode_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out,
+                                void* stream) {
+  return tmd_decode_batch(h, 1, in, out, stream);
+}
+
+extern "C" int tmd_decode_batch(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
+                                const tmd_frame_out* out, void* stream) {
+  if (!h) return TMD_ERR_ARG;
+  if (n == 0) return TMD_OK;
+  if (!in || !out) return tmd_set_error(h, TMD_ERR_ARG, "null frame arrays");
+  for (uint32_t f = 0; f < n; f++) {
+    const int rc = tmd_validate_frame(h, &in[f], &out[f]);
+    if (rc != TMD_OK) return rc;
+  }
+  return tmd_launch(h, n, in, out, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,
+                                 void* stream) {
+  if (!h) return TMD_ERR_ARG;
+  if (!in || !out) return tmd_set_error(h, TMD_ERR_ARG, "null descriptor");
+  const uint64_t nt = in->n_tracks, na = in->n_attached;
+  if (na < nt) return tmd_set_error(h, TMD_ERR_ARG, "n_attached < n_tracks");
+  if (!out->status) return tmd_set_error(h, TMD_ERR_ARG, "status is NULL");
+  const void* need_t[] = {in->qpt, in->ncl, out->qpt, out->row, out->slice, out->pad, out->time,
+                          out->ncl};
+  const void* need_a[] = {in->row, in->sector, in->leg, in->pad, in->time};
+  const void* need_d[] = {out->row_diff, out->slice_leg_diff, out->pad_res, out->time_res};
+  for (const void* p : need_t)
+    if (nt && !p) return tmd_set_error(h, TMD_ERR_ARG, "per-track array is NULL");
+  for (const void* p : need_a)
+    if (na && !p) return tmd_set_error(h, TMD_ERR_ARG, "per-cluster array is NULL");
+  for (const void* p : need_d)
+    if (na > nt && !p) return tmd_set_error(h, TMD_ERR_ARG, "residual array is NULL");
+  return tmd_launch(h, 1, nullptr, nullptr, in, out, static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,71 @@
+// tmd_api_internal.h -- the handle behind the C-ABI and the host helpers
+// shared by the library's host translation units.
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tmd.h"
+
+struct TmdServer;  // serving state (tmd_serve.cu)
+
+// Kernel ids of the instrumentation.
+enum TmdKernel {
+  kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKCountRank, kKGroupSum,
+  kKRowOffsets, kKTileBase, kKTrackDecode, kKUnattDecode, kKTrackEncode, kKNum
+};
+
+struct TmdProfile {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;             // free events
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  double ms[kKNum] = {};
+  uint32_t launches[kKNum] = {};
+  cudaEvent_t get();
+  void drain(size_t keep);                   // accumulate all but the newest `keep`
+  ~TmdProfile();
+};
+
+struct tmd_handle {
+  static constexpr int kSlots = 8;
+  struct Slot {
+    void* host = nullptr;   // pinned launch record
+    void* dev = nullptr;    // device copy of the record
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;  // recorded after the last kernel using the slot
+    bool used = false;
+  };
+  int device = 0;
+  int sms = 0;
+  int occ_decode = 1, occ_unatt = 1, occ_encode = 1;
+  uint64_t mem_budget = 0;
+  uint32_t max_slots = 0;
+  std::string autotune_cache;
+  std::string err;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  Slot slots[kSlots];
+  int next_slot = 0;
+  void* stage = nullptr;  // device staging of tmd_decode_frame_host
+  size_t stage_bytes = 0;
+  TmdServer* server = nullptr;
+  TmdProfile prof;
+
+  int ensure_scratch(size_t bytes);
+  int acquire_slot(size_t bytes, int& slot);
+  ~tmd_handle();
+};
+
+int tmd_set_error(tmd_handle* h, int code, const char* fmt, ...);
+int tmd_cuda_check(tmd_handle* h, cudaError_t e, const char* what);
+int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out);
+// Launch the decode chain for nf frames (in/out), or the encode chain for one
+// frame (tin/tout), on stream st, using the handle's scratch.
+int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
+               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st);
+void tmd_serve_shutdown(tmd_handle* h);

@@ -1,0 +1,144 @@
+// tmd_internal.cuh -- device-side frame descriptors and launch helpers shared
+// by the decoder's CUDA translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tmd_model.cuh"
+
+namespace tmd {
+
+// Work decomposition (fixed by the decoder, independent of the GPU model).
+constexpr int kTrackBlk = 2048;          // tracks per block of the track scan
+constexpr int kTile = 32768;             // attached clusters per ranking tile
+constexpr int kTileWarps = 8;            // warps per ranking tile
+constexpr int kTileSub = kTile / kTileWarps;  // clusters per warp of a tile
+constexpr int kGroup = 32;               // tiles per group of the tile scan
+constexpr int kBinBlk = 256;             // bins per block of the tile scan
+constexpr int kBinBlocks = (kNBin + kBinBlk - 1) / kBinBlk;
+constexpr int kChunk = 2048;             // unattached clusters per scan chunk
+constexpr int kLenBuckets = 1024;        // track-length buckets of the decode order
+
+// One frame as the kernels see it: caller inputs, caller outputs, scratch.
+struct FrameDev {
+  uint32_t n_tracks, n_att, n_unatt;
+  uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
+  // per track
+  const uint8_t* qpt;
+  const uint8_t* row;
+  const uint8_t* slice;
+  const uint16_t* pad;
+  const uint32_t* time;
+  const uint16_t* ncl;
+  // per attached cluster
+  const uint16_t* qtot_a;
+  const uint16_t* qmax_a;
+  const uint8_t* flags_a;
+  const uint8_t* sigp_a;
+  const uint8_t* sigt_a;
+  // per attached cluster after the first of its track
+  const uint8_t* row_diff;
+  const uint8_t* sld;
+  const uint16_t* pad_res;
+  const uint32_t* time_res;
+  // per (sector,row)
+  const uint32_t* n_unatt_bin;
+  // per unattached cluster
+  const uint16_t* pad_diff_u;
+  const uint32_t* time_diff_u;
+  const uint16_t* qtot_u;
+  const uint16_t* qmax_u;
+  const uint8_t* flags_u;
+  const uint8_t* sigp_u;
+  const uint8_t* sigt_u;
+  // outputs
+  uint8_t* native;
+  uint32_t* row_start;
+  uint32_t* att_count;
+  uint32_t* status;
+  // scratch
+  uint32_t* track_start;   // n_tracks + 1
+  uint32_t* order;         // n_tracks, longest tracks first
+  uint32_t* heads;         // bit j set iff a track starts at attached cluster j
+  uint16_t* rank;          // n_att: rank of a cluster within its (tile, bin)
+  uint16_t* tile_hist;     // n_tiles x kNBin
+  uint32_t* group_sum;     // n_groups x kNBin
+  uint32_t* tile_base;     // n_tiles x kNBin: first native index of (tile, bin)
+  uint32_t* unatt_start;   // kNBin + 1
+  uint32_t* blk_sum;       // n_tblocks
+  uint32_t* len_cursor;    // kLenBuckets (zeroed)
+  unsigned long long* lookback;  // n_chunks (zeroed)
+};
+
+// Encoder view of a frame: attached truth in, compressed attached streams out.
+struct EncDev {
+  uint32_t n_tracks, n_att;
+  const uint8_t* qpt;
+  const uint16_t* ncl;
+  const uint8_t* row;
+  const uint8_t* sector;
+  const uint8_t* leg;
+  const uint16_t* pad;
+  const uint32_t* time;
+  uint8_t* o_qpt;
+  uint8_t* o_row;
+  uint8_t* o_slice;
+  uint16_t* o_pad;
+  uint32_t* o_time;
+  uint16_t* o_ncl;
+  uint8_t* o_row_diff;
+  uint8_t* o_sld;
+  uint16_t* o_pad_res;
+  uint32_t* o_time_res;
+};
+
+// Launch plan of a batch: for each kernel family the exclusive prefix over
+// frames of its work items, so that a block can find its frame.
+struct PlanDev {
+  uint32_t n_frames;
+  const uint32_t* pre_tblk;   // track-scan blocks
+  const uint32_t* pre_tile;   // ranking tiles
+  const uint32_t* pre_grp;    // tile-group blocks (n_groups * kBinBlocks)
+  const uint32_t* pre_warp;   // decode warp tasks (ceil(n_tracks / 32))
+  const uint32_t* pre_chunk;  // unattached chunks
+  uint32_t* counters;         // [0] decode task, [1] unattached ticket (zeroed)
+};
+
+// Largest f with pre[f] <= item (pre has n+1 entries, pre[0] = 0).
+__device__ __forceinline__ uint32_t find_frame(const uint32_t* pre, uint32_t n, uint32_t item) {
+  uint32_t lo = 0, hi = n;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(pre + mid) <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t lanemask_le() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Kernels (launched by tmd_api.cu).
+__global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames);
+__global__ void k_track_scan1(const FrameDev* frames, PlanDev plan);
+__global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);
+__global__ void k_track_scan2(const FrameDev* frames, PlanDev plan);
+__global__ void k_count_rank(const FrameDev* frames, PlanDev plan);
+__global__ void k_group_sum(const FrameDev* frames, PlanDev plan);
+__global__ void k_row_offsets(const FrameDev* frames, PlanDev plan);
+__global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
+__global__ void k_track_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tasks);
+__global__ void k_unatt_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tickets);
+__global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
+                               uint32_t n_tasks);
+
+constexpr int kCountRankSmem = kTileWarps * kNBin * 2;
+
+}  // namespace tmd

@@ -1,0 +1,240 @@
+// tmd_model.cuh -- device track model for TPC track-model encoding/decoding
+// (arXiv:2411.02206, Sec. 3: "every GPU-thread receives one track, it
+// propagates it through the TPC and computes the absolute values of the
+// coordinates using the residuals given in input and the reconstructed track").
+//
+// The paper leaves the track model to its reference [rohr-global-track]; this
+// library defines it as a linear Kalman filter in the sector-local frame:
+//   y-block (y, ty = dy/dx, c = d2y/dx2), a parabola in x, 3x3 covariance;
+//   t-block (t, tt = dt/dx), a line in drift time, 2x2 covariance.
+// Encoder and decoder run the same sequence of binary32 operations; every
+// operation below is an explicit round-to-nearest intrinsic so that no
+// multiply-add can be contracted, whatever the compiler flags.
+#pragma once
+#include <cstdint>
+
+namespace tmd {
+
+constexpr int kNSec = 36;
+constexpr int kNRow = 152;
+constexpr int kNBin = kNSec * kNRow;
+constexpr int kRecBytes = 12;
+
+// status bits (also in include/tmd.h)
+constexpr uint32_t kStCount = 1u;
+constexpr uint32_t kStRow = 2u;
+constexpr uint32_t kStTime = 4u;
+constexpr uint32_t kStTimeout = 8u;
+constexpr uint32_t kStLimit = 16u;
+
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// Model constants (binary32).
+constexpr float kSY2 = 0.01f;     // measurement variance of y [cm^2]
+constexpr float kST2 = 0.04f;     // measurement variance of t [bin^2]
+constexpr float kQTY = 1.0e-6f;   // process noise of dy/dx per cm of |dx|
+constexpr float kQTT = 4.0e-6f;   // process noise of dt/dx per cm of |dx|
+constexpr float kCTY0 = 0.01f;    // seed variance of dy/dx
+constexpr float kCC0 = 1.0e-8f;   // seed variance of d2y/dx2 [cm^-2]
+constexpr float kCTT0 = 4.0f;     // seed variance of dt/dx
+constexpr float kSYR = 0.25f;     // y variance after a sector or leg change
+constexpr float kKC = 0.0015f;    // |d2y/dx2| per unit q/pT
+constexpr float kTan10 = 0x1.691e1ep-3f;  // binary32 nearest tan(10 deg)
+constexpr float kPadHi = 65535.0f;
+constexpr float kTimeHi = 8388607.0f;
+
+// cos/sin of k * 20 deg, k = 0..17, correctly rounded to binary32.
+__constant__ float c_cos20[18] = {
+    0x1p+0f,         0x1.e11f64p-1f,  0x1.8836fap-1f,  0x1p-1f,         0x1.63a1a8p-3f,
+    -0x1.63a1a8p-3f, -0x1p-1f,        -0x1.8836fap-1f, -0x1.e11f64p-1f, -0x1p+0f,
+    -0x1.e11f64p-1f, -0x1.8836fap-1f, -0x1p-1f,        -0x1.63a1a8p-3f, 0x1.63a1a8p-3f,
+    0x1p-1f,         0x1.8836fap-1f,  0x1.e11f64p-1f};
+__constant__ float c_sin20[18] = {
+    0.0f,            0x1.5e3a88p-2f,  0x1.491b76p-1f,  0x1.bb67aep-1f,  0x1.f838b8p-1f,
+    0x1.f838b8p-1f,  0x1.bb67aep-1f,  0x1.491b76p-1f,  0x1.5e3a88p-2f,  0.0f,
+    -0x1.5e3a88p-2f, -0x1.491b76p-1f, -0x1.bb67aep-1f, -0x1.f838b8p-1f, -0x1.f838b8p-1f,
+    -0x1.bb67aep-1f, -0x1.491b76p-1f, -0x1.5e3a88p-2f};
+
+// Per-row geometry, filled in shared memory by every block that needs it:
+// x = 85 + r cm; nPads = 66 + floor(72 r / 151); pad width w = 2 x tan10 / nPads.
+struct RowGeo {
+  float x[kNRow];
+  float w[kNRow];
+  float invw[kNRow];
+  float halfnp[kNRow];
+};
+
+__device__ __forceinline__ void fill_row_geo(RowGeo* g) {
+  for (int r = threadIdx.x; r < kNRow; r += blockDim.x) {
+    const int np = 66 + (72 * r) / 151;
+    const float x = 85.0f + (float)r;
+    const float w = fdiv(fmul(fmul(2.0f, x), kTan10), (float)np);
+    g->x[r] = x;
+    g->w[r] = w;
+    g->invw[r] = fdiv(1.0f, w);
+    g->halfnp[r] = fmul(0.5f, (float)np);
+  }
+}
+
+// Quantiser: clamp to [lo, hi] (NaN to lo), then floor(v + 0.5).
+__device__ __forceinline__ uint32_t quant(float v, float lo, float hi) {
+  v = (v >= lo) ? v : lo;
+  v = (v <= hi) ? v : hi;
+  return (uint32_t)floorf(fadd(v, 0.5f));
+}
+
+struct Track {
+  float x, y, ty, c;
+  float c00, c01, c02, c11, c12, c22;
+  float t, tt, d00, d01, d11;
+  int raw_row;  // row accumulator (mod 256); the model uses min(raw_row, 151)
+  int row;
+  int sec;
+};
+
+__device__ __forceinline__ float pad_to_y(const RowGeo* g, uint32_t padq, int r) {
+  return fmul(fsub(fmul((float)padq, 0.015625f), g->halfnp[r]), g->w[r]);
+}
+__device__ __forceinline__ float time_to_t(uint32_t timeq) {
+  return fmul((float)timeq, 0.03125f);
+}
+
+__device__ __forceinline__ void reset_ycov(Track& s) {
+  s.c00 = kSYR; s.c01 = 0.0f; s.c02 = 0.0f;
+  s.c11 = kCTY0; s.c12 = 0.0f; s.c22 = kCC0;
+}
+
+// Seed from the first cluster (stored absolute): the parabola through the
+// origin with curvature -kc * q/pT; zero time slope.
+__device__ __forceinline__ void seed(const RowGeo* g, Track& s, uint8_t qpta, int raw_row,
+                                     int sec, uint32_t padq, uint32_t timeq) {
+  const float qpt = fmul(fsub((float)qpta, 127.5f), 0.078125f);
+  s.raw_row = raw_row;
+  s.row = raw_row < kNRow ? raw_row : kNRow - 1;
+  s.sec = sec;
+  s.x = g->x[s.row];
+  s.y = pad_to_y(g, padq, s.row);
+  s.c = fmul(-kKC, qpt);
+  s.ty = fadd(fdiv(s.y, s.x), fmul(fmul(s.c, s.x), 0.5f));
+  s.c00 = kSY2; s.c01 = 0.0f; s.c02 = 0.0f;
+  s.c11 = kCTY0; s.c12 = 0.0f; s.c22 = kCC0;
+  s.t = time_to_t(timeq);
+  s.tt = 0.0f;
+  s.d00 = kST2; s.d01 = 0.0f; s.d11 = kCTT0;
+}
+
+// Leg change: x turns back; slope, curvature and time slope change sign.
+__device__ __forceinline__ void leg_change(Track& s) {
+  s.ty = -s.ty;
+  s.c = -s.c;
+  s.tt = -s.tt;
+  s.d01 = -s.d01;
+  reset_ycov(s);
+}
+
+// Sector change to nsec: rotate the parabola's point, slope and curvature by
+// k * 20 deg; a change of side (A/C) reverses the time slope.
+__device__ __forceinline__ void sector_change(Track& s, int nsec) {
+  const int k = ((nsec % 18) - (s.sec % 18) + 18) % 18;
+  const float ca = c_cos20[k], sa = c_sin20[k];
+  float a = fadd(ca, fmul(s.ty, sa));
+  const float b = fsub(fmul(s.ty, ca), sa);
+  if (!(a >= 1.0e-3f || a <= -1.0e-3f)) a = (a < 0.0f) ? -1.0e-3f : 1.0e-3f;
+  const float nx = fadd(fmul(s.x, ca), fmul(s.y, sa));
+  const float ny = fsub(fmul(s.y, ca), fmul(s.x, sa));
+  s.ty = fdiv(b, a);
+  s.c = fdiv(s.c, fmul(fmul(a, a), a));
+  s.x = nx;
+  s.y = ny;
+  if ((s.sec < 18) != (nsec < 18)) {
+    s.tt = -s.tt;
+    s.d01 = -s.d01;
+  }
+  s.sec = nsec;
+  reset_ycov(s);
+}
+
+// Key step of one cluster: row and sector/leg differences.  Returns kStRow if
+// the row left the detector.
+__device__ __forceinline__ uint32_t key_step(Track& s, uint32_t row_diff, uint32_t sld) {
+  const uint32_t leg = sld / kNSec;
+  const uint32_t sd = sld - leg * kNSec;
+  s.raw_row = (s.raw_row + (int)row_diff) & 255;
+  uint32_t st = 0;
+  s.row = s.raw_row;
+  if (s.row >= kNRow) { st = kStRow; s.row = kNRow - 1; }
+  if (leg != 0) leg_change(s);
+  if (sd != 0) {
+    int ns = s.sec + (int)sd;
+    ns = ns >= kNSec ? ns - kNSec : ns;
+    sector_change(s, ns);
+  }
+  return st;
+}
+
+// Propagate to the plane of the current row and return the quantised
+// prediction (pad code, time code).
+__device__ __forceinline__ void propagate_predict(const RowGeo* g, Track& s, uint32_t& ppad,
+                                                  uint32_t& ptime) {
+  const int r = s.row;
+  const float xr = g->x[r];
+  const float dx = fsub(xr, s.x);
+  const float adx = fabsf(dx);
+  const float h = fmul(fmul(0.5f, s.c), dx);
+  s.y = fadd(s.y, fmul(dx, fadd(s.ty, h)));
+  s.ty = fadd(s.ty, fmul(s.c, dx));
+  s.t = fadd(s.t, fmul(s.tt, dx));
+  s.x = xr;
+  const float h2 = fmul(fmul(0.5f, dx), dx);
+  const float a0 = fadd(fadd(s.c00, fmul(dx, s.c01)), fmul(h2, s.c02));
+  const float a1 = fadd(fadd(s.c01, fmul(dx, s.c11)), fmul(h2, s.c12));
+  const float a2 = fadd(fadd(s.c02, fmul(dx, s.c12)), fmul(h2, s.c22));
+  const float b1 = fadd(s.c11, fmul(dx, s.c12));
+  const float b2 = fadd(s.c12, fmul(dx, s.c22));
+  s.c00 = fadd(fadd(a0, fmul(dx, a1)), fmul(h2, a2));
+  s.c01 = fadd(a1, fmul(dx, a2));
+  s.c02 = a2;
+  s.c11 = fadd(fadd(b1, fmul(dx, b2)), fmul(kQTY, adx));
+  s.c12 = b2;
+  const float e0 = fadd(s.d00, fmul(dx, s.d01));
+  const float e1 = fadd(s.d01, fmul(dx, s.d11));
+  s.d00 = fadd(e0, fmul(dx, e1));
+  s.d01 = e1;
+  s.d11 = fadd(s.d11, fmul(kQTT, adx));
+  const float pp = fadd(fmul(s.y, g->invw[r]), g->halfnp[r]);
+  ppad = quant(fmul(pp, 64.0f), 0.0f, kPadHi);
+  ptime = quant(fmul(s.t, 32.0f), 0.0f, kTimeHi);
+}
+
+// Kalman update with the measured cluster.
+__device__ __forceinline__ void update(const RowGeo* g, Track& s, uint32_t padq, uint32_t timeq) {
+  const float ym = pad_to_y(g, padq, s.row);
+  const float tm = time_to_t(timeq);
+  const float inv = fdiv(1.0f, fadd(s.c00, kSY2));
+  const float k0 = fmul(s.c00, inv), k1 = fmul(s.c01, inv), k2 = fmul(s.c02, inv);
+  const float r = fsub(ym, s.y);
+  s.y = fadd(s.y, fmul(k0, r));
+  s.ty = fadd(s.ty, fmul(k1, r));
+  s.c = fadd(s.c, fmul(k2, r));
+  const float c00 = s.c00, c01 = s.c01, c02 = s.c02;
+  s.c00 = fsub(c00, fmul(k0, c00));
+  s.c01 = fsub(c01, fmul(k0, c01));
+  s.c02 = fsub(c02, fmul(k0, c02));
+  s.c11 = fsub(s.c11, fmul(k1, c01));
+  s.c12 = fsub(s.c12, fmul(k1, c02));
+  s.c22 = fsub(s.c22, fmul(k2, c02));
+  const float invt = fdiv(1.0f, fadd(s.d00, kST2));
+  const float g0 = fmul(s.d00, invt), g1 = fmul(s.d01, invt);
+  const float rt = fsub(tm, s.t);
+  s.t = fadd(s.t, fmul(g0, rt));
+  s.tt = fadd(s.tt, fmul(g1, rt));
+  const float d00 = s.d00, d01 = s.d01;
+  s.d00 = fsub(d00, fmul(g0, d00));
+  s.d01 = fsub(d01, fmul(g0, d01));
+  s.d11 = fsub(s.d11, fmul(g1, d01));
+}
+
+}  // namespace tmd

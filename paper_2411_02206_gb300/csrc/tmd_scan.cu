@@ -1,0 +1,209 @@
+// tmd_scan.cu -- track preparation and row offsets of the decoder.
+//
+// Track preparation (replaces the CPU-precomputed SoA indices of Sec. 3 of
+// arXiv:2411.02206 with device scans): trackStart = exclusive scan of the
+// track lengths, a bitmap of track starts, and a decode order with the longest
+// tracks first (bucketed by length), so that warps of the persistent decoder
+// take similar tracks and the tail is short.
+//
+// Row offsets: per (sector,row) bin the attached count (summed from the
+// per-tile histograms of k_count_rank) plus the unattached count, exclusive
+// scan -> rowStart; then per (tile, bin) the first native index of the tile's
+// clusters in that bin.
+#include "tmd_internal.cuh"
+
+namespace tmd {
+
+// Exclusive scan over a block of B threads: returns the exclusive prefix of v
+// and sets total to the block total (all threads).
+template <int B>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total) {
+  __shared__ uint32_t warp_tot[B / 32];
+  __shared__ uint32_t block_tot;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t t = lane < B / 32 ? warp_tot[lane] : 0u;
+    uint32_t s = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < B / 32) warp_tot[lane] = s - t;
+    if (lane == 31) block_tot = s;
+  }
+  __syncthreads();
+  const uint32_t r = warp_tot[w] + x - v;
+  total = block_tot;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames) {
+  for (uint32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < n_frames;
+       f += gridDim.x * blockDim.x)
+    *frames[f].status = 0u;
+}
+
+// Block totals of the track lengths, zero-length check, length histogram.
+__global__ void __launch_bounds__(256) k_track_scan1(const FrameDev* frames, PlanDev plan) {
+  __shared__ uint32_t hist[kLenBuckets];
+  uint32_t tot;
+  const uint32_t f = find_frame(plan.pre_tblk, plan.n_frames, blockIdx.x);
+  const FrameDev& F = frames[f];
+  const uint32_t lb = blockIdx.x - plan.pre_tblk[f];
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const uint32_t t0 = lb * kTrackBlk + threadIdx.x * 8;
+  uint32_t sum = 0;
+  bool zero = false;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const uint32_t t = t0 + k;
+    if (t < F.n_tracks) {
+      const uint32_t n = F.ncl[t];
+      sum += n;
+      zero |= (n == 0);
+      atomicAdd(&hist[n < kLenBuckets ? n : kLenBuckets - 1], 1u);
+    }
+  }
+  if (__syncthreads_or(zero) && threadIdx.x == 0) atomicOr(F.status, kStCount);
+  block_excl_scan<256>(sum, tot);
+  if (threadIdx.x == 0) F.blk_sum[lb] = tot;
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x)
+    if (hist[i]) atomicAdd(&F.len_cursor[i], hist[i]);
+}
+
+// Per frame: offsets of the track blocks, decode-order bucket offsets (longest
+// first), unattached bin starts, count checks.
+__global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, PlanDev plan) {
+  uint32_t tot;
+  const FrameDev& F = frames[blockIdx.x];
+  const uint32_t tid = threadIdx.x;
+  unsigned long long carry = 0;
+  for (uint32_t base = 0; base < F.n_tblocks; base += 1024) {
+    const uint32_t i = base + tid;
+    const uint32_t v = i < F.n_tblocks ? F.blk_sum[i] : 0u;
+    const uint32_t e = block_excl_scan<1024>(v, tot);
+    if (i < F.n_tblocks) F.blk_sum[i] = (uint32_t)carry + e;
+    carry += tot;
+  }
+  if (tid == 0 && carry != F.n_att) atomicOr(F.status, kStCount);
+  {
+    const uint32_t b = kLenBuckets - 1 - tid;  // descending length
+    const uint32_t v = F.len_cursor[b];
+    const uint32_t e = block_excl_scan<1024>(v, tot);
+    F.len_cursor[b] = e;
+  }
+  carry = 0;
+  for (uint32_t base = 0; base < (uint32_t)kNBin; base += 1024) {
+    const uint32_t i = base + tid;
+    const uint32_t v = i < (uint32_t)kNBin ? F.n_unatt_bin[i] : 0u;
+    const uint32_t e = block_excl_scan<1024>(v, tot);
+    if (i < (uint32_t)kNBin) F.unatt_start[i] = (uint32_t)carry + e;
+    carry += tot;
+  }
+  if (tid == 0) {
+    F.unatt_start[kNBin] = (uint32_t)carry;
+    if (carry != F.n_unatt) atomicOr(F.status, kStCount);
+  }
+}
+
+// trackStart, start bitmap and decode order.
+__global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, PlanDev plan) {
+  uint32_t tot;
+  const uint32_t f = find_frame(plan.pre_tblk, plan.n_frames, blockIdx.x);
+  const FrameDev& F = frames[f];
+  if (*F.status & kStCount) return;
+  const uint32_t lb = blockIdx.x - plan.pre_tblk[f];
+  const uint32_t t0 = lb * kTrackBlk + threadIdx.x * 8;
+  uint32_t n[8];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const uint32_t t = t0 + k;
+    n[k] = t < F.n_tracks ? (uint32_t)F.ncl[t] : 0u;
+    sum += n[k];
+  }
+  uint32_t start = F.blk_sum[lb] + block_excl_scan<256>(sum, tot);
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const uint32_t t = t0 + k;
+    if (t < F.n_tracks) {
+      F.track_start[t] = start;
+      atomicOr(&F.heads[start >> 5], 1u << (start & 31));
+      const uint32_t b = n[k] < kLenBuckets ? n[k] : kLenBuckets - 1;
+      F.order[atomicAdd(&F.len_cursor[b], 1u)] = t;
+      start += n[k];
+      if (t == F.n_tracks - 1) F.track_start[F.n_tracks] = start;
+    }
+  }
+}
+
+// Sum of the tile histograms over groups of kGroup tiles, per bin.
+__global__ void __launch_bounds__(kBinBlk) k_group_sum(const FrameDev* frames, PlanDev plan) {
+  const uint32_t f = find_frame(plan.pre_grp, plan.n_frames, blockIdx.x);
+  const FrameDev& F = frames[f];
+  if (*F.status & kStCount) return;
+  const uint32_t lb = blockIdx.x - plan.pre_grp[f];
+  const uint32_t g = lb / kBinBlocks;
+  const uint32_t b = (lb % kBinBlocks) * kBinBlk + threadIdx.x;
+  if (b >= (uint32_t)kNBin) return;
+  const uint32_t te = min((g + 1) * kGroup, F.n_tiles);
+  uint32_t s = 0;
+  for (uint32_t tile = g * kGroup; tile < te; tile++) s += F.tile_hist[(size_t)tile * kNBin + b];
+  F.group_sum[(size_t)g * kNBin + b] = s;
+}
+
+// Per frame: attached count per bin, group offsets, rowStart.
+__global__ void __launch_bounds__(1024) k_row_offsets(const FrameDev* frames, PlanDev plan) {
+  uint32_t tot;
+  const FrameDev& F = frames[blockIdx.x];
+  if (*F.status & kStCount) return;
+  for (uint32_t b = threadIdx.x; b < (uint32_t)kNBin; b += blockDim.x) {
+    uint32_t run = 0;
+    for (uint32_t g = 0; g < F.n_groups; g++) {
+      const uint32_t c = F.group_sum[(size_t)g * kNBin + b];
+      F.group_sum[(size_t)g * kNBin + b] = run;
+      run += c;
+    }
+    F.att_count[b] = run;
+  }
+  __syncthreads();
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < (uint32_t)kNBin; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < (uint32_t)kNBin ? F.att_count[i] + F.n_unatt_bin[i] : 0u;
+    const uint32_t e = block_excl_scan<1024>(v, tot);
+    if (i < (uint32_t)kNBin) F.row_start[i] = carry + e;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) F.row_start[kNBin] = carry;
+}
+
+// First native index of every (tile, bin).
+__global__ void __launch_bounds__(kBinBlk) k_tile_base(const FrameDev* frames, PlanDev plan) {
+  const uint32_t f = find_frame(plan.pre_grp, plan.n_frames, blockIdx.x);
+  const FrameDev& F = frames[f];
+  if (*F.status & kStCount) return;
+  const uint32_t lb = blockIdx.x - plan.pre_grp[f];
+  const uint32_t g = lb / kBinBlocks;
+  const uint32_t b = (lb % kBinBlocks) * kBinBlk + threadIdx.x;
+  if (b >= (uint32_t)kNBin) return;
+  const uint32_t te = min((g + 1) * kGroup, F.n_tiles);
+  uint32_t run = F.row_start[b] + F.group_sum[(size_t)g * kNBin + b];
+  for (uint32_t tile = g * kGroup; tile < te; tile++) {
+    F.tile_base[(size_t)tile * kNBin + b] = run;
+    run += F.tile_hist[(size_t)tile * kNBin + b];
+  }
+}
+
+}  // namespace tmd

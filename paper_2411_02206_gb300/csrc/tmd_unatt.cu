@@ -1,0 +1,201 @@
+// tmd_unatt.cu -- unattached-cluster decoding (arXiv:2411.02206, Sec. 3: each
+// coordinate is the stored difference plus the coordinate of the previously
+// decoded cluster of the same TPC region).
+//
+// The paper gives each GPU thread one region and walks it serially; here the
+// concatenated unattached stream of all (sector,row) bins is one segmented
+// inclusive scan (pad mod 2^16, time mod 2^32, restarting at every bin), cut
+// into chunks of kChunk clusters.  A persistent kernel takes chunks in ticket
+// order; each chunk scans in registers and shared memory and gets its carry
+// from the preceding chunks by decoupled look-back (a chunk that contains a
+// bin start stops the look-back).  Waits are bounded: a chunk that waits too
+// long sets TMD_STATUS_TIMEOUT and continues with a zero carry.
+#include "tmd_internal.cuh"
+
+namespace tmd {
+
+namespace {
+
+constexpr unsigned long long kLbAgg = 1ull;   // aggregate published
+constexpr unsigned long long kLbInc = 2ull;   // inclusive prefix published
+constexpr unsigned long long kLbHead = 4ull;  // the chunk contains a bin start
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned long long lb_pack(unsigned long long st, bool head,
+                                                      uint32_t pad, uint32_t time) {
+  return st | (head ? kLbHead : 0ull) | ((unsigned long long)(pad & 0xFFFFu) << 16) |
+         ((unsigned long long)time << 32);
+}
+
+// Segmented sum (flag = a segment starts inside the right operand).
+struct Seg {
+  uint32_t flag, pad, time;
+};
+__device__ __forceinline__ Seg seg_add(const Seg& a, const Seg& b) {
+  if (b.flag) return b;
+  return Seg{a.flag, (a.pad + b.pad) & 0xFFFFu, a.time + b.time};
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_unatt_decode(const FrameDev* frames, PlanDev plan,
+                                                      uint32_t n_tickets) {
+  __shared__ uint32_t s_ticket;
+  __shared__ Seg s_warp[8];
+  __shared__ Seg s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_ticket = atomicAdd(&plan.counters[1], 1u);
+    __syncthreads();
+    const uint32_t ticket = s_ticket;
+    __syncthreads();
+    if (ticket >= n_tickets) break;
+    const uint32_t f = find_frame(plan.pre_chunk, plan.n_frames, ticket);
+    const FrameDev& F = frames[f];
+    if (*F.status & kStCount) continue;
+    const uint32_t c = ticket - plan.pre_chunk[f];
+    const uint32_t n = F.n_unatt;
+    const uint32_t e0 = c * (uint32_t)kChunk + tid * 8u;
+    // load 8 consecutive clusters
+    uint32_t pd[8], td[8];
+    if (e0 + 8 <= n) {
+      const uint4 p = *reinterpret_cast<const uint4*>(F.pad_diff_u + e0);
+      const uint4 t0 = *reinterpret_cast<const uint4*>(F.time_diff_u + e0);
+      const uint4 t1 = *reinterpret_cast<const uint4*>(F.time_diff_u + e0 + 4);
+      pd[0] = p.x & 0xFFFFu; pd[1] = p.x >> 16; pd[2] = p.y & 0xFFFFu; pd[3] = p.y >> 16;
+      pd[4] = p.z & 0xFFFFu; pd[5] = p.z >> 16; pd[6] = p.w & 0xFFFFu; pd[7] = p.w >> 16;
+      td[0] = t0.x; td[1] = t0.y; td[2] = t0.z; td[3] = t0.w;
+      td[4] = t1.x; td[5] = t1.y; td[6] = t1.z; td[7] = t1.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const uint32_t e = e0 + k;
+        pd[k] = e < n ? F.pad_diff_u[e] : 0u;
+        td[k] = e < n ? F.time_diff_u[e] : 0u;
+      }
+    }
+    // bin of every cluster, bin starts are segment heads
+    uint32_t bin = 0;
+    if (e0 < n) {
+      uint32_t lo = 0, hi = kNBin;  // largest b with unatt_start[b] <= e0
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (F.unatt_start[mid] <= e0) lo = mid; else hi = mid;
+      }
+      bin = lo;
+    }
+    uint32_t bins[8];
+    uint32_t headmask = 0;
+    uint32_t next = e0 < n ? F.unatt_start[bin + 1] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t e = e0 + k;
+      if (e < n) {
+        while (e >= next) {
+          bin++;
+          next = F.unatt_start[bin + 1];
+        }
+        if (e == F.unatt_start[bin]) headmask |= 1u << k;
+      }
+      bins[k] = bin;
+    }
+    // thread-local inclusive scan
+    Seg loc[8];
+    Seg run{0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      run = seg_add(run, Seg{(headmask >> k) & 1u, pd[k], td[k]});
+      loc[k] = run;
+    }
+    // block exclusive scan of the thread aggregates
+    Seg x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      Seg y;
+      y.flag = __shfl_up_sync(0xffffffffu, x.flag, o);
+      y.pad = __shfl_up_sync(0xffffffffu, x.pad, o);
+      y.time = __shfl_up_sync(0xffffffffu, x.time, o);
+      if (lane >= o) x = seg_add(y, x);
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (tid == 0) {
+      Seg acc = s_warp[0];
+      for (int w = 1; w < 8; w++) {
+        const Seg v = s_warp[w];
+        s_warp[w] = acc;  // exclusive prefix of warp w (warp 0 handled below)
+        acc = seg_add(acc, v);
+      }
+      // acc = aggregate of the whole chunk.  Publish it, then look back for
+      // the carry of the clusters before the chunk's first bin start.
+      Seg carry{0u, 0u, 0u};
+      unsigned long long* lb = F.lookback;
+      const bool first_is_head = (headmask & 1u) != 0;
+      if (acc.flag || c == 0)
+        atomicExch(lb + c, lb_pack(kLbInc, acc.flag != 0, acc.pad, acc.time));
+      else
+        atomicExch(lb + c, lb_pack(kLbAgg, false, acc.pad, acc.time));
+      if (c > 0 && !first_is_head) {
+        uint32_t p = c - 1;
+        uint32_t spins = 0;
+        for (;;) {
+          const unsigned long long v = *(volatile unsigned long long*)(lb + p);
+          const unsigned long long st = v & 3ull;
+          if (st == 0) {
+            if (++spins > kSpinLimit) {
+              atomicOr(F.status, kStTimeout);
+              break;
+            }
+            __nanosleep(64);
+            continue;
+          }
+          carry = seg_add(Seg{0u, (uint32_t)(v >> 16) & 0xFFFFu, (uint32_t)(v >> 32)}, carry);
+          if (st == kLbInc || (v & kLbHead) || p == 0) break;
+          p--;
+        }
+        if (!acc.flag) {
+          const Seg inc = seg_add(carry, acc);
+          atomicExch(lb + c, lb_pack(kLbInc, false, inc.pad, inc.time));
+        }
+      }
+      s_carry = carry;
+    }
+    __syncthreads();
+    // exclusive prefix of this thread = carry (+) warp prefix (+) lane prefix
+    Seg ex{0u, 0u, 0u};
+    {
+      Seg lane_ex;
+      lane_ex.flag = __shfl_up_sync(0xffffffffu, x.flag, 1);
+      lane_ex.pad = __shfl_up_sync(0xffffffffu, x.pad, 1);
+      lane_ex.time = __shfl_up_sync(0xffffffffu, x.time, 1);
+      if (lane == 0) lane_ex = Seg{0u, 0u, 0u};
+      const Seg wex = wid == 0 ? Seg{0u, 0u, 0u} : s_warp[wid];
+      ex = seg_add(seg_add(s_carry, wex), lane_ex);
+    }
+    // write the records
+    const uint32_t n_total = F.n_att + F.n_unatt;
+    uint32_t st = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t e = e0 + k;
+      if (e < n) {
+        const Seg v = seg_add(ex, loc[k]);
+        const uint32_t b = bins[k];
+        const uint32_t pos = F.row_start[b] + F.att_count[b] + (e - F.unatt_start[b]);
+        if (v.time > 0xFFFFFFu) st |= kStTime;
+        if (pos >= n_total) {
+          st |= kStLimit;
+          continue;
+        }
+        uint32_t* dst = reinterpret_cast<uint32_t*>(F.native + (size_t)pos * kRecBytes);
+        dst[0] = (v.time & 0xFFFFFFu) | ((uint32_t)F.flags_u[e] << 24);
+        dst[1] = v.pad | ((uint32_t)F.sigt_u[e] << 16) | ((uint32_t)F.sigp_u[e] << 24);
+        dst[2] = (uint32_t)F.qmax_u[e] | ((uint32_t)F.qtot_u[e] << 16);
+      }
+    }
+    if (st) atomicOr(F.status, st);
+    __syncthreads();
+  }
+}
+
+}  // namespace tmd

@@ -1,0 +1,269 @@
+"""ctypes binding of libtmd.so (the C-ABI in include/tmd.h).
+
+The functions keep the C names (tmd_create, tmd_decode_frame, ...) and only
+marshal arguments: every step of decoding runs in the library's CUDA kernels.
+Loading fails loudly when libtmd.so is missing; there is no other decoder.
+
+Frames are dicts whose keys are the tmd_frame_in field names; values are
+torch tensors (device-resident for the device entry points, host for
+tmd_decode_frame_host) or anything with a data_ptr()/ctypes pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "libtmd.so")
+
+NSEC, NROW = 36, 152
+NBIN = NSEC * NROW
+REC_BYTES = 12
+
+TMD_OK, TMD_PENDING = 0, 1
+TMD_ERR_ARG, TMD_ERR_CORRUPT, TMD_ERR_BUDGET, TMD_ERR_TIMEOUT = -1, -2, -3, -4
+TMD_ERR_CUDA, TMD_ERR_NOMEM, TMD_ERR_STATE = -5, -6, -7
+STATUS_COUNT, STATUS_ROW, STATUS_TIME, STATUS_TIMEOUT, STATUS_LIMIT = 1, 2, 4, 8, 16
+
+# (field, element bytes, length kind) in tmd_frame_in order
+FRAME_FIELDS = [
+    ("qpt", 1, "track"), ("row", 1, "track"), ("slice", 1, "track"), ("pad", 2, "track"),
+    ("time", 4, "track"), ("ncl", 2, "track"),
+    ("qtot_a", 2, "att"), ("qmax_a", 2, "att"), ("flags_a", 1, "att"),
+    ("sigma_pad_a", 1, "att"), ("sigma_time_a", 1, "att"),
+    ("row_diff", 1, "diff"), ("slice_leg_diff", 1, "diff"), ("pad_res", 2, "diff"),
+    ("time_res", 4, "diff"),
+    ("n_unatt", 4, "bin"),
+    ("pad_diff_u", 2, "unatt"), ("time_diff_u", 4, "unatt"), ("qtot_u", 2, "unatt"),
+    ("qmax_u", 2, "unatt"), ("flags_u", 1, "unatt"), ("sigma_pad_u", 1, "unatt"),
+    ("sigma_time_u", 1, "unatt"),
+]
+TRUTH_FIELDS = ["qpt", "ncl", "row", "sector", "leg", "pad", "time"]
+TRACK_OUT_FIELDS = ["qpt", "row", "slice", "pad", "time", "ncl", "row_diff", "slice_leg_diff",
+                    "pad_res", "time_res", "status"]
+
+_P = ctypes.c_void_p
+
+
+class tmd_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64),
+                ("max_slots", ctypes.c_uint32), ("autotune_cache", ctypes.c_char_p),
+                ("flags", ctypes.c_uint32)]
+
+
+class tmd_frame_in(ctypes.Structure):
+    _fields_ = [("n_tracks", ctypes.c_uint32), ("n_attached", ctypes.c_uint32),
+                ("n_unattached", ctypes.c_uint32)] + [(n, _P) for n, _, _ in FRAME_FIELDS]
+
+
+class tmd_frame_out(ctypes.Structure):
+    _fields_ = [("native", _P), ("row_start", _P), ("att_count", _P), ("status", _P)]
+
+
+class tmd_truth_in(ctypes.Structure):
+    _fields_ = [("n_tracks", ctypes.c_uint32), ("n_attached", ctypes.c_uint32)] + [
+        (n, _P) for n in TRUTH_FIELDS]
+
+
+class tmd_track_out(ctypes.Structure):
+    _fields_ = [(n, _P) for n in TRACK_OUT_FIELDS]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libtmd.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(
+                    f"{LIB} is missing: build it with paper_2411_02206_gb300.build.build()")
+            L = ctypes.CDLL(LIB)
+            H = ctypes.c_void_p
+            for name, args in {
+                "tmd_create": [ctypes.POINTER(tmd_config), ctypes.POINTER(H)],
+                "tmd_destroy": [H],
+                "tmd_decode_frame": [H, ctypes.POINTER(tmd_frame_in),
+                                     ctypes.POINTER(tmd_frame_out), _P],
+                "tmd_decode_batch": [H, ctypes.c_uint32, ctypes.POINTER(tmd_frame_in),
+                                     ctypes.POINTER(tmd_frame_out), _P],
+                "tmd_decode_frame_host": [H, ctypes.POINTER(tmd_frame_in),
+                                          ctypes.POINTER(tmd_frame_out), _P],
+                "tmd_encode_tracks": [H, ctypes.POINTER(tmd_truth_in),
+                                      ctypes.POINTER(tmd_track_out), _P],
+                "tmd_submit": [H, ctypes.POINTER(tmd_frame_in), ctypes.POINTER(ctypes.c_uint64)],
+                "tmd_poll": [H, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(tmd_frame_out)],
+                "tmd_release": [H, ctypes.c_uint64],
+            }.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.tmd_profile_enable.argtypes = [H, ctypes.c_int]
+            L.tmd_profile_enable.restype = ctypes.c_int
+            L.tmd_profile_read.argtypes = [H, ctypes.c_uint32, ctypes.c_char_p,
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_uint32),
+                                           ctypes.POINTER(ctypes.c_uint32)]
+            L.tmd_profile_read.restype = ctypes.c_int
+            L.tmd_last_error_string.argtypes = [H]
+            L.tmd_last_error_string.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+class TmdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tmd error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr() if x.numel() else 0
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data if x.size else 0
+    return int(x)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def counts(frame: dict) -> tuple[int, int, int]:
+    """(n_tracks, n_attached, n_unattached) of a frame dict."""
+    def n(x):
+        return int(x.numel() if hasattr(x, "numel") else x.size)
+    return n(frame["ncl"]), n(frame["qtot_a"]), n(frame["qtot_u"])
+
+
+def frame_in(frame: dict) -> tmd_frame_in:
+    nt, na, nu = counts(frame)
+    return tmd_frame_in(nt, na, nu, *[_ptr(frame[n]) for n, _, _ in FRAME_FIELDS])
+
+
+def frame_out(native, row_start, att_count, status) -> tmd_frame_out:
+    return tmd_frame_out(_ptr(native), _ptr(row_start), _ptr(att_count), _ptr(status))
+
+
+class Decoder:
+    """Owns a tmd_handle; thin wrappers over the C entry points."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_slots: int = 0):
+        self._L = lib()
+        self.h = ctypes.c_void_p()
+        cfg = tmd_config(device, mem_budget_bytes, max_slots, None, 0)
+        rc = self._L.tmd_create(ctypes.byref(cfg), ctypes.byref(self.h))
+        if rc != TMD_OK:
+            raise TmdError(rc, "tmd_create failed")
+
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            msg = self._L.tmd_last_error_string(self.h)
+            raise TmdError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if self.h:
+            self._L.tmd_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tmd_decode_frame(self, fin: tmd_frame_in, fout: tmd_frame_out, stream=None) -> int:
+        return self._check(self._L.tmd_decode_frame(self.h, ctypes.byref(fin), ctypes.byref(fout),
+                                                    _P(_stream_ptr(stream))))
+
+    def tmd_decode_batch(self, fins, fouts, stream=None) -> int:
+        n = len(fins)
+        ins = (tmd_frame_in * n)(*fins)
+        outs = (tmd_frame_out * n)(*fouts)
+        return self._check(self._L.tmd_decode_batch(self.h, n, ins, outs, _P(_stream_ptr(stream))))
+
+    def tmd_decode_frame_host(self, fin: tmd_frame_in, fout: tmd_frame_out, stream=None) -> int:
+        return self._check(self._L.tmd_decode_frame_host(
+            self.h, ctypes.byref(fin), ctypes.byref(fout), _P(_stream_ptr(stream))))
+
+    def tmd_encode_tracks(self, tin: tmd_truth_in, tout: tmd_track_out, stream=None) -> int:
+        return self._check(self._L.tmd_encode_tracks(self.h, ctypes.byref(tin), ctypes.byref(tout),
+                                                     _P(_stream_ptr(stream))))
+
+    def tmd_submit(self, fin: tmd_frame_in) -> int:
+        rid = ctypes.c_uint64(0)
+        self._check(self._L.tmd_submit(self.h, ctypes.byref(fin), ctypes.byref(rid)))
+        return int(rid.value)
+
+    def tmd_poll(self, req_id: int, timeout_us: int):
+        out = tmd_frame_out()
+        rc = self._check(self._L.tmd_poll(self.h, req_id, timeout_us, ctypes.byref(out)))
+        return rc, out
+
+    def tmd_release(self, req_id: int) -> int:
+        return self._check(self._L.tmd_release(self.h, req_id))
+
+    def tmd_profile_enable(self, on: bool) -> int:
+        return self._check(self._L.tmd_profile_enable(self.h, 1 if on else 0))
+
+    def tmd_profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read."""
+        mx = 32
+        names = ctypes.create_string_buffer(32 * mx)
+        ms = (ctypes.c_double * mx)()
+        cnt = (ctypes.c_uint32 * mx)()
+        n = ctypes.c_uint32(0)
+        self._check(self._L.tmd_profile_read(self.h, mx, names, ms, cnt, ctypes.byref(n)))
+        out = {}
+        for i in range(n.value):
+            nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
+            out[nm] = (float(ms[i]), int(cnt[i]))
+        return out
+
+    # -- torch conveniences (allocation only) ------------------------------
+    def decode(self, frame: dict, stream=None):
+        """Decode a device-resident frame dict; returns (native uint8[N,12],
+        row_start int32[5473], att_count int32[5472], status int32[1])."""
+        import torch
+        nt, na, nu = counts(frame)
+        dev = frame["n_unatt"].device
+        native = torch.empty((na + nu, REC_BYTES), dtype=torch.uint8, device=dev)
+        row_start = torch.empty(NBIN + 1, dtype=torch.int32, device=dev)
+        att = torch.empty(NBIN, dtype=torch.int32, device=dev)
+        status = torch.empty(1, dtype=torch.int32, device=dev)
+        self.tmd_decode_frame(frame_in(frame), frame_out(native, row_start, att, status), stream)
+        return native, row_start, att, status
+
+    def encode(self, truth: dict, stream=None) -> dict:
+        """GPU track-model encoding of the attached truth (device tensors);
+        returns the compressed attached streams plus 'status'."""
+        import torch
+        nt = int(truth["ncl"].numel())
+        na = int(truth["row"].numel())
+        dev = truth["row"].device
+        out = {
+            "qpt": torch.empty(nt, dtype=torch.uint8, device=dev),
+            "row": torch.empty(nt, dtype=torch.uint8, device=dev),
+            "slice": torch.empty(nt, dtype=torch.uint8, device=dev),
+            "pad": torch.empty(nt, dtype=torch.int16, device=dev),
+            "time": torch.empty(nt, dtype=torch.int32, device=dev),
+            "ncl": torch.empty(nt, dtype=torch.int16, device=dev),
+            "row_diff": torch.empty(na - nt, dtype=torch.uint8, device=dev),
+            "slice_leg_diff": torch.empty(na - nt, dtype=torch.uint8, device=dev),
+            "pad_res": torch.empty(na - nt, dtype=torch.int16, device=dev),
+            "time_res": torch.empty(na - nt, dtype=torch.int32, device=dev),
+            "status": torch.empty(1, dtype=torch.int32, device=dev),
+        }
+        tin = tmd_truth_in(nt, na, *[_ptr(truth[n]) for n in TRUTH_FIELDS])
+        tout = tmd_track_out(*[_ptr(out[n]) for n in TRACK_OUT_FIELDS])
+        self.tmd_encode_tracks(tin, tout, stream)
+        return out

@@ -1,0 +1,174 @@
+"""CUDA path vs the CPU oracle, bit for bit (tolerance 0: every output is an
+integer or a byte), through the C-ABI."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_02206_gb300 import synth
+
+import gpu_helpers as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dec():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_02206_gb300 import build, tmd
+    build.build()
+    d = tmd.Decoder(0)
+    yield d
+    d.close()
+
+
+def _check_truth(dec, truth, what):
+    enc, _, gpu = G.gpu_encode_decode(dec, truth)
+    of = G.oracle_frame(truth)
+    assert enc["status"] == 0, what
+    for k in ("qpt", "row", "slice", "pad", "time", "ncl", "row_diff", "slice_leg_diff",
+              "pad_res", "time_res"):
+        assert np.array_equal(enc[k], of[k]), f"{what}: encoder field {k} differs"
+    G.assert_same_decode(gpu, O.decode(of), what)
+
+
+def test_smoke():
+    import __graft_entry__ as g
+    g.smoke()
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n_tracks=2000, n_unatt=100_000, seed=1, max_clusters=152),     # small frame shape
+    dict(n_tracks=3000, n_unatt=50_000, seed=5, looper_frac=0.5, max_legs=6, pt_mean=0.2),
+    dict(n_tracks=700, n_unatt=0, seed=6),                              # tracks only
+    dict(n_tracks=0, n_unatt=77_777, seed=7),                           # unattached only
+    dict(n_tracks=5000, n_unatt=3000, seed=8, min_clusters=1, secondary_frac=0.95),
+])
+def test_encode_decode_parity(dec, kw):
+    _check_truth(dec, synth.make_truth(**kw), str(kw))
+
+
+def test_stress_shape_scaled(dec):
+    _check_truth(dec, synth.shape_truth("stress", scale=0.03), "stress x0.03")
+
+
+def test_tile_boundaries(dec):
+    # attached counts exactly at, just below and just above a 32768-cluster tile
+    for target in (32768, 65535, 65537):
+        truth = synth.make_truth(n_tracks=800, n_unatt=4097, seed=target, min_clusters=20)
+        na = len(truth["row"])
+        # trim or pad with single-cluster tracks to hit the target exactly
+        ncl = truth["ncl"].astype(np.int64)
+        cut = np.searchsorted(np.cumsum(ncl), target, side="right")
+        keep = int(np.cumsum(ncl)[cut - 1]) if cut else 0
+        sub = {k: truth[k] for k in synth.UNATT}
+        for k in ("qpt", "ncl"):
+            sub[k] = truth[k][:cut]
+        for k in ("row", "sector", "leg", "pad", "time", "qtot_a", "qmax_a", "flags_a",
+                  "sigma_pad_a", "sigma_time_a"):
+            sub[k] = truth[k][:keep]
+        extra = target - keep
+        if extra > 0:
+            idx = np.arange(extra) % max(1, keep)
+            sub["qpt"] = np.concatenate([sub["qpt"], np.full(extra, 130, np.uint8)])
+            sub["ncl"] = np.concatenate([sub["ncl"], np.ones(extra, np.uint16)])
+            for k in ("row", "sector", "leg", "pad", "time", "qtot_a", "qmax_a", "flags_a",
+                      "sigma_pad_a", "sigma_time_a"):
+                add = truth[k][idx] if na else np.zeros(extra, truth[k].dtype)
+                if k == "leg":
+                    add = np.zeros(extra, np.uint8)
+                sub[k] = np.concatenate([sub[k], add])
+        assert len(sub["row"]) == target
+        _check_truth(dec, sub, f"tile boundary {target}")
+
+
+def test_hot_bin_spans_many_chunks(dec):
+    rng = np.random.default_rng(3)
+    truth = synth.make_truth(n_tracks=100, n_unatt=0, seed=9)
+    n_b = np.zeros(5472, np.int64)
+    n_b[[0, 17, 5471]] = [5, 50_000, 9_000]
+    n_b[rng.integers(0, 5472, 300)] += 1
+    nu = int(n_b.sum())
+    u = synth.make_unattached(rng, 0)
+    u["n_unatt"] = n_b.astype(np.uint32)
+    u["time_diff_u"] = rng.integers(0, 2 ** 32, nu, dtype=np.uint64).astype(np.uint32)
+    u["pad_diff_u"] = rng.integers(0, 2 ** 16, nu).astype(np.uint16)
+    for k, dt in (("qtot_u", np.uint16), ("qmax_u", np.uint16), ("flags_u", np.uint8),
+                  ("sigma_pad_u", np.uint8), ("sigma_time_u", np.uint8)):
+        u[k] = rng.integers(0, np.iinfo(dt).max + 1, nu).astype(dt)
+    truth.update(u)
+    of = G.oracle_frame(truth)
+    ora = O.decode(of)
+    assert ora[3] & O.ST_TIME  # random 32-bit differences overflow 24 bits
+    G.assert_same_decode(G.gpu_decode_np(dec, of), ora, "hot bin")
+
+
+def test_empty_frame(dec):
+    f = {n: np.zeros(5472 if k == "bin" else 0, dt) for n, dt, k in O.FRAME_FIELDS}
+    G.assert_same_decode(G.gpu_decode_np(dec, f), O.decode(f), "empty")
+
+
+def test_corrupt_frames_set_status(dec):
+    truth = synth.make_truth(n_tracks=200, n_unatt=5000, seed=12)
+    f = G.oracle_frame(truth)
+    cases = {}
+    g = dict(f); g["ncl"] = f["ncl"].copy(); g["ncl"][5] = 0; cases["ncl0"] = g
+    g = dict(f); g["n_unatt"] = f["n_unatt"].copy(); g["n_unatt"][100] += 3; cases["nunatt"] = g
+    g = dict(f); g["row_diff"] = f["row_diff"].copy(); g["row_diff"][40] = 180; cases["row"] = g
+    g = dict(f); g["slice"] = f["slice"].copy(); g["slice"][3] = 77; cases["slice"] = g
+    for name, g in cases.items():
+        gpu = G.gpu_decode_np(dec, g)
+        ora = O.decode(g)
+        assert ora[3] != 0, name
+        assert gpu[3] == ora[3], f"{name}: status gpu={gpu[3]} oracle={ora[3]}"
+
+
+def test_batch_equals_single(dec):
+    import torch
+    from paper_2411_02206_gb300 import frames, tmd
+    specs = synth.batch_specs(n_frames=5, seed=77, lo=2e4, hi=4e5)
+    npf = [G.oracle_frame(synth.make_truth(**s)) for s in specs]
+    devs = [frames.to_torch(f, "cuda:0") for f in npf]
+    outs, fins, fouts = [], [], []
+    for d in devs:
+        nt, na, nu = tmd.counts(d)
+        o = (torch.empty((na + nu, 12), dtype=torch.uint8, device="cuda:0"),
+             torch.empty(5473, dtype=torch.int32, device="cuda:0"),
+             torch.empty(5472, dtype=torch.int32, device="cuda:0"),
+             torch.empty(1, dtype=torch.int32, device="cuda:0"))
+        outs.append(o)
+        fins.append(tmd.frame_in(d))
+        fouts.append(tmd.frame_out(*o))
+    dec.tmd_decode_batch(fins, fouts)
+    torch.cuda.synchronize()
+    for i, (d, o) in enumerate(zip(devs, outs)):
+        single = dec.decode(d)
+        torch.cuda.synchronize()
+        assert torch.equal(o[0], single[0]) and torch.equal(o[1], single[1])
+        assert int(o[3].item()) == int(single[3].item()) == 0
+        G.assert_same_decode((o[0].cpu().numpy(), frames.to_numpy(o[1], np.uint32),
+                              frames.to_numpy(o[2], np.uint32), int(o[3].item())),
+                             O.decode(npf[i]), f"batch frame {i}")
+
+
+def test_host_entry_point(dec):
+    from paper_2411_02206_gb300 import frames, tmd
+    truth = synth.make_truth(n_tracks=1500, n_unatt=40_000, seed=21)
+    of = G.oracle_frame(truth)
+    host = frames.to_torch(of, None, pin=True)
+    nt, na, nu = tmd.counts(host)
+    native = np.zeros((na + nu, 12), np.uint8)
+    rs = np.zeros(5473, np.uint32)
+    att = np.zeros(5472, np.uint32)
+    st = np.zeros(1, np.uint32)
+    dec.tmd_decode_frame_host(tmd.frame_in(host), tmd.frame_out(native, rs, att, st))
+    G.assert_same_decode((native, rs, att, int(st[0])), O.decode(of), "host entry")
+
+
+@pytest.mark.slow
+def test_full_size_pbpb_frame(dec):
+    """The full Pb-Pb-shaped frame (400 k tracks, ~37 M attached, 20 M
+    unattached): GPU encoder and decoder against the oracle on every field."""
+    truth = synth.shape_truth("pbpb")
+    _check_truth(dec, truth, "pbpb full size")
