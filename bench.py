@@ -44,9 +44,11 @@ def _peaks():
 
 
 def _config(n_tracks, n_att, n_unatt, seed, note):
-    return {"workload": f"{WORKLOAD}: full Pb-Pb-shaped time frame, {n_tracks} tracks, "
-                        f"{n_att} attached + {n_unatt} unattached clusters, seed {seed}",
-            "frame_clusters": n_att + n_unatt, "n_tracks": n_tracks, "l2": note}
+    att = f"{n_att} attached" if n_att is not None else "about 37 M attached"
+    return {"workload": f"{WORKLOAD}: full Pb-Pb-shaped time frame, {n_tracks} tracks of 20-152 "
+                        f"clusters, {att} + {n_unatt} unattached clusters, seed {seed}",
+            "frame_clusters": (n_att + n_unatt) if n_att is not None else None,
+            "n_tracks": n_tracks, "l2": note}
 
 
 def _dist():
@@ -106,10 +108,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(seed_offset: int = 0):
+def make_inputs(seed_offset: int = 0, scale: float = 1.0):
     from paper_2411_02206_gb300 import synth
     kw = dict(synth.SHAPES[WORKLOAD])
     kw["seed"] = kw["seed"] + seed_offset
+    kw["n_tracks"] = int(round(kw["n_tracks"] * scale))
+    kw["n_unatt"] = int(round(kw["n_unatt"] * scale))
     return synth.make_truth(**kw), kw["seed"]
 
 
@@ -153,16 +157,24 @@ def decode_kernel_bytes(nt, na):
 
 
 def run_reference(args):
+    """The reference arm: the serial CPU oracle decoding the same Pb-Pb-shaped
+    workload on this host's cores.  Each step decodes a bounded sample of the
+    frame (same generator and distributions, fewer tracks and unattached
+    clusters) sized so that the whole run takes about a minute."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
     from oracle import oracle as O
     from paper_2411_02206_gb300 import synth
     O.build()
-    scale = 0.1
-    kw = dict(synth.SHAPES[WORKLOAD])
-    kw["n_tracks"] = int(kw["n_tracks"] * scale)
-    kw["n_unatt"] = int(kw["n_unatt"] * scale)
+    full = synth.SHAPES[WORKLOAD]
+    full_clusters = 57e6            # attached + unattached of the full frame
+    oracle_rate = 2.0e7             # clusters/s of the oracle, order of magnitude
+    per_step = 60.0 * oracle_rate / max(1, args.steps + args.warmup)
+    scale = min(1.0, max(0.002, per_step / full_clusters))
+    kw = dict(full)
+    kw["n_tracks"] = max(1, int(full["n_tracks"] * scale))
+    kw["n_unatt"] = int(full["n_unatt"] * scale)
     truth = synth.make_truth(**kw)
     f = oracle_frame(truth)
     nt, na, nu = O.frame_counts(f)
@@ -173,13 +185,14 @@ def run_reference(args):
         O.decode(f)
     dt = time.perf_counter() - t0
     value = args.steps * (na + nu) / dt
-    sample = (f"{WORKLOAD} shape at 10 % scale ({nt} tracks, {na + nu} clusters) per step, "
-              f"serial C oracle")
+    sample = (f"each step: the {WORKLOAD} workload at {scale:.3f} scale ({nt} tracks, "
+              f"{na + nu} clusters, same generator), serial C oracle, 1 thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": _config(nt, na, nu, kw["seed"], "CPU only"),
+            "config": _config(full["n_tracks"], None, full["n_unatt"], full["seed"],
+                              "CPU only; per-step sample described in cpu_baseline"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -198,7 +211,7 @@ def run(args):
     from paper_2411_02206_gb300 import build, frames, tmd
     build.build()
     dec = tmd.Decoder(local)
-    truth, seed = make_inputs(seed_offset=rank)
+    truth, seed = make_inputs(seed_offset=rank, scale=args.scale)
     dev_truth = frames.to_torch(truth, f"cuda:{local}")
     enc = dec.encode(dev_truth)
     frame = frames.assemble(dev_truth, enc)
@@ -328,6 +341,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="tmd", choices=["tmd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload (profiling runs only; the bench line uses 1.0)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -173,6 +173,20 @@ int tmd_decode_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out*
 int tmd_decode_batch(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
                      const tmd_frame_out* out, void* stream);
 
+/* Batched, graph-captured decoding (the multi-frame schedule).  A batch is
+ * planned once for n frames: it owns scratch memory and a launch record
+ * sized for them, and the whole decode chain over all n frames (each kernel
+ * spanning the work items of every frame) is captured in one CUDA graph.
+ * tmd_batch_launch replays it with a single graph launch on `stream`.  The
+ * frames' input and output buffers must keep their addresses (and the
+ * counts their values) for the life of the batch; their contents may change
+ * between launches.  Results equal those of n tmd_decode_frame calls. */
+typedef struct tmd_batch tmd_batch;
+int tmd_batch_create(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
+                     const tmd_frame_out* out, tmd_batch** out_batch);
+int tmd_batch_launch(tmd_batch* b, void* stream);
+int tmd_batch_destroy(tmd_batch* b);
+
 /* Decode one frame given HOST buffers: the inputs are copied to handle-owned
  * device memory, decoded, and native / row_start / att_count / status copied
  * back to the host buffers in `out`.  Synchronous on return.  Pinned host

@@ -317,12 +317,11 @@ static RecordLayout record_layout(uint32_t n, bool enc) {
   return r;
 }
 
-int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
-               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st) {
+// Scratch and record sizes of a call (nf decode frames, or one encode frame).
+static void plan_all(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin,
+                     std::vector<FrameLayout>& L, size_t& zbytes, size_t& pbytes) {
   const bool encode = tin != nullptr;
-  CK(cudaSetDevice(h->device));
-  // plan every frame
-  std::vector<FrameLayout> L(nf);
+  L.resize(nf);
   size_t zoff = 256 + align_up((size_t)kNBin * 4, 256);  // counters + zero bins
   size_t poff = 0;
   for (uint32_t f = 0; f < nf; f++) {
@@ -331,17 +330,48 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
     const uint32_t nu = encode ? 0u : in[f].n_unattached;
     plan_frame(nt, na, nu, zoff, poff, L[f]);
   }
-  const size_t zbytes = align_up(zoff, 256);
-  int rc = h->ensure_scratch(zbytes + poff);
+  zbytes = align_up(zoff, 256);
+  pbytes = align_up(poff, 256);
+}
+
+void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin,
+                    size_t* scratch_bytes, size_t* record_bytes) {
+  std::vector<FrameLayout> L;
+  size_t zb = 0, pb = 0;
+  plan_all(nf, in, tin, L, zb, pb);
+  *scratch_bytes = zb + pb;
+  *record_bytes = record_layout(nf, tin != nullptr).bytes;
+}
+
+int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
+               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st) {
+  CK(cudaSetDevice(h->device));
+  size_t scratch_bytes = 0, record_bytes = 0;
+  tmd_call_sizes(nf, in, tin, &scratch_bytes, &record_bytes);
+  int rc = h->ensure_scratch(scratch_bytes);
   if (rc != TMD_OK) return rc;
-  char* zb = static_cast<char*>(h->scratch);
+  int slot = 0;
+  if ((rc = h->acquire_slot(record_bytes, slot)) != TMD_OK) return rc;
+  tmd_handle::Slot& S = h->slots[slot];
+  rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st);
+  if (rc != TMD_OK) return rc;
+  CK(cudaEventRecord(S.done, st));
+  S.used = true;
+  return TMD_OK;
+}
+
+int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
+                const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
+                void* host_record, void* dev_record, cudaStream_t st) {
+  const bool encode = tin != nullptr;
+  std::vector<FrameLayout> L;
+  size_t zbytes = 0, pbytes = 0;
+  plan_all(nf, in, tin, L, zbytes, pbytes);
+  char* zb = static_cast<char*>(scratch);
   char* pb = zb + zbytes;
   const RecordLayout R = record_layout(nf, encode);
-  int slot = 0;
-  if ((rc = h->acquire_slot(R.bytes, slot)) != TMD_OK) return rc;
-  tmd_handle::Slot& S = h->slots[slot];
-  char* host = static_cast<char*>(S.host);
-  char* dev = static_cast<char*>(S.dev);
+  char* host = static_cast<char*>(host_record);
+  char* dev = static_cast<char*>(dev_record);
   uint32_t* pre = reinterpret_cast<uint32_t*>(host + R.pre);
   uint32_t* pre_tblk = pre;
   uint32_t* pre_tile = pre + (nf + 1);
@@ -459,8 +489,6 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
     }
   }
   CK(cudaGetLastError());
-  CK(cudaEventRecord(S.done, st));
-  S.used = true;
   return TMD_OK;
 }
 

@@ -68,4 +68,13 @@ int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_ou
 // frame (tin/tout), on stream st, using the handle's scratch.
 int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st);
+// Bytes of scratch and of launch record that a call needs.
+void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin,
+                    size_t* scratch_bytes, size_t* record_bytes);
+// Fill the launch record (host_record, pinned) for the given scratch and enqueue
+// the record upload and the kernel chain on st.  The caller keeps scratch and
+// both record buffers alive until the stream has passed the chain.
+int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
+                const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
+                void* host_record, void* dev_record, cudaStream_t st);
 void tmd_serve_shutdown(tmd_handle* h);

@@ -102,6 +102,14 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
+            L.tmd_batch_create.argtypes = [H, ctypes.c_uint32, ctypes.POINTER(tmd_frame_in),
+                                           ctypes.POINTER(tmd_frame_out),
+                                           ctypes.POINTER(ctypes.c_void_p)]
+            L.tmd_batch_create.restype = ctypes.c_int
+            L.tmd_batch_launch.argtypes = [ctypes.c_void_p, _P]
+            L.tmd_batch_launch.restype = ctypes.c_int
+            L.tmd_batch_destroy.argtypes = [ctypes.c_void_p]
+            L.tmd_batch_destroy.restype = ctypes.c_int
             L.tmd_profile_enable.argtypes = [H, ctypes.c_int]
             L.tmd_profile_enable.restype = ctypes.c_int
             L.tmd_profile_read.argtypes = [H, ctypes.c_uint32, ctypes.c_char_p,
@@ -211,6 +219,22 @@ class Decoder:
 
     def tmd_release(self, req_id: int) -> int:
         return self._check(self._L.tmd_release(self.h, req_id))
+
+    def tmd_batch_create(self, fins, fouts):
+        """Plan and capture a batch; returns an opaque batch pointer.  Keep
+        fins/fouts' buffers alive and in place while the batch exists."""
+        n = len(fins)
+        ins = (tmd_frame_in * n)(*fins)
+        outs = (tmd_frame_out * n)(*fouts)
+        b = ctypes.c_void_p()
+        self._check(self._L.tmd_batch_create(self.h, n, ins, outs, ctypes.byref(b)))
+        return b
+
+    def tmd_batch_launch(self, batch, stream=None) -> int:
+        return self._check(self._L.tmd_batch_launch(batch, _P(_stream_ptr(stream))))
+
+    def tmd_batch_destroy(self, batch) -> int:
+        return self._check(self._L.tmd_batch_destroy(batch))
 
     def tmd_profile_enable(self, on: bool) -> int:
         return self._check(self._L.tmd_profile_enable(self.h, 1 if on else 0))
