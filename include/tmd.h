@@ -194,6 +194,26 @@ int tmd_batch_destroy(tmd_batch* b);
 int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out,
                           void* stream);
 
+/* Decode one frame without allocating anything (the paper has no
+ * counterpart; this is an integration aid).  For callers that cannot
+ * allocate device memory while they run -- code inside a memory pool it
+ * does not own, or a process whose allocator must not be touched after
+ * start-up -- this entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its working memory is one fixed array compiled into
+ * the library (4 KiB of launch record + 64 MiB of scratch), which every GPU
+ * that loads the library holds until the process exits.  Inputs and outputs
+ * are the caller's device buffers, as for tmd_decode_frame; the results are
+ * identical.  Frames that need more than 64 MiB of scratch (roughly more
+ * than 19 million attached clusters) are rejected with TMD_ERR_ARG and a
+ * message in err.  Runs on the current device and `stream`; the first call
+ * on a device looks up the array's device address (once per device), so
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  err (err_len bytes,
+ * may be NULL) receives a description of a failure. */
+int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_out* out, void* stream,
+                             char* err, size_t err_len);
+
 /* Track-model encoding of the attached clusters (the synchronous side of
  * Sec. 3), device buffers, asynchronous on `stream`. */
 int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,

@@ -91,16 +91,8 @@ int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_ou
   return TMD_OK;
 }
 
-// Scratch layout of one frame.  The zeroed part of all frames is contiguous.
-struct FrameLayout {
-  uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
-  size_t z_heads, z_len, z_lb;                    // offsets in the zeroed part
-  size_t track_start, order, rank, tile_hist, group_sum, tile_base, unatt_start, blk_sum,
-      att_count;                                  // offsets in the plain part
-};
-
-static void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
-                       FrameLayout& L) {
+void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
+                FrameLayout& L) {
   L.n_tblocks = ceil_div(nt, kTrackBlk);
   L.n_tiles = ceil_div(na, kTile);
   L.n_groups = ceil_div(L.n_tiles, kGroup);

@@ -68,6 +68,17 @@ int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_ou
 // frame (tin/tout), on stream st, using the handle's scratch.
 int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st);
+// Scratch layout of one frame.  The zeroed part of all frames is contiguous.
+struct FrameLayout {
+  uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
+  size_t z_heads, z_len, z_lb;                    // offsets in the zeroed part
+  size_t track_start, order, rank, tile_hist, group_sum, tile_base, unatt_start, blk_sum,
+      att_count;                                  // offsets in the plain part
+};
+// Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts.
+void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
+                FrameLayout& L);
+
 // Bytes of scratch and of launch record that a call needs.
 void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin,
                     size_t* scratch_bytes, size_t* record_bytes);

@@ -110,6 +110,10 @@ def lib():
             L.tmd_batch_launch.restype = ctypes.c_int
             L.tmd_batch_destroy.argtypes = [ctypes.c_void_p]
             L.tmd_batch_destroy.restype = ctypes.c_int
+            L.tmd_decode_frame_noalloc.argtypes = [ctypes.POINTER(tmd_frame_in),
+                                                   ctypes.POINTER(tmd_frame_out), _P,
+                                                   ctypes.c_char_p, ctypes.c_size_t]
+            L.tmd_decode_frame_noalloc.restype = ctypes.c_int
             L.tmd_profile_enable.argtypes = [H, ctypes.c_int]
             L.tmd_profile_enable.restype = ctypes.c_int
             L.tmd_profile_read.argtypes = [H, ctypes.c_uint32, ctypes.c_char_p,
@@ -121,6 +125,15 @@ def lib():
             L.tmd_last_error_string.restype = ctypes.c_char_p
             _lib = L
     return _lib
+
+
+def tmd_decode_frame_noalloc(fin: tmd_frame_in, fout: tmd_frame_out, stream=None):
+    """The allocation-free entry point on the current device; returns
+    (return code, error message)."""
+    err = ctypes.create_string_buffer(512)
+    rc = lib().tmd_decode_frame_noalloc(ctypes.byref(fin), ctypes.byref(fout),
+                                        _P(_stream_ptr(stream)), err, len(err))
+    return rc, err.value.decode()
 
 
 class TmdError(RuntimeError):
