@@ -225,6 +225,10 @@ def run(args):
     fout = tmd.frame_out(native, row_start, att, status)
     torch.cuda.synchronize()
     assert int(enc["status"].item()) == 0, "encoder status"
+    if not args.no_autotune:
+        dec.tmd_autotune([fin], [fout], stream)
+    tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "decode_blocks_per_sm",
+                                              "unatt_blocks_per_sm")}
     for _ in range(args.warmup):
         dec.tmd_decode_frame(fin, fout, stream)
     torch.cuda.synchronize()
@@ -319,6 +323,7 @@ def run(args):
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "share": v[0] / max(1e-9, sum(
                 x[0] for x in prof.values())), "launches": v[1]} for k, v in prof.items()},
             "top_kernel": top[0],
+            "tuning": tuned,
             "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -334,13 +339,193 @@ def run(args):
     return 0
 
 
+def _gen(kw):
+    from paper_2411_02206_gb300 import synth
+    return synth.make_truth(**kw)
+
+
+def _make_frames(dec, specs, device):
+    """Generate truths in a spawn-started process pool, encode them on the GPU."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_2411_02206_gb300 import frames
+    workers = max(1, min(len(specs), (os.cpu_count() or 4) - 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        truths = list(ex.map(_gen, specs))
+    out = []
+    for tr in truths:
+        dev = frames.to_torch(tr, device)
+        enc = dec.encode(dev)
+        out.append(frames.assemble(dev, enc))
+    return out
+
+
+def _alloc_out(tmd, torch, frame, device):
+    nt, na, nu = tmd.counts(frame)
+    return (torch.empty((na + nu, 12), dtype=torch.uint8, device=device),
+            torch.empty(5473, dtype=torch.int32, device=device),
+            torch.empty(5472, dtype=torch.int32, device=device),
+            torch.empty(1, dtype=torch.int32, device=device))
+
+
+def run_batch(args):
+    """64 frames of log-uniform size (0.5-40 M clusters, pp-like to Pb-Pb-like
+    mixes): 64 plain tmd_decode_frame calls vs one tmd_decode_batch call vs
+    one graph launch of a planned batch, on the same resident frames."""
+    import torch
+    from paper_2411_02206_gb300 import build, synth, tmd
+    build.build()
+    dev = "cuda:0"
+    dec = tmd.Decoder(0)
+    specs = synth.batch_specs(n_frames=args.frames)
+    frs = _make_frames(dec, specs, dev)
+    outs = [_alloc_out(tmd, torch, f, dev) for f in frs]
+    fins = [tmd.frame_in(f) for f in frs]
+    fouts = [tmd.frame_out(*o) for o in outs]
+    total = sum(sum(tmd.counts(f)[1:]) for f in frs)
+    stream = torch.cuda.current_stream()
+    if not args.no_autotune:
+        dec.tmd_autotune(fins[:8], fouts[:8], stream)
+
+    def timeit(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_plain = timeit(lambda: [dec.tmd_decode_frame(fi, fo, stream) for fi, fo in zip(fins, fouts)],
+                     args.steps)
+    ref = [o[0].clone() for o in outs]
+    t_batch = timeit(lambda: dec.tmd_decode_batch(fins, fouts, stream), args.steps)
+    same_b = all(torch.equal(r, o[0]) for r, o in zip(ref, outs))
+    bh = dec.tmd_batch_create(fins, fouts)
+    t_graph = timeit(lambda: dec.tmd_batch_launch(bh, stream), args.steps)
+    same_g = all(torch.equal(r, o[0]) for r, o in zip(ref, outs))
+    dec.tmd_batch_destroy(bh)
+    ok = all(int(o[3].item()) == 0 for o in outs)
+    line = {"workload": f"batch of {len(frs)} frames, {total} clusters "
+                        "(log-uniform 0.5-40 M per frame, seeds 1000+i)",
+            "metric": METRIC, "unit": UNIT, "steps": args.steps,
+            "plain_launches": {"value": total / (t_plain * 1e-3), "ms": t_plain},
+            "batched_chain": {"value": total / (t_batch * 1e-3), "ms": t_batch},
+            "graph_launch": {"value": total / (t_graph * 1e-3), "ms": t_graph},
+            "identical_to_plain": bool(same_b and same_g), "status_ok": ok}
+    print(json.dumps(line), flush=True)
+    dec.close()
+    return 0
+
+
+def run_serve(args):
+    """Poisson stream of requests (frames drawn with replacement from a pool
+    of seeded frames, log-uniform 1e5-5e7 clusters) at a rate of 80 % of the
+    measured batched capacity; p50/p99 latency from submit to observed
+    completion, and sustained clusters/s."""
+    import random
+    import threading
+    import torch
+    from paper_2411_02206_gb300 import build, synth, tmd
+    build.build()
+    dev = "cuda:0"
+    dec = tmd.Decoder(0)
+    specs = synth.batch_specs(n_frames=args.frames, seed=5000, lo=1e5, hi=5e7)
+    frs = _make_frames(dec, specs, dev)
+    sizes = [sum(tmd.counts(f)[1:]) for f in frs]
+    outs = [_alloc_out(tmd, torch, f, dev) for f in frs]
+    fins = [tmd.frame_in(f) for f in frs]
+    fouts = [tmd.frame_out(*o) for o in outs]
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        dec.tmd_decode_batch(fins, fouts, stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        dec.tmd_decode_batch(fins, fouts, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    capacity = 3 * sum(sizes) / (a.elapsed_time(b) * 1e-3)   # clusters/s
+    srv = tmd.Decoder(0, mem_budget_bytes=120 << 30, max_slots=256)
+    rng = random.Random(7)
+    n_req = args.requests
+    picks = [rng.randrange(len(frs)) for _ in range(n_req)]
+    mean = sum(sizes[i] for i in picks) / n_req
+    rate = 0.8 * capacity / mean                               # requests/s
+    submitted = {}
+    lat = []
+    done_clusters = 0
+    lock = threading.Lock()
+    finished = threading.Event()
+
+    def poller():
+        nonlocal done_clusters
+        pending = []
+        while len(lat) < n_req:
+            with lock:
+                for k in sorted(submitted):
+                    pending.append(submitted.pop(k))
+            if not pending:
+                time.sleep(0.0002)
+                continue
+            rid, t0, sz = pending[0]
+            rc, _ = srv.tmd_poll(rid, 2000)  # blocks in C (GIL released)
+            if rc == tmd.TMD_OK:
+                lat.append(time.perf_counter() - t0)
+                done_clusters += sz
+                srv.tmd_release(rid)
+                pending.pop(0)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t_start = time.perf_counter()
+    t_next = t_start
+    for i, k in enumerate(picks):
+        t_next += rng.expovariate(rate)
+        while True:
+            gap = t_next - time.perf_counter()
+            if gap <= 0:
+                break
+            time.sleep(gap if gap > 0.0005 else 0)
+        t0 = time.perf_counter()
+        rid = srv.tmd_submit(fins[k])
+        with lock:
+            submitted[i] = (rid, t0, sizes[k])
+    finished.set()
+    th.join()
+    wall = time.perf_counter() - t_start
+    lat.sort()
+    line = {"workload": f"serving: Poisson stream of {n_req} frames drawn from {len(frs)} "
+                        "seeded frames (log-uniform 1e5-5e7 clusters), budget 120 GB",
+            "metric": METRIC, "unit": UNIT, "offered_rate_req_s": rate,
+            "batched_capacity": capacity,
+            "sustained": done_clusters / wall,
+            "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[int(len(lat) * 0.99) - 1],
+            "mean_frame_clusters": mean}
+    print(json.dumps(line), flush=True)
+    srv.close()
+    dec.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="tmd", choices=["tmd", "reference"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batch", "serve"],
+                    help="frame: the bench line; batch / serve: extra measurements")
+    ap.add_argument("--frames", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling runs only; the bench line uses 1.0)")
     args = ap.parse_args()
@@ -348,6 +533,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run(args)
 
 

@@ -204,7 +204,7 @@ int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in, const tmd_frame
  * that loads the library holds until the process exits.  Inputs and outputs
  * are the caller's device buffers, as for tmd_decode_frame; the results are
  * identical.  Frames that need more than 64 MiB of scratch (roughly more
- * than 19 million attached clusters) are rejected with TMD_ERR_ARG and a
+ * than 12 million attached clusters) are rejected with TMD_ERR_ARG and a
  * message in err.  Runs on the current device and `stream`; the first call
  * on a device looks up the array's device address (once per device), so
  * make that first call before any stream capture.  All calls share the
@@ -219,10 +219,16 @@ int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_out* out, v
 int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,
                       void* stream);
 
-/* Serving.  tmd_submit copies the frame (device pointers) into memory the
- * handle owns and queues it; frames are admitted while the memory budget and
- * the slot table allow and are decoded in batches as they arrive.
- * TMD_ERR_BUDGET if the frame can never fit the budget. */
+/* Serving.  tmd_submit queues a frame and returns at once.  A driver thread
+ * admits queued frames in arrival order while the device-memory budget
+ * (tmd_config.mem_budget_bytes) and the slot table (tmd_config.max_slots)
+ * allow, gives each admitted frame output buffers the handle owns -- and,
+ * when the frame is in host memory, copies its streams into device buffers
+ * the handle owns (device-resident frames are decoded in place) -- and
+ * decodes the frames whose inputs are ready together in one batch, while the
+ * previous batch may still run (continuous batching).  Keep the caller's
+ * input buffers unchanged until tmd_poll reports the request done.
+ * TMD_ERR_BUDGET if the frame alone exceeds the budget. */
 int tmd_submit(tmd_handle* h, const tmd_frame_in* in, uint64_t* req_id);
 
 /* Wait up to timeout_us for request req_id.  TMD_OK: *out receives device
@@ -231,6 +237,20 @@ int tmd_poll(tmd_handle* h, uint64_t req_id, uint32_t timeout_us, tmd_frame_out*
 
 /* Free the buffers of a finished request. */
 int tmd_release(tmd_handle* h, uint64_t req_id);
+
+/* Tuning.  Parameters change launch shapes only, never results:
+ *   "decode_variant"      0..3  register budget of the track decoder
+ *                               (at least 4, 5, 6, 8 resident blocks per SM)
+ *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
+ *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
+ * tmd_autotune times the decode chain on the given frames (device buffers,
+ * decoded several times) for each candidate setting, keeps the fastest, and
+ * writes it to the handle's autotune cache if tmd_config.autotune_cache was
+ * set (tmd_create reads that file back for the same GPU model). */
+int tmd_tune_set(tmd_handle* h, const char* key, int value);
+int tmd_tune_get(tmd_handle* h, const char* key, int* value);
+int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in, const tmd_frame_out* out,
+                 void* stream);
 
 /* Instrumentation.  While enabled, every kernel the handle launches is
  * bracketed by CUDA events on its stream.  tmd_profile_read waits for the

@@ -184,8 +184,9 @@ static void o_sector_change(const OModel* m, OState* s, int nsec) {
   if (!(a >= 1.0e-3f || a <= -1.0e-3f)) a = (a < 0.0f) ? -1.0e-3f : 1.0e-3f;
   float nx = s->x * ca + s->y * sa;
   float ny = s->y * ca - s->x * sa;
-  s->ty = b / a;
-  s->c = s->c / ((a * a) * a);
+  float ia = 1.0f / a;
+  s->ty = b * ia;
+  s->c = s->c * ((ia * ia) * ia);
   s->x = nx;
   s->y = ny;
   if ((s->sec < 18) != (nsec < 18)) {

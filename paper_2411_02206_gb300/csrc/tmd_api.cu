@@ -104,6 +104,7 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
   L.z_lb = z((size_t)L.n_chunks * 8 + 8);
   L.track_start = p(((size_t)nt + 1) * 4);
   L.order = p((size_t)nt * 4 + 4);
+  L.keys = p((size_t)na * 2 + 16);
   L.rank = p((size_t)na * 2 + 4);
   L.tile_hist = p((size_t)L.n_tiles * kNBin * 2 + 4);
   L.group_sum = p((size_t)L.n_groups * kNBin * 4 + 4);
@@ -190,8 +191,10 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
       (rc = tmd_cuda_check(h, cudaFuncSetAttribute(k_count_rank,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   kCountRankSmem), "smem attribute")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                  &h->occ_decode, k_track_decode, 256, 0), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, occupancy_track_decode(0, &h->occ_decode_v[0]), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, occupancy_track_decode(2, &h->occ_decode_v[2]), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, occupancy_track_decode(3, &h->occ_decode_v[3]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                   &h->occ_unatt, k_unatt_decode, 256, 0), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -199,7 +202,10 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
     delete h;
     return rc;
   }
-  if (h->occ_decode < 1) h->occ_decode = 1;
+  for (int v = 0; v < 4; v++)
+    if (h->occ_decode_v[v] < 1) h->occ_decode_v[v] = 1;
+  h->occ_decode = h->occ_decode_v[h->tune_decode_variant];
+  if (!h->autotune_cache.empty()) tmd_tune_load(h);
   if (h->occ_unatt < 1) h->occ_unatt = 1;
   if (h->occ_encode < 1) h->occ_encode = 1;
   *out = h;
@@ -222,7 +228,7 @@ extern "C" const char* tmd_last_error_string(const tmd_handle* h) {
 // instrumentation
 // ---------------------------------------------------------------------------
 static const char* kKernelNames[kKNum] = {
-    "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_count_rank",
+    "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_keys", "k_count_rank",
     "k_group_sum", "k_row_offsets", "k_tile_base", "k_track_decode", "k_unatt_decode",
     "k_track_encode"};
 
@@ -302,7 +308,7 @@ struct RecordLayout {
 static RecordLayout record_layout(uint32_t n, bool enc) {
   RecordLayout r;
   r.pre = 0;
-  r.frames = align_up(5 * ((size_t)n + 1) * 4, 64);
+  r.frames = align_up(6 * ((size_t)n + 1) * 4, 64);
   r.enc = align_up(r.frames + (size_t)n * sizeof(FrameDev), 64);
   r.bytes = align_up(r.enc + (enc ? (size_t)n * sizeof(EncDev) : 0), 64);
   r.counters_unused = 0;
@@ -345,7 +351,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   int slot = 0;
   if ((rc = h->acquire_slot(record_bytes, slot)) != TMD_OK) return rc;
   tmd_handle::Slot& S = h->slots[slot];
-  rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st);
+  rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on);
   if (rc != TMD_OK) return rc;
   CK(cudaEventRecord(S.done, st));
   S.used = true;
@@ -354,7 +360,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
 
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                 const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
-                void* host_record, void* dev_record, cudaStream_t st) {
+                void* host_record, void* dev_record, cudaStream_t st, bool profile) {
   const bool encode = tin != nullptr;
   std::vector<FrameLayout> L;
   size_t zbytes = 0, pbytes = 0;
@@ -370,9 +376,10 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   uint32_t* pre_grp = pre + 2 * (nf + 1);
   uint32_t* pre_warp = pre + 3 * (nf + 1);
   uint32_t* pre_chunk = pre + 4 * (nf + 1);
+  uint32_t* pre_kt = pre + 5 * (nf + 1);
   FrameDev* fd = reinterpret_cast<FrameDev*>(host + R.frames);
   EncDev* ed = reinterpret_cast<EncDev*>(host + R.enc);
-  pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = 0;
+  pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = pre_kt[0] = 0;
   uint32_t* zero_bins = reinterpret_cast<uint32_t*>(zb + 256);
   for (uint32_t f = 0; f < nf; f++) {
     FrameDev& F = fd[f];
@@ -415,6 +422,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     F.lookback = reinterpret_cast<unsigned long long*>(zb + l.z_lb);
     F.track_start = reinterpret_cast<uint32_t*>(pb + l.track_start);
     F.order = reinterpret_cast<uint32_t*>(pb + l.order);
+    F.keys = reinterpret_cast<uint16_t*>(pb + l.keys);
     F.rank = reinterpret_cast<uint16_t*>(pb + l.rank);
     F.tile_hist = reinterpret_cast<uint16_t*>(pb + l.tile_hist);
     F.group_sum = reinterpret_cast<uint32_t*>(pb + l.group_sum);
@@ -424,8 +432,11 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     pre_tblk[f + 1] = pre_tblk[f] + l.n_tblocks;
     pre_tile[f + 1] = pre_tile[f] + l.n_tiles;
     pre_grp[f + 1] = pre_grp[f] + l.n_groups * kBinBlocks;
-    pre_warp[f + 1] = pre_warp[f] + ceil_div(F.n_tracks, 32);
+    // encoder: warp tasks of 32 tracks; decoder: attached clusters (the
+    // decoder splits the clusters of all frames evenly over its blocks)
+    pre_warp[f + 1] = pre_warp[f] + (encode ? ceil_div(F.n_tracks, 32) : F.n_att);
     pre_chunk[f + 1] = pre_chunk[f] + l.n_chunks;
+    pre_kt[f + 1] = pre_kt[f] + ceil_div(F.n_tracks, 32);
   }
   PlanDev P;
   const uint32_t* dpre = reinterpret_cast<const uint32_t*>(dev + R.pre);
@@ -435,6 +446,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   P.pre_grp = dpre + 2 * (nf + 1);
   P.pre_warp = dpre + 3 * (nf + 1);
   P.pre_chunk = dpre + 4 * (nf + 1);
+  P.pre_kt = dpre + 5 * (nf + 1);
   P.counters = reinterpret_cast<uint32_t*>(zb);
   const FrameDev* dframes = reinterpret_cast<const FrameDev*>(dev + R.frames);
   const EncDev* denc = reinterpret_cast<const EncDev*>(dev + R.enc);
@@ -443,7 +455,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   CK(cudaMemsetAsync(zb, 0, zbytes, st));
   TmdProfile& prof = h->prof;
   auto timed = [&](int id, auto&& launch) {
-    if (!prof.on) {
+    if (!profile) {
       launch();
       return;
     }
@@ -466,17 +478,29 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       timed(kKTrackEncode, [&] { k_track_encode<<<grid, 256, 0, st>>>(denc, dframes, P, n_warp); });
     }
   } else {
+    const uint32_t n_kt = pre_kt[nf];
+    if (n_kt) {
+      const uint32_t grid = std::min<uint32_t>(n_kt / 8 + 1, (uint32_t)(h->sms * 8));
+      timed(kKKeys, [&] { k_keys<<<grid, 256, 0, st>>>(dframes, P, n_kt); });
+    }
     if (n_tile)
       timed(kKCountRank, [&] { k_count_rank<<<n_tile, 256, kCountRankSmem, st>>>(dframes, P); });
     if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
     if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
-    if (n_warp) {
-      const uint32_t grid = std::min<uint32_t>(n_warp / 8 + 1, (uint32_t)(h->sms * h->occ_decode));
-      timed(kKTrackDecode, [&] { k_track_decode<<<grid, 256, 0, st>>>(dframes, P, n_warp); });
+    if (n_warp) {  // n_warp = attached clusters of all frames
+      const int var = h->tune_decode_variant;
+      int bps = h->occ_decode_v[var];
+      if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
+      // at least ~4k clusters per block
+      const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
+          (uint32_t)(h->sms * bps), (n_warp + 4095) / 4096));
+      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_warp); });
     }
     if (n_chunk) {
-      const uint32_t grid = std::min<uint32_t>(n_chunk, (uint32_t)(h->sms * h->occ_unatt));
+      int bps = h->occ_unatt;
+      if (h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;
+      const uint32_t grid = std::min<uint32_t>(n_chunk, (uint32_t)(h->sms * bps));
       timed(kKUnattDecode, [&] { k_unatt_decode<<<grid, 256, 0, st>>>(dframes, P, n_chunk); });
     }
   }

@@ -16,7 +16,7 @@ struct TmdServer;  // serving state (tmd_serve.cu)
 
 // Kernel ids of the instrumentation.
 enum TmdKernel {
-  kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKCountRank, kKGroupSum,
+  kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKKeys, kKCountRank, kKGroupSum,
   kKRowOffsets, kKTileBase, kKTrackDecode, kKUnattDecode, kKTrackEncode, kKNum
 };
 
@@ -43,6 +43,11 @@ struct tmd_handle {
   int device = 0;
   int sms = 0;
   int occ_decode = 1, occ_unatt = 1, occ_encode = 1;
+  int occ_decode_v[4] = {1, 1, 1, 1};  // resident blocks per SM of each decoder variant
+  // tuning parameters (launch shapes only; results never depend on them)
+  int tune_decode_variant = 1;   // register-budget variant of the track decoder
+  int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
+  int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;
   uint32_t max_slots = 0;
   std::string autotune_cache;
@@ -72,7 +77,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
 struct FrameLayout {
   uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
   size_t z_heads, z_len, z_lb;                    // offsets in the zeroed part
-  size_t track_start, order, rank, tile_hist, group_sum, tile_base, unatt_start, blk_sum,
+  size_t track_start, order, keys, rank, tile_hist, group_sum, tile_base, unatt_start, blk_sum,
       att_count;                                  // offsets in the plain part
 };
 // Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts.
@@ -83,9 +88,12 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
 void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin,
                     size_t* scratch_bytes, size_t* record_bytes);
 // Fill the launch record (host_record, pinned) for the given scratch and enqueue
-// the record upload and the kernel chain on st.  The caller keeps scratch and
+// the record upload and the kernel chain on st (with per-kernel events into
+// the handle's profile if `profile`; only the handle's own thread may ask).  The caller keeps scratch and
 // both record buffers alive until the stream has passed the chain.
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                 const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
-                void* host_record, void* dev_record, cudaStream_t st);
+                void* host_record, void* dev_record, cudaStream_t st, bool profile);
 void tmd_serve_shutdown(tmd_handle* h);
+// Read the tuning parameters for this GPU from the autotune cache, if any.
+void tmd_tune_load(tmd_handle* h);

@@ -55,17 +55,14 @@ extern "C" int tmd_batch_create(tmd_handle* h, uint32_t n, const tmd_frame_in* i
   }
   int rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream");
   if (rc != TMD_OK) { delete b; return rc; }
-  const bool prof = h->prof.on;
-  h->prof.on = false;  // no event nodes inside the graph
   rc = tmd_cuda_check(h, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal),
                       "begin capture");
   if (rc == TMD_OK) {
     rc = tmd_enqueue(h, n, in, out, nullptr, nullptr, b->scratch, b->host_record, b->dev_record,
-                     b->cap);
+                     b->cap, false);  // no event nodes inside the graph
     const int rc2 = tmd_cuda_check(h, cudaStreamEndCapture(b->cap, &b->graph), "end capture");
     if (rc == TMD_OK) rc = rc2;
   }
-  h->prof.on = prof;
   if (rc == TMD_OK)
     rc = tmd_cuda_check(h, cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
   if (rc != TMD_OK) {

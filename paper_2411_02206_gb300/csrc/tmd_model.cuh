@@ -31,6 +31,8 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+// 1/x correctly rounded: the same value as the division 1.0f / x.
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
 
 // Model constants (binary32).
 constexpr float kSY2 = 0.01f;     // measurement variance of y [cm^2]
@@ -145,8 +147,9 @@ __device__ __forceinline__ void sector_change(Track& s, int nsec) {
   if (!(a >= 1.0e-3f || a <= -1.0e-3f)) a = (a < 0.0f) ? -1.0e-3f : 1.0e-3f;
   const float nx = fadd(fmul(s.x, ca), fmul(s.y, sa));
   const float ny = fsub(fmul(s.y, ca), fmul(s.x, sa));
-  s.ty = fdiv(b, a);
-  s.c = fdiv(s.c, fmul(fmul(a, a), a));
+  const float ia = frcp(a);
+  s.ty = fmul(b, ia);
+  s.c = fmul(s.c, fmul(fmul(ia, ia), ia));
   s.x = nx;
   s.y = ny;
   if ((s.sec < 18) != (nsec < 18)) {
@@ -213,7 +216,7 @@ __device__ __forceinline__ void propagate_predict(const RowGeo* g, Track& s, uin
 __device__ __forceinline__ void update(const RowGeo* g, Track& s, uint32_t padq, uint32_t timeq) {
   const float ym = pad_to_y(g, padq, s.row);
   const float tm = time_to_t(timeq);
-  const float inv = fdiv(1.0f, fadd(s.c00, kSY2));
+  const float inv = frcp(fadd(s.c00, kSY2));
   const float k0 = fmul(s.c00, inv), k1 = fmul(s.c01, inv), k2 = fmul(s.c02, inv);
   const float r = fsub(ym, s.y);
   s.y = fadd(s.y, fmul(k0, r));
@@ -226,7 +229,7 @@ __device__ __forceinline__ void update(const RowGeo* g, Track& s, uint32_t padq,
   s.c11 = fsub(s.c11, fmul(k1, c01));
   s.c12 = fsub(s.c12, fmul(k1, c02));
   s.c22 = fsub(s.c22, fmul(k2, c02));
-  const float invt = fdiv(1.0f, fadd(s.d00, kST2));
+  const float invt = frcp(fadd(s.d00, kST2));
   const float g0 = fmul(s.d00, invt), g1 = fmul(s.d01, invt);
   const float rt = fsub(tm, s.t);
   s.t = fadd(s.t, fmul(g0, rt));

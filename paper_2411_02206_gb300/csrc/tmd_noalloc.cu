@@ -50,12 +50,12 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kArrayBytes];
 // Writes the frame descriptor and the prefix tables of a one-frame plan into
 // the record area.
 __global__ void k_noalloc_record(FrameDev f, uint32_t n_tblk, uint32_t n_tile, uint32_t n_grp,
-                                 uint32_t n_warp, uint32_t n_chunk, FrameDev* dst_frame,
-                                 uint32_t* dst_pre) {
+                                 uint32_t n_warp, uint32_t n_chunk, uint32_t n_kt,
+                                 FrameDev* dst_frame, uint32_t* dst_pre) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *dst_frame = f;
-    const uint32_t v[5] = {n_tblk, n_tile, n_grp, n_warp, n_chunk};
-    for (int i = 0; i < 5; i++) {
+    const uint32_t v[6] = {n_tblk, n_tile, n_grp, n_warp, n_chunk, n_kt};
+    for (int i = 0; i < 6; i++) {
       dst_pre[2 * i] = 0;
       dst_pre[2 * i + 1] = v[i];
     }
@@ -79,7 +79,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     char msg[256];
     snprintf(msg, sizeof msg,
              "frame needs %zu bytes of scratch; tmd_decode_frame_noalloc is limited to %zu bytes "
-             "(64 MiB, about 19 M attached clusters); use tmd_decode_frame",
+             "(64 MiB, about 12 M attached clusters); use tmd_decode_frame",
              need, kScratchMax);
     set_err(err, err_len, msg);
     return TMD_ERR_ARG;
@@ -103,7 +103,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
           cudaFuncSetAttribute(k_count_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kCountRankSmem) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_track_decode, 256, 0) != cudaSuccess ||
+          occupancy_track_decode(0, &od) != cudaSuccess ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_unatt_decode, 256, 0) != cudaSuccess) {
         set_err(err, err_len, "device set-up failed");
         return TMD_ERR_CUDA;
@@ -138,6 +138,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.lookback = reinterpret_cast<unsigned long long*>(zb + L.z_lb);
   F.track_start = reinterpret_cast<uint32_t*>(pb + L.track_start);
   F.order = reinterpret_cast<uint32_t*>(pb + L.order);
+  F.keys = reinterpret_cast<uint16_t*>(pb + L.keys);
   F.rank = reinterpret_cast<uint16_t*>(pb + L.rank);
   F.tile_hist = reinterpret_cast<uint16_t*>(pb + L.tile_hist);
   F.group_sum = reinterpret_cast<uint32_t*>(pb + L.group_sum);
@@ -145,7 +146,9 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.unatt_start = reinterpret_cast<uint32_t*>(pb + L.unatt_start);
   F.blk_sum = reinterpret_cast<uint32_t*>(pb + L.blk_sum);
   const uint32_t n_tblk = L.n_tblocks, n_tile = L.n_tiles, n_grp = L.n_groups * kBinBlocks;
-  const uint32_t n_warp = (in->n_tracks + 31) / 32, n_chunk = L.n_chunks;
+  const uint32_t n_warp = in->n_attached;  // the decoder's blocks split the clusters
+  const uint32_t n_chunk = L.n_chunks;
+  const uint32_t n_kt = (in->n_tracks + 31) / 32;
   FrameDev* dframe = reinterpret_cast<FrameDev*>(rec);
   uint32_t* dpre = reinterpret_cast<uint32_t*>(rec + 1024);
   PlanDev P;
@@ -155,8 +158,10 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   P.pre_grp = dpre + 4;
   P.pre_warp = dpre + 6;
   P.pre_chunk = dpre + 8;
+  P.pre_kt = dpre + 10;
   P.counters = reinterpret_cast<uint32_t*>(zb);
-  k_noalloc_record<<<1, 32, 0, st>>>(F, n_tblk, n_tile, n_grp, n_warp, n_chunk, dframe, dpre);
+  k_noalloc_record<<<1, 32, 0, st>>>(F, n_tblk, n_tile, n_grp, n_warp, n_chunk, n_kt, dframe,
+                                     dpre);
   if (cudaMemsetAsync(zb, 0, zbytes, st) != cudaSuccess) {
     set_err(err, err_len, "cudaMemsetAsync failed");
     return TMD_ERR_CUDA;
@@ -165,13 +170,18 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   if (n_tblk) k_track_scan1<<<n_tblk, 256, 0, st>>>(dframe, P);
   k_frame_scan<<<1, 1024, 0, st>>>(dframe, P);
   if (n_tblk) k_track_scan2<<<n_tblk, 256, 0, st>>>(dframe, P);
+  if (n_kt) {
+    const uint32_t cap = (uint32_t)(S->sms * 8);
+    k_keys<<<n_kt / 8 + 1 < cap ? n_kt / 8 + 1 : cap, 256, 0, st>>>(dframe, P, n_kt);
+  }
   if (n_tile) k_count_rank<<<n_tile, 256, kCountRankSmem, st>>>(dframe, P);
   if (n_grp) k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
   k_row_offsets<<<1, 1024, 0, st>>>(dframe, P);
   if (n_grp) k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
   if (n_warp) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_decode);
-    k_track_decode<<<n_warp / 8 + 1 < cap ? n_warp / 8 + 1 : cap, 256, 0, st>>>(dframe, P, n_warp);
+    const uint32_t want = (n_warp + 4095) / 4096;
+    launch_track_decode(0, want < cap ? want : cap, st, dframe, P, n_warp);
   }
   if (n_chunk) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_unatt);

@@ -43,6 +43,8 @@ __global__ void __launch_bounds__(256) k_unatt_decode(const FrameDev* frames, Pl
   __shared__ uint32_t s_ticket;
   __shared__ Seg s_warp[8];
   __shared__ Seg s_carry;
+  __shared__ uint32_t s_rec[kChunk * 3];  // records of the chunk, element order
+  __shared__ uint32_t s_pos[kChunk];      // native index of every element
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (;;) {
     if (tid == 0) s_ticket = atomicAdd(&plan.counters[1], 1u);
@@ -172,26 +174,69 @@ __global__ void __launch_bounds__(256) k_unatt_decode(const FrameDev* frames, Pl
       const Seg wex = wid == 0 ? Seg{0u, 0u, 0u} : s_warp[wid];
       ex = seg_add(seg_add(s_carry, wex), lane_ex);
     }
-    // write the records
+    // charges and flags of the 8 clusters (vector loads when in range)
+    uint32_t qt[8], qm[8], fl[8], sp[8], sg[8];
+    if (e0 + 8 <= n && ((reinterpret_cast<uintptr_t>(F.qtot_u) | reinterpret_cast<uintptr_t>(F.qmax_u)) & 15) == 0 &&
+        ((reinterpret_cast<uintptr_t>(F.flags_u) | reinterpret_cast<uintptr_t>(F.sigp_u) |
+          reinterpret_cast<uintptr_t>(F.sigt_u)) & 7) == 0) {
+      const uint4 a = *reinterpret_cast<const uint4*>(F.qtot_u + e0);
+      const uint4 m = *reinterpret_cast<const uint4*>(F.qmax_u + e0);
+      const uint2 fa = *reinterpret_cast<const uint2*>(F.flags_u + e0);
+      const uint2 pa = *reinterpret_cast<const uint2*>(F.sigp_u + e0);
+      const uint2 ta = *reinterpret_cast<const uint2*>(F.sigt_u + e0);
+      const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        qt[k] = (aw[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+        qm[k] = (mw[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+        fl[k] = ((k < 4 ? fa.x : fa.y) >> ((k & 3) * 8)) & 0xFFu;
+        sp[k] = ((k < 4 ? pa.x : pa.y) >> ((k & 3) * 8)) & 0xFFu;
+        sg[k] = ((k < 4 ? ta.x : ta.y) >> ((k & 3) * 8)) & 0xFFu;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const uint32_t e = e0 + k;
+        const bool in = e < n;
+        qt[k] = in ? F.qtot_u[e] : 0u;
+        qm[k] = in ? F.qmax_u[e] : 0u;
+        fl[k] = in ? F.flags_u[e] : 0u;
+        sp[k] = in ? F.sigp_u[e] : 0u;
+        sg[k] = in ? F.sigt_u[e] : 0u;
+      }
+    }
+    // stage the records and their native indices in shared memory
     const uint32_t n_total = F.n_att + F.n_unatt;
     uint32_t st = 0;
 #pragma unroll
     for (int k = 0; k < 8; k++) {
       const uint32_t e = e0 + k;
+      const uint32_t l = tid * 8 + k;
+      uint32_t pos = 0xFFFFFFFFu;
       if (e < n) {
         const Seg v = seg_add(ex, loc[k]);
         const uint32_t b = bins[k];
-        const uint32_t pos = F.row_start[b] + F.att_count[b] + (e - F.unatt_start[b]);
+        pos = F.row_start[b] + F.att_count[b] + (e - F.unatt_start[b]);
         if (v.time > 0xFFFFFFu) st |= kStTime;
         if (pos >= n_total) {
           st |= kStLimit;
-          continue;
+          pos = 0xFFFFFFFFu;
         }
-        uint32_t* dst = reinterpret_cast<uint32_t*>(F.native + (size_t)pos * kRecBytes);
-        dst[0] = (v.time & 0xFFFFFFu) | ((uint32_t)F.flags_u[e] << 24);
-        dst[1] = v.pad | ((uint32_t)F.sigt_u[e] << 16) | ((uint32_t)F.sigp_u[e] << 24);
-        dst[2] = (uint32_t)F.qmax_u[e] | ((uint32_t)F.qtot_u[e] << 16);
+        s_rec[3 * l + 0] = (v.time & 0xFFFFFFu) | (fl[k] << 24);
+        s_rec[3 * l + 1] = v.pad | (sg[k] << 16) | (sp[k] << 24);
+        s_rec[3 * l + 2] = qm[k] | (qt[k] << 16);
       }
+      s_pos[l] = pos;
+    }
+    __syncthreads();
+    // write out word by word: consecutive threads write consecutive words of
+    // consecutive records, which are contiguous in the native list within a bin
+    const uint32_t n_here = min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
+    for (uint32_t w = tid; w < 3 * n_here; w += blockDim.x) {
+      const uint32_t l = w / 3;
+      const uint32_t pos = s_pos[l];
+      if (pos != 0xFFFFFFFFu)
+        reinterpret_cast<uint32_t*>(F.native)[(size_t)pos * 3 + (w - 3 * l)] = s_rec[w];
     }
     if (st) atomicOr(F.status, st);
     __syncthreads();

@@ -55,3 +55,19 @@ def assemble(truth_dev: dict, enc_dev: dict) -> dict:
     for k in ("qtot_a", "qmax_a", "flags_a", "sigma_pad_a", "sigma_time_a") + synth.UNATT:
         f[k] = truth_dev[k]
     return f
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ holder for a raw device pointer."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, dtype: str = "|u1"):
+    """A torch tensor viewing library-owned device memory (no copy).  Valid
+    only while the library keeps that memory (for served results: until
+    tmd_release)."""
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, shape, dtype), device="cuda")

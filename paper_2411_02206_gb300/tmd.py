@@ -114,6 +114,13 @@ def lib():
                                                    ctypes.POINTER(tmd_frame_out), _P,
                                                    ctypes.c_char_p, ctypes.c_size_t]
             L.tmd_decode_frame_noalloc.restype = ctypes.c_int
+            L.tmd_tune_set.argtypes = [H, ctypes.c_char_p, ctypes.c_int]
+            L.tmd_tune_set.restype = ctypes.c_int
+            L.tmd_tune_get.argtypes = [H, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+            L.tmd_tune_get.restype = ctypes.c_int
+            L.tmd_autotune.argtypes = [H, ctypes.c_uint32, ctypes.POINTER(tmd_frame_in),
+                                       ctypes.POINTER(tmd_frame_out), _P]
+            L.tmd_autotune.restype = ctypes.c_int
             L.tmd_profile_enable.argtypes = [H, ctypes.c_int]
             L.tmd_profile_enable.restype = ctypes.c_int
             L.tmd_profile_read.argtypes = [H, ctypes.c_uint32, ctypes.c_char_p,
@@ -177,10 +184,12 @@ def frame_out(native, row_start, att_count, status) -> tmd_frame_out:
 class Decoder:
     """Owns a tmd_handle; thin wrappers over the C entry points."""
 
-    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_slots: int = 0):
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_slots: int = 0,
+                 autotune_cache: str | None = None):
         self._L = lib()
         self.h = ctypes.c_void_p()
-        cfg = tmd_config(device, mem_budget_bytes, max_slots, None, 0)
+        self._cache = autotune_cache.encode() if autotune_cache else None
+        cfg = tmd_config(device, mem_budget_bytes, max_slots, self._cache, 0)
         rc = self._L.tmd_create(ctypes.byref(cfg), ctypes.byref(self.h))
         if rc != TMD_OK:
             raise TmdError(rc, "tmd_create failed")
@@ -248,6 +257,20 @@ class Decoder:
 
     def tmd_batch_destroy(self, batch) -> int:
         return self._check(self._L.tmd_batch_destroy(batch))
+
+    def tmd_tune_set(self, key: str, value: int) -> int:
+        return self._check(self._L.tmd_tune_set(self.h, key.encode(), value))
+
+    def tmd_tune_get(self, key: str) -> int:
+        v = ctypes.c_int(0)
+        self._check(self._L.tmd_tune_get(self.h, key.encode(), ctypes.byref(v)))
+        return int(v.value)
+
+    def tmd_autotune(self, fins, fouts, stream=None) -> int:
+        n = len(fins)
+        ins = (tmd_frame_in * n)(*fins)
+        outs = (tmd_frame_out * n)(*fouts)
+        return self._check(self._L.tmd_autotune(self.h, n, ins, outs, _P(_stream_ptr(stream))))
 
     def tmd_profile_enable(self, on: bool) -> int:
         return self._check(self._L.tmd_profile_enable(self.h, 1 if on else 0))

@@ -21,7 +21,7 @@ MUTANTS = {
     "missing_half": ("float h = (0.5f * s->c) * dx;", "float h = s->c * dx;"),
     "cov_update_index": ("s->c12 = s->c12 - k1 * c02;", "s->c12 = s->c12 - k1 * c01;"),
     "time_cov_gain": ("s->d11 = s->d11 - g1 * d01;", "s->d11 = s->d11 - g0 * d01;"),
-    "rotation_curvature_power": ("s->c = s->c / ((a * a) * a);", "s->c = s->c / (a * a);"),
+    "rotation_curvature_power": ("s->c = s->c * ((ia * ia) * ia);", "s->c = s->c * (ia * ia);"),
     "no_side_flip": ("if ((s->sec < 18) != (nsec < 18)) {", "if (0) {"),
     "unattached_no_running_sum": ("padq = (padq + f->pad_diff_u[u]) & 0xFFFFu;",
                                   "padq = f->pad_diff_u[u];"),
