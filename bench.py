@@ -148,12 +148,39 @@ def cpu_baseline(truth, min_seconds=10.0, max_reps=8):
                       f"serial C oracle, {t:.1f} s"}
 
 
-def decode_kernel_bytes(nt, na):
-    """Algorithmic bytes of one k_track_decode launch: per attached cluster
-    7 B of charges/sigmas/flags read and 12 B of native record written, per
-    cluster after the first of its track 8 B of residual streams read, per
-    track an 11 B header read."""
-    return 7 * na + 8 * (na - nt) + 11 * nt + 12 * na
+def kernel_bytes(name, nt, na, nu):
+    """Algorithmic bytes of one launch of a decoder kernel (each input byte
+    read once, each output byte written once):
+      k_track_decode  per track a 19 B header (qpt, row, slice, pad, time,
+                      ncl, track start, decode order), per cluster after the
+                      first of its track 8 B of residual streams; per cluster
+                      8 B written (key, pad code, time code);
+      k_att_scatter   per attached cluster 17 B read (key, rank, pad code,
+                      time code, 7 B of charges, sigmas and flags) and the
+                      12 B native record written;
+      k_count_rank    per attached cluster the 2 B key read and the 2 B rank
+                      written, per ranking tile a 2 B count per bin written;
+      k_unatt_decode  per unattached cluster 13 B read and 12 B written, the
+                      per-bin counts read."""
+    n_tiles = -(-na // 32768)
+    table = {
+        "k_track_decode": 8 * (na - nt) + 19 * nt + 8 * na,
+        "k_att_scatter": 29 * na,
+        "k_count_rank": 4 * na + 2 * 5472 * n_tiles,
+        "k_unatt_decode": 25 * nu + 4 * 5472,
+    }
+    return table.get(name)
+
+
+def _kernel_entry(name, v, prof, nt, na, nu, peak):
+    ms = v[0] / v[1]
+    e = {"ms_per_launch": ms, "share": v[0] / max(1e-9, sum(x[0] for x in prof.values())),
+         "launches": v[1]}
+    b = kernel_bytes(name, nt, na, nu)
+    if b:
+        e["gbs"] = b / (ms * 1e-3) / 1e9
+        e["frac_hbm"] = e["gbs"] / peak
+    return e
 
 
 def run_reference(args):
@@ -263,14 +290,15 @@ def run(args):
     # roofline of the dominant kernel
     top = max(prof.items(), key=lambda kv: kv[1][0])
     peak, peak_src = _peaks()
-    dk_ms, dk_n = prof.get("k_track_decode", (0.0, 0))
-    dk_bytes = decode_kernel_bytes(nt, na)
-    achieved = dk_bytes / (dk_ms / dk_n * 1e-3) / 1e9 if dk_n else None
+    dk_name = top[0]
+    dk_ms, dk_n = prof[dk_name]
+    dk_bytes = kernel_bytes(dk_name, nt, na, nu)
+    achieved = dk_bytes / (dk_ms / dk_n * 1e-3) / 1e9 if (dk_n and dk_bytes) else None
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
-            traffic = json.load(open(tfile)).get("k_track_decode_bytes_per_launch")
+            traffic = json.load(open(tfile)).get(dk_name + "_bytes_per_launch")
         except Exception:
             traffic = None
     # end to end through the host-buffer entry point
@@ -315,13 +343,12 @@ def run(args):
             "dtype": "u32", "data": "synthetic",
             "config": _config(nt, na, nu, seed,
                               "inputs (0.9 GB) + outputs (0.7 GB) larger than L2 (129 MB)"),
-            "roofline": {"bound": "hbm", "kernel": "k_track_decode", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": dk_name, "achieved": achieved,
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "algorithmic_bytes": dk_bytes,
                          "ms_per_launch": dk_ms / dk_n if dk_n else None},
-            "kernels": {k: {"ms_per_launch": v[0] / v[1], "share": v[0] / max(1e-9, sum(
-                x[0] for x in prof.values())), "launches": v[1]} for k, v in prof.items()},
+            "kernels": {k: _kernel_entry(k, v, prof, nt, na, nu, peak) for k, v in prof.items()},
             "top_kernel": top[0],
             "tuning": tuned,
             "cpu_baseline": base,

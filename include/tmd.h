@@ -204,7 +204,7 @@ int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in, const tmd_frame
  * that loads the library holds until the process exits.  Inputs and outputs
  * are the caller's device buffers, as for tmd_decode_frame; the results are
  * identical.  Frames that need more than 64 MiB of scratch (roughly more
- * than 12 million attached clusters) are rejected with TMD_ERR_ARG and a
+ * than 5 million attached clusters) are rejected with TMD_ERR_ARG and a
  * message in err.  Runs on the current device and `stream`; the first call
  * on a device looks up the array's device address (once per device), so
  * make that first call before any stream capture.  All calls share the
@@ -240,7 +240,7 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
 
 /* Tuning.  Parameters change launch shapes only, never results:
  *   "decode_variant"      0..3  register budget of the track decoder
- *                               (at least 4, 5, 6, 8 resident blocks per SM)
+ *                               (at least 3, 4, 5, 6 resident blocks per SM)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
  * tmd_autotune times the decode chain on the given frames (device buffers,

@@ -5,9 +5,10 @@
 // and finds its frame from a prefix table (tmd_internal.cuh).
 //
 //   k_zero_status -> k_track_scan1 -> k_frame_scan -> k_track_scan2   (a1)
+//   k_track_decode: coordinates and (sector,row) keys                  (a4, a2)
 //   k_count_rank                                                       (a2)
 //   k_group_sum -> k_row_offsets -> k_tile_base                        (a3)
-//   k_track_decode                                                     (a4)
+//   k_att_scatter: native records of the attached clusters             (a4)
 //   k_unatt_decode                                                     (a5)
 #include <cstdio>
 #include <cstring>
@@ -105,6 +106,8 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
   L.track_start = p(((size_t)nt + 1) * 4);
   L.order = p((size_t)nt * 4 + 4);
   L.keys = p((size_t)na * 2 + 16);
+  L.kf_pad = p((size_t)na * 2 + 16);
+  L.kf_time = p((size_t)na * 4 + 16);
   L.rank = p((size_t)na * 2 + 4);
   L.tile_hist = p((size_t)L.n_tiles * kNBin * 2 + 4);
   L.group_sum = p((size_t)L.n_groups * kNBin * 4 + 4);
@@ -228,9 +231,9 @@ extern "C" const char* tmd_last_error_string(const tmd_handle* h) {
 // instrumentation
 // ---------------------------------------------------------------------------
 static const char* kKernelNames[kKNum] = {
-    "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_keys", "k_count_rank",
-    "k_group_sum", "k_row_offsets", "k_tile_base", "k_track_decode", "k_unatt_decode",
-    "k_track_encode"};
+    "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_track_decode",
+    "k_count_rank", "k_group_sum", "k_row_offsets", "k_tile_base", "k_att_scatter",
+    "k_unatt_decode", "k_track_encode"};
 
 cudaEvent_t TmdProfile::get() {
   if (pool.empty()) {
@@ -423,6 +426,8 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     F.track_start = reinterpret_cast<uint32_t*>(pb + l.track_start);
     F.order = reinterpret_cast<uint32_t*>(pb + l.order);
     F.keys = reinterpret_cast<uint16_t*>(pb + l.keys);
+    F.kf_pad = reinterpret_cast<uint16_t*>(pb + l.kf_pad);
+    F.kf_time = reinterpret_cast<uint32_t*>(pb + l.kf_time);
     F.rank = reinterpret_cast<uint16_t*>(pb + l.rank);
     F.tile_hist = reinterpret_cast<uint16_t*>(pb + l.tile_hist);
     F.group_sum = reinterpret_cast<uint32_t*>(pb + l.group_sum);
@@ -432,9 +437,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     pre_tblk[f + 1] = pre_tblk[f] + l.n_tblocks;
     pre_tile[f + 1] = pre_tile[f] + l.n_tiles;
     pre_grp[f + 1] = pre_grp[f] + l.n_groups * kBinBlocks;
-    // encoder: warp tasks of 32 tracks; decoder: attached clusters (the
-    // decoder splits the clusters of all frames evenly over its blocks)
-    pre_warp[f + 1] = pre_warp[f] + (encode ? ceil_div(F.n_tracks, 32) : F.n_att);
+    pre_warp[f + 1] = pre_warp[f] + ceil_div(F.n_tracks, 32);  // encoder warp tasks
     pre_chunk[f + 1] = pre_chunk[f] + l.n_chunks;
     pre_kt[f + 1] = pre_kt[f] + ceil_div(F.n_tracks, 32);
   }
@@ -479,24 +482,24 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     }
   } else {
     const uint32_t n_kt = pre_kt[nf];
-    if (n_kt) {
-      const uint32_t grid = std::min<uint32_t>(n_kt / 8 + 1, (uint32_t)(h->sms * 8));
-      timed(kKKeys, [&] { k_keys<<<grid, 256, 0, st>>>(dframes, P, n_kt); });
+    if (n_kt) {  // warp tasks of 32 tracks, taken from counters[0]
+      const int var = h->tune_decode_variant;
+      int bps = h->occ_decode_v[var];
+      if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
+      const uint32_t per_block = kDecodeThreads / 32;
+      const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
+          (uint32_t)(h->sms * bps), (n_kt + per_block - 1) / per_block));
+      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt); });
     }
     if (n_tile)
       timed(kKCountRank, [&] { k_count_rank<<<n_tile, 256, kCountRankSmem, st>>>(dframes, P); });
     if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
     if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
-    if (n_warp) {  // n_warp = attached clusters of all frames
-      const int var = h->tune_decode_variant;
-      int bps = h->occ_decode_v[var];
-      if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
-      // at least ~4k clusters per block
-      const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
-          (uint32_t)(h->sms * bps), (n_warp + 4095) / 4096));
-      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_warp); });
-    }
+    if (n_tile)
+      timed(kKAttScatter, [&] {
+        k_att_scatter<<<n_tile * kScatBlocksPerTile, kScatThreads, 0, st>>>(dframes, P);
+      });
     if (n_chunk) {
       int bps = h->occ_unatt;
       if (h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;

@@ -3,14 +3,31 @@
 // the TPC and restores each cluster's absolute coordinates from the stored
 // residual and the track prediction).
 //
-// Decoder: a persistent kernel whose warps take 32 tracks at a time from the
-// length-sorted order (longest first, so lanes of a warp run similar loops
-// and the tail is short).  For every cluster the lane applies the row and
-// sector/leg differences, propagates the model to the row, adds the modular
-// residuals to the quantised prediction, updates the model with the decoded
-// cluster and writes the 12-byte native record at
-//   tileBase[tile(j)][bin] + rank[j]
-// computed by k_count_rank / k_tile_base (deterministic, no atomics).
+// Decoding of the attached clusters runs in two kernels:
+//
+//   k_track_decode  one lane per track, warps take 32 tracks at a time from
+//                   the length-sorted order (longest first, so lanes of a warp
+//                   run loops of similar length and the tail is short).  For
+//                   every cluster the lane applies the row and sector/leg
+//                   differences, propagates the model to the row, adds the
+//                   modular residuals to the quantised prediction and updates
+//                   the model with the decoded cluster.  It writes, in input
+//                   order j, the cluster's (sector,row) key, pad code and time
+//                   code.
+//   k_att_scatter   one thread per attached cluster: assembles the 12-byte
+//                   native record from the decoded coordinates and the charge
+//                   streams and writes it at tileBase[tile(j)][key] + rank[j]
+//                   (k_count_rank / k_tile_base: deterministic, no atomics).
+//
+// The lane-per-track walk reads each stream at 32 unrelated positions per
+// warp.  Read directly, every lane pulls whole sectors for a few bytes and
+// the L2 has to hold one line per lane and stream until the lane has walked
+// past it.  k_track_decode therefore moves data in rounds of kRound steps:
+// the warp stages the differences of the next kRound clusters of each of its
+// 32 tracks in shared memory with coalesced loads (one instruction loads 32
+// consecutive elements of one track), the lanes run the model from shared
+// memory, and the round's outputs leave through the same buffer with
+// coalesced stores.
 //
 // Encoder: the same walk with the truth as measurement; it writes the header
 // and the residual streams (the synchronous side of the method).
@@ -26,297 +43,186 @@ __device__ __forceinline__ uint32_t next_task(uint32_t* counter) {
   return __shfl_sync(0xffffffffu, task, 0);
 }
 
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int kRound = 32;        // model steps per staging round
+constexpr int kPitch = kRound + 1;  // words per track row of a staging buffer
+
+// Staging buffers of one warp: for track-lane i and step q of the round,
+//   a[i][q] = row_diff | sld << 8 | pad_res << 16   (in)
+//             key | pad << 16                        (out)
+//   b[i][q] = time_res (in) / time (out)
+// Rows are padded to kPitch words: the coalesced fill (fixed i, q = lane)
+// and the model's reads (fixed q, i = lane) are both free of bank conflicts.
+struct WarpStage {
+  uint32_t a[32 * kPitch];
+  uint32_t b[32 * kPitch];
+};
+
 }  // namespace
 
-// Per-lane sequential reading in chunks.  A lane walks its track's clusters in
-// order, so each input stream is read sequentially.  The lanes of a warp
-// advance in chunks of kChunkSteps clusters: at a chunk boundary every lane
-// loads, for each of its ten streams, the aligned 8-byte blocks that are new
-// to the chunk (the first block of a chunk is the last block of the previous
-// one, kept in registers), then shifts the window so that element i of the
-// chunk sits at a fixed register position; the chunk's steps read their
-// inputs at compile-time positions, with no per-step loads or branches.  Only
-// blocks holding an element of the lane's own track are loaded, so every
-// access stays within the granules of the caller's buffers.
-constexpr int kChunkSteps = 8;
-
-__device__ __forceinline__ uint2 ld8(uintptr_t a) {
-  uint2 v;  // read-only, streaming: not allocated in L1 (which keeps the bin bases)
-  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(a));
-  return v;
-}
-
-// A stream of E-byte elements of one track: elements [first, end) of the
-// array at base.  The window of a chunk starting at element i covers blocks
-// floor8(base + i E) + 8 q, q = 0..E; block 0 is carried from the previous
-// chunk (or loaded by stream_begin), blocks 1..E are loaded here.
-// i may be -1 (the difference window of a track's first chunk): addresses are
-// computed in signed 64-bit arithmetic and blocks outside [first, end) are
-// never read.
-template <int E>
-__device__ __forceinline__ void load_chunk(const void* base, int64_t i, uint32_t first,
-                                           uint32_t end, uint2& carry, uint32_t (&out)[2 * E]) {
-  const uintptr_t b0 = reinterpret_cast<uintptr_t>(base);
-  const uintptr_t a = (uintptr_t)((int64_t)b0 + i * E);
-  const uintptr_t w = a & ~(uintptr_t)7;
-  const uintptr_t lo = b0 + (size_t)first * E, hi = b0 + (size_t)end * E;
-  uint32_t win[2 * E + 2];
-  win[0] = carry.x;
-  win[1] = carry.y;
-#pragma unroll
-  for (int q = 1; q <= E; q++) {
-    uint2 v = make_uint2(0u, 0u);
-    const uintptr_t bq = w + 8 * q;
-    if (bq < hi && bq + 8 > lo) v = ld8(bq);
-    win[2 * q] = v.x;
-    win[2 * q + 1] = v.y;
-  }
-  carry = make_uint2(win[2 * E], win[2 * E + 1]);
-  const uint32_t o = (uint32_t)(a & 7u);
-  const bool sel = (o & 4u) != 0;
-  const uint32_t sh = 8u * (o & 3u);
-#pragma unroll
-  for (int q = 0; q < 2 * E; q++) {
-    const uint32_t lw = sel ? win[q + 1] : win[q];
-    const uint32_t hw = sel ? win[q + 2] : win[q + 1];
-    out[q] = __funnelshift_r(lw, hw, sh);
-  }
-}
-
-// Block 0 of the first chunk (starting at element i) of a stream.
-template <int E>
-__device__ __forceinline__ uint2 stream_begin(const void* base, int64_t i, uint32_t first,
-                                              uint32_t end) {
-  const uintptr_t b0 = reinterpret_cast<uintptr_t>(base);
-  const uintptr_t w = (uintptr_t)((int64_t)b0 + i * E) & ~(uintptr_t)7;
-  const uintptr_t lo = b0 + (size_t)first * E, hi = b0 + (size_t)end * E;
-  return (w < hi && w + 8 > lo) ? ld8(w) : make_uint2(0u, 0u);
-}
-
-template <int Q> __device__ __forceinline__ uint32_t u8_at(const uint32_t (&b)[2]) {
-  return (b[Q >> 2] >> (8 * (Q & 3))) & 0xFFu;
-}
-template <int Q> __device__ __forceinline__ uint32_t u16_at(const uint32_t (&b)[4]) {
-  return (b[Q >> 1] >> (16 * (Q & 1))) & 0xFFFFu;
-}
-
-// Header of a track, fetched one track ahead.
-struct Head {
-  uint32_t t, j0, n, qpt_row_slice, pad, time;
-};
-
-__device__ __forceinline__ Head fetch_head(const FrameDev& F, uint32_t t) {
-  Head h;
-  h.t = t;
-  h.j0 = F.track_start[t];
-  h.n = F.ncl[t];
-  h.qpt_row_slice = (uint32_t)F.qpt[t] | ((uint32_t)F.row[t] << 8) | ((uint32_t)F.slice[t] << 16);
-  h.pad = F.pad[t];
-  h.time = F.time[t];
-  return h;
-}
-
-// Lane state of one track being decoded.  k is the first cluster of the next
-// chunk; the per-cluster streams of a chunk start at cluster j0 + k, the
-// per-difference streams at difference d0 + k - 1 (one difference before the
-// chunk's first cluster; cluster 0 has none).
-struct LaneTrack {
-  Track s;
-  uint32_t t, j0, d0, n, k;
-  uint32_t pad0, time0;  // first cluster, stored absolute
-  uint2 k_fl, k_sp, k_sg, k_qt, k_qm, k_rk, k_rd, k_sld, k_pr, k_tr;  // carried blocks
-};
-
-struct Chunk {
-  uint32_t fl[2], sp[2], sg[2], qt[4], qm[4], rk[4];
-  uint32_t rd[2], sld[2], pr[4], tr[8];
-};
-
-__device__ __forceinline__ void emit_record(const FrameDev& F, uint32_t pos, uint32_t n_total,
-                                            uint32_t w0, uint32_t w1, uint32_t w2, uint32_t& st) {
-  if (pos < n_total) {
-    uint32_t* dst = reinterpret_cast<uint32_t*>(F.native + (size_t)pos * kRecBytes);
-    if ((pos & 1u) == 0) {  // record starts on an 8-byte boundary
-      *reinterpret_cast<uint2*>(dst) = make_uint2(w0, w1);
-      dst[2] = w2;
-    } else {
-      dst[0] = w0;
-      *reinterpret_cast<uint2*>(dst + 1) = make_uint2(w1, w2);
-    }
-  } else {
-    st |= kStLimit;
-  }
-}
-
-// Bin base of cluster j: the first native index of bin `bin` in the tile of
-// j.  A block's lanes decode consecutive tracks, so they read the rows of one
-// or two tiles, which stay in L1.
-__device__ __forceinline__ uint32_t bin_base(const FrameDev& F, uint32_t j, uint32_t bin) {
-  return __ldg(F.tile_base + (size_t)(j / kTile) * kNBin + bin);
-}
-
-// Start the track whose header is h: seed the model, fetch the first blocks.
-__device__ __forceinline__ void lane_start(const FrameDev& F, const RowGeo* geo, LaneTrack& L,
-                                           const Head& h) {
-  L.t = h.t;
-  L.j0 = h.j0;
-  L.d0 = h.j0 - h.t;
-  L.n = h.n;
-  L.k = 0;
-  L.pad0 = h.pad;
-  L.time0 = h.time;
-  const uint32_t sl = (h.qpt_row_slice >> 16) & 255u;
-  seed(geo, L.s, h.qpt_row_slice & 255u, (h.qpt_row_slice >> 8) & 255u,
-       sl < (uint32_t)kNSec ? sl : kNSec - 1, h.pad, h.time);
-  const uint32_t j0 = L.j0, je = L.j0 + L.n, d0 = L.d0, de = L.d0 + L.n - 1;
-  L.k_fl = stream_begin<1>(F.flags_a, j0, j0, je);
-  L.k_sp = stream_begin<1>(F.sigp_a, j0, j0, je);
-  L.k_sg = stream_begin<1>(F.sigt_a, j0, j0, je);
-  L.k_qt = stream_begin<2>(F.qtot_a, j0, j0, je);
-  L.k_qm = stream_begin<2>(F.qmax_a, j0, j0, je);
-  L.k_rk = stream_begin<2>(F.rank, j0, j0, je);
-  // the difference window of the first chunk starts one element early
-  const int64_t dm = (int64_t)d0 - 1;
-  L.k_rd = stream_begin<1>(F.row_diff, dm, d0, de);
-  L.k_sld = stream_begin<1>(F.sld, dm, d0, de);
-  L.k_pr = stream_begin<2>(F.pad_res, dm, d0, de);
-  L.k_tr = stream_begin<4>(F.time_res, dm, d0, de);
-}
-
-__device__ __forceinline__ void load_all(const FrameDev& F, LaneTrack& L, Chunk& C) {
-  const uint32_t j = L.j0 + L.k, j0 = L.j0, je = L.j0 + L.n;
-  const int64_t d = (int64_t)L.d0 + L.k - 1;
-  const uint32_t d0 = L.d0, de = L.d0 + L.n - 1;
-  load_chunk<1>(F.flags_a, j, j0, je, L.k_fl, C.fl);
-  load_chunk<1>(F.sigp_a, j, j0, je, L.k_sp, C.sp);
-  load_chunk<1>(F.sigt_a, j, j0, je, L.k_sg, C.sg);
-  load_chunk<2>(F.qtot_a, j, j0, je, L.k_qt, C.qt);
-  load_chunk<2>(F.qmax_a, j, j0, je, L.k_qm, C.qm);
-  load_chunk<2>(F.rank, j, j0, je, L.k_rk, C.rk);
-  load_chunk<1>(F.row_diff, d, d0, de, L.k_rd, C.rd);
-  load_chunk<1>(F.sld, d, d0, de, L.k_sld, C.sld);
-  load_chunk<2>(F.pad_res, d, d0, de, L.k_pr, C.pr);
-  load_chunk<4>(F.time_res, d, d0, de, L.k_tr, C.tr);
-}
-
-// Step Q of the chunk: decode cluster k = L.k + Q of the lane's track.
-template <int Q>
-__device__ __forceinline__ uint32_t chunk_step(const FrameDev& F, const RowGeo* geo, LaneTrack& L,
-                                               const Chunk& C, uint32_t n_total) {
-  uint32_t st = 0, padq, timeq;
-  if (Q == 0 && L.k == 0) {  // first cluster of the track: stored absolute
-    padq = L.pad0;
-    timeq = L.time0;
-  } else {
-    st = key_step(L.s, u8_at<Q>(C.rd), u8_at<Q>(C.sld));
-    uint32_t ppad, ptime;
-    propagate_predict(geo, L.s, ppad, ptime);
-    padq = (ppad + u16_at<Q>(C.pr)) & 0xFFFFu;
-    timeq = ptime + C.tr[Q];
-    update(geo, L.s, padq, timeq);
-  }
-  const uint32_t j = L.j0 + L.k + Q;
-  if (timeq > 0xFFFFFFu) st |= kStTime;
-  const uint32_t pos = bin_base(F, j, L.s.sec * kNRow + L.s.row) + u16_at<Q>(C.rk);
-  emit_record(F, pos, n_total, (timeq & 0xFFFFFFu) | (u8_at<Q>(C.fl) << 24),
-              (padq & 0xFFFFu) | (u8_at<Q>(C.sg) << 16) | (u8_at<Q>(C.sp) << 24),
-              u16_at<Q>(C.qm) | (u16_at<Q>(C.qt) << 16), st);
-  return st;
-}
-
-template <int Q>
-__device__ __forceinline__ void chunk_steps(const FrameDev& F, const RowGeo* geo, LaneTrack& L,
-                                            const Chunk& C, uint32_t n_total, uint32_t& st) {
-  if (L.k + Q < L.n) st |= chunk_step<Q>(F, geo, L, C, n_total);
-  if constexpr (Q + 1 < kChunkSteps) chunk_steps<Q + 1>(F, geo, L, C, n_total, st);
-}
-
-// Static, cluster-balanced partition: the attached clusters of all frames
-// are split into gridDim.x equal ranges, and block c decodes the tracks whose
-// first cluster lies in range c (frame by frame), its lanes pulling the
-// tracks one by one and fetching the header of their next track while they
-// decode the current one.  Consecutive tracks keep the block's reads and
-// writes inside one window of memory, so L2 merges neighbouring records.
-// pre_warp holds the prefix of the frames' attached-cluster counts.
 template <int MINB>
 __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const FrameDev* frames,
                                                                        PlanDev plan,
-                                                                       uint32_t unused) {
+                                                                       uint32_t n_tasks) {
   __shared__ RowGeo geo;
-  __shared__ uint32_t s_next, s_end;
+  __shared__ WarpStage stage[kDecodeThreads / 32];
   fill_row_geo(&geo);
-  const uint64_t total = plan.pre_warp[plan.n_frames];
-  const uint64_t c0 = total * blockIdx.x / gridDim.x, c1 = total * (blockIdx.x + 1) / gridDim.x;
-  uint32_t f = c0 < total ? find_frame(plan.pre_warp, plan.n_frames, (uint32_t)c0) : plan.n_frames;
-  for (; f < plan.n_frames && plan.pre_warp[f] < c1; f++) {
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31;
+  WarpStage& W = stage[threadIdx.x >> 5];
+  for (;;) {
+    const uint32_t task = next_task(&plan.counters[0]);
+    if (task >= n_tasks) break;
+    const uint32_t f = find_frame(plan.pre_kt, plan.n_frames, task);
     const FrameDev& F = frames[f];
-    const uint32_t fa = plan.pre_warp[f];
-    if (*F.status & kStCount || F.n_tracks == 0) continue;
-    // tracks of frame f whose first cluster lies in [c0, c1) (frame-local)
-    const uint32_t lo_c = c0 > fa ? (uint32_t)(c0 - fa) : 0u;
-    const uint64_t hi64 = c1 - fa;
-    const uint32_t hi_c = hi64 < (uint64_t)F.n_att ? (uint32_t)hi64 : F.n_att;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t lo = 0, hi = F.n_tracks;  // first t with trackStart[t] >= lo_c
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (F.track_start[mid] < lo_c) lo = mid + 1; else hi = mid;
-      }
-      s_next = lo;
-      hi = F.n_tracks;  // first t with trackStart[t] >= hi_c
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (F.track_start[mid] < hi_c) lo = mid + 1; else hi = mid;
-      }
-      s_end = lo;
+    if (*F.status & kStCount) continue;
+    const uint32_t idx = (task - plan.pre_kt[f]) * 32u + lane;
+    // the lane's track: first cluster j0, n clusters, differences from d0
+    uint32_t j0 = 0, n = 0, dm1 = 0, pad0 = 0, time0 = 0, st = 0;
+    Track s;
+    if (idx < F.n_tracks) {
+      const uint32_t t = F.order[idx];
+      j0 = F.track_start[t];
+      n = F.ncl[t];
+      dm1 = j0 - t - 1u;  // difference index of cluster k is dm1 + k (mod 2^32)
+      pad0 = F.pad[t];
+      time0 = F.time[t];
+      const uint32_t raw = F.row[t], sec = F.slice[t];
+      if (raw >= (uint32_t)kNRow || sec >= (uint32_t)kNSec) st |= kStRow;
+      seed(&geo, s, F.qpt[t], (int)raw, sec < (uint32_t)kNSec ? (int)sec : kNSec - 1, pad0,
+           time0);
     }
-    __syncthreads();
-    const uint32_t tb = s_end;
-    const uint32_t n_total = F.n_att + F.n_unatt;
-    uint32_t st = 0;
-    LaneTrack L;
-    Chunk C;
-    // the lane's next track and its header, fetched one track ahead
-    uint32_t tn = atomicAdd(&s_next, 1u);
-    Head hn;
-    if (tn < tb) hn = fetch_head(F, tn);
-    bool active = false;
-    for (;;) {
-      if (!active && tn < tb) {
-        lane_start(F, &geo, L, hn);
-        active = true;
-        tn = atomicAdd(&s_next, 1u);
-        if (tn < tb) hn = fetch_head(F, tn);
-      }
-      if (!__any_sync(0xffffffffu, active)) break;
-      if (active) {
-        load_all(F, L, C);
-        chunk_steps<0>(F, &geo, L, C, n_total, st);
-        L.k += kChunkSteps;
-        active = L.k < L.n;
+    const uint32_t nmax = __reduce_max_sync(kFull, n);
+    // stage round 0 (cluster 0 is stored absolute: differences from k = 1)
+#pragma unroll 4
+    for (int i = 0; i < 32; i++) {
+      const uint32_t ni = __shfl_sync(kFull, n, i), di = __shfl_sync(kFull, dm1, i);
+      if (lane >= 1 && lane < ni) {
+        const uint32_t d = di + lane;
+        W.a[i * kPitch + lane] = (uint32_t)F.row_diff[d] | ((uint32_t)F.sld[d] << 8) |
+                                 ((uint32_t)F.pad_res[d] << 16);
+        W.b[i * kPitch + lane] = F.time_res[d];
       }
     }
-    if (st) atomicOr(F.status, st);
+    __syncwarp();
+    for (uint32_t k0 = 0; k0 < nmax; k0 += kRound) {
+      const uint32_t qn = nmax - k0 < (uint32_t)kRound ? nmax - k0 : (uint32_t)kRound;
+      const uint32_t rem = n > k0 ? n - k0 : 0u;  // steps of this lane in the round
+      for (uint32_t q = 0; q < qn; q++) {
+        if (q < rem) {
+          uint32_t padq, timeq;
+          if (k0 + q == 0) {
+            padq = pad0;
+            timeq = time0;
+          } else {
+            const uint32_t a = W.a[lane * kPitch + q], tr = W.b[lane * kPitch + q];
+            st |= key_step(s, a & 255u, (a >> 8) & 255u);
+            uint32_t ppad, ptime;
+            propagate_predict(&geo, s, ppad, ptime);
+            padq = (ppad + (a >> 16)) & 0xFFFFu;
+            timeq = ptime + tr;
+            update(&geo, s, padq, timeq);
+          }
+          if (timeq > 0xFFFFFFu) st |= kStTime;
+          W.a[lane * kPitch + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
+          W.b[lane * kPitch + q] = timeq;
+        }
+      }
+      __syncwarp();
+      // write this round's outputs and stage the next round's differences
+      const uint32_t k = k0 + lane, kn = k + kRound;
+      const bool more = k0 + kRound < nmax;
+#pragma unroll 4
+      for (int i = 0; i < 32; i++) {
+        const uint32_t ni = __shfl_sync(kFull, n, i), ji = __shfl_sync(kFull, j0, i);
+        const uint32_t di = __shfl_sync(kFull, dm1, i);
+        if (k < ni) {
+          const uint32_t a = W.a[i * kPitch + lane];
+          F.keys[ji + k] = (uint16_t)(a & 0xFFFFu);
+          F.kf_pad[ji + k] = (uint16_t)(a >> 16);
+          F.kf_time[ji + k] = W.b[i * kPitch + lane];
+        }
+        if (more && kn < ni) {
+          const uint32_t d = di + kn;
+          W.a[i * kPitch + lane] = (uint32_t)F.row_diff[d] | ((uint32_t)F.sld[d] << 8) |
+                                   ((uint32_t)F.pad_res[d] << 16);
+          W.b[i * kPitch + lane] = F.time_res[d];
+        }
+      }
+      __syncwarp();
+    }
+    st = __reduce_or_sync(kFull, st);
+    if (st && lane == 0) atomicOr(F.status, st);
   }
 }
 
+// One thread per attached cluster, kScatPerThread clusters per thread at a
+// stride of the block size (coalesced reads).  Blocks cover kTile /
+// kScatBlocksPerTile consecutive clusters of one ranking tile.
+__global__ void __launch_bounds__(kScatThreads) k_att_scatter(const FrameDev* frames,
+                                                              PlanDev plan) {
+  const uint32_t gtile = blockIdx.x / kScatBlocksPerTile;
+  const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
+  const FrameDev& F = frames[f];
+  if (*F.status & kStCount) return;
+  const uint32_t tile = gtile - plan.pre_tile[f];
+  const uint32_t jb = tile * (uint32_t)kTile +
+                      (blockIdx.x % kScatBlocksPerTile) * (uint32_t)(kTile / kScatBlocksPerTile);
+  const uint32_t* tb = F.tile_base + (size_t)tile * kNBin;
+  const uint32_t n_att = F.n_att, n_total = F.n_att + F.n_unatt;
+  uint32_t st = 0;
+  uint32_t w0[kScatPerThread], w1[kScatPerThread], w2[kScatPerThread], pos[kScatPerThread];
+#pragma unroll
+  for (int u = 0; u < kScatPerThread; u++) {
+    const uint32_t j = jb + u * kScatThreads + threadIdx.x;
+    pos[u] = 0xFFFFFFFFu;
+    if (j < n_att) {
+      const uint32_t key = __ldg(F.keys + j);
+      const uint32_t rk = __ldg(F.rank + j);
+      w0[u] = (__ldg(F.kf_time + j) & 0xFFFFFFu) | ((uint32_t)__ldg(F.flags_a + j) << 24);
+      w1[u] = (uint32_t)__ldg(F.kf_pad + j) | ((uint32_t)__ldg(F.sigt_a + j) << 16) |
+              ((uint32_t)__ldg(F.sigp_a + j) << 24);
+      w2[u] = (uint32_t)__ldg(F.qmax_a + j) | ((uint32_t)__ldg(F.qtot_a + j) << 16);
+      pos[u] = __ldg(tb + key) + rk;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kScatPerThread; u++) {
+    const uint32_t j = jb + u * kScatThreads + threadIdx.x;
+    if (j < n_att) {
+      if (pos[u] < n_total) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(F.native + (size_t)pos[u] * kRecBytes);
+        if ((pos[u] & 1u) == 0) {  // record starts on an 8-byte boundary
+          *reinterpret_cast<uint2*>(dst) = make_uint2(w0[u], w1[u]);
+          dst[2] = w2[u];
+        } else {
+          dst[0] = w0[u];
+          *reinterpret_cast<uint2*>(dst + 1) = make_uint2(w1[u], w2[u]);
+        }
+      } else {
+        st |= kStLimit;
+      }
+    }
+  }
+  if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(F.status, kStLimit);
+}
+
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_items) {
+                         PlanDev plan, uint32_t n_tasks) {
   switch (variant) {
-    case 0: k_track_decode<4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_items); break;
-    case 2: k_track_decode<6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_items); break;
-    case 3: k_track_decode<8><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_items); break;
-    default: k_track_decode<5><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_items); break;
+    case 0: k_track_decode<3><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 2: k_track_decode<5><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 3: k_track_decode<6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    default: k_track_decode<4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
   }
 }
 
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm) {
   switch (variant) {
-    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<4>, kDecodeThreads, 0);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<6>, kDecodeThreads, 0);
-    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<8>, kDecodeThreads, 0);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<5>, kDecodeThreads, 0);
+    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<3>, kDecodeThreads, 0);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<5>, kDecodeThreads, 0);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<6>, kDecodeThreads, 0);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<4>, kDecodeThreads, 0);
   }
 }
 

@@ -19,6 +19,9 @@ constexpr int kBinBlocks = (kNBin + kBinBlk - 1) / kBinBlk;
 constexpr int kChunk = 2048;             // unattached clusters per scan chunk
 constexpr int kLenBuckets = 1024;        // track-length buckets of the decode order
 constexpr int kDecodeThreads = 128;      // threads per block of the track decoder
+constexpr int kScatThreads = 256;        // threads per block of the record scatter
+constexpr int kScatPerThread = 8;        // clusters per thread of the record scatter
+constexpr int kScatBlocksPerTile = kTile / (kScatThreads * kScatPerThread);
 
 // One frame as the kernels see it: caller inputs, caller outputs, scratch.
 struct FrameDev {
@@ -62,6 +65,8 @@ struct FrameDev {
   uint32_t* order;         // n_tracks, longest tracks first
   uint32_t* heads;         // bit j set iff a track starts at attached cluster j
   uint16_t* keys;          // n_att: (sector,row) bin of every attached cluster
+  uint16_t* kf_pad;        // n_att: decoded pad code of every attached cluster
+  uint32_t* kf_time;       // n_att: decoded time code of every attached cluster
   uint16_t* rank;          // n_att: rank of a cluster within its (tile, bin)
   uint16_t* tile_hist;     // n_tiles x kNBin
   uint32_t* group_sum;     // n_groups x kNBin
@@ -101,10 +106,10 @@ struct PlanDev {
   const uint32_t* pre_tblk;   // track-scan blocks
   const uint32_t* pre_tile;   // ranking tiles
   const uint32_t* pre_grp;    // tile-group blocks (n_groups * kBinBlocks)
-  const uint32_t* pre_warp;   // decoder: attached clusters; encoder: warp tasks of 32 tracks
+  const uint32_t* pre_warp;   // encoder: warp tasks of 32 tracks
   const uint32_t* pre_chunk;  // unattached chunks
-  const uint32_t* pre_kt;     // key tasks: warps of 32 tracks
-  uint32_t* counters;         // [0] decode task, [1] unattached ticket (zeroed)
+  const uint32_t* pre_kt;     // decoder: warp tasks of 32 tracks
+  uint32_t* counters;         // [0] decode/encode task, [1] unattached ticket (zeroed)
 };
 
 // Largest f with pre[f] <= item (pre has n+1 entries, pre[0] = 0).
@@ -133,19 +138,19 @@ __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames);
 __global__ void k_track_scan1(const FrameDev* frames, PlanDev plan);
 __global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);
 __global__ void k_track_scan2(const FrameDev* frames, PlanDev plan);
-__global__ void k_keys(const FrameDev* frames, PlanDev plan, uint32_t n_tasks);
 __global__ void k_count_rank(const FrameDev* frames, PlanDev plan);
 __global__ void k_group_sum(const FrameDev* frames, PlanDev plan);
 __global__ void k_row_offsets(const FrameDev* frames, PlanDev plan);
 __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
 // The track decoder is instantiated for four register budgets (variant 0..3:
-// at least 4, 5, 6, 8 resident blocks per SM; a tuning parameter, every
+// at least 3, 4, 5, 6 resident blocks per SM; a tuning parameter, every
 // instance computes identical results); host code launches it through these
-// two functions.  It splits the attached clusters of all frames evenly over
-// its blocks (pre_warp of the plan holds the prefix of the frames' counts).
+// two functions.  Its warps take tasks of 32 tracks (pre_kt of the plan) from
+// counters[0].
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_tiles);
+                         PlanDev plan, uint32_t n_tasks);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
+__global__ void k_att_scatter(const FrameDev* frames, PlanDev plan);
 __global__ void k_unatt_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tickets);
 __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
                                uint32_t n_tasks);

@@ -79,7 +79,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     char msg[256];
     snprintf(msg, sizeof msg,
              "frame needs %zu bytes of scratch; tmd_decode_frame_noalloc is limited to %zu bytes "
-             "(64 MiB, about 12 M attached clusters); use tmd_decode_frame",
+             "(64 MiB, about 5 M attached clusters); use tmd_decode_frame",
              need, kScratchMax);
     set_err(err, err_len, msg);
     return TMD_ERR_ARG;
@@ -139,6 +139,8 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.track_start = reinterpret_cast<uint32_t*>(pb + L.track_start);
   F.order = reinterpret_cast<uint32_t*>(pb + L.order);
   F.keys = reinterpret_cast<uint16_t*>(pb + L.keys);
+  F.kf_pad = reinterpret_cast<uint16_t*>(pb + L.kf_pad);
+  F.kf_time = reinterpret_cast<uint32_t*>(pb + L.kf_time);
   F.rank = reinterpret_cast<uint16_t*>(pb + L.rank);
   F.tile_hist = reinterpret_cast<uint16_t*>(pb + L.tile_hist);
   F.group_sum = reinterpret_cast<uint32_t*>(pb + L.group_sum);
@@ -146,9 +148,9 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.unatt_start = reinterpret_cast<uint32_t*>(pb + L.unatt_start);
   F.blk_sum = reinterpret_cast<uint32_t*>(pb + L.blk_sum);
   const uint32_t n_tblk = L.n_tblocks, n_tile = L.n_tiles, n_grp = L.n_groups * kBinBlocks;
-  const uint32_t n_warp = in->n_attached;  // the decoder's blocks split the clusters
+  const uint32_t n_kt = (in->n_tracks + 31) / 32;  // decoder warp tasks
+  const uint32_t n_warp = n_kt;
   const uint32_t n_chunk = L.n_chunks;
-  const uint32_t n_kt = (in->n_tracks + 31) / 32;
   FrameDev* dframe = reinterpret_cast<FrameDev*>(rec);
   uint32_t* dpre = reinterpret_cast<uint32_t*>(rec + 1024);
   PlanDev P;
@@ -171,18 +173,15 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   k_frame_scan<<<1, 1024, 0, st>>>(dframe, P);
   if (n_tblk) k_track_scan2<<<n_tblk, 256, 0, st>>>(dframe, P);
   if (n_kt) {
-    const uint32_t cap = (uint32_t)(S->sms * 8);
-    k_keys<<<n_kt / 8 + 1 < cap ? n_kt / 8 + 1 : cap, 256, 0, st>>>(dframe, P, n_kt);
+    const uint32_t cap = (uint32_t)(S->sms * S->occ_decode);
+    const uint32_t want = (n_kt + kDecodeThreads / 32 - 1) / (kDecodeThreads / 32);
+    launch_track_decode(0, want < cap ? want : cap, st, dframe, P, n_kt);
   }
   if (n_tile) k_count_rank<<<n_tile, 256, kCountRankSmem, st>>>(dframe, P);
   if (n_grp) k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
   k_row_offsets<<<1, 1024, 0, st>>>(dframe, P);
   if (n_grp) k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
-  if (n_warp) {
-    const uint32_t cap = (uint32_t)(S->sms * S->occ_decode);
-    const uint32_t want = (n_warp + 4095) / 4096;
-    launch_track_decode(0, want < cap ? want : cap, st, dframe, P, n_warp);
-  }
+  if (n_tile) k_att_scatter<<<n_tile * kScatBlocksPerTile, kScatThreads, 0, st>>>(dframe, P);
   if (n_chunk) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_unatt);
     k_unatt_decode<<<n_chunk < cap ? n_chunk : cap, 256, 0, st>>>(dframe, P, n_chunk);
