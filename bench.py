@@ -172,6 +172,14 @@ def kernel_bytes(name, nt, na, nu):
     return table.get(name)
 
 
+def _apply_tune(dec, settings):
+    """Tuning settings given as key=value on the command line (after the
+    autotuner, which they override)."""
+    for kv in settings or []:
+        k, v = kv.split("=", 1)
+        dec.tmd_tune_set(k, int(v))
+
+
 def _kernel_entry(name, v, prof, nt, na, nu, peak):
     ms = v[0] / v[1]
     e = {"ms_per_launch": ms, "share": v[0] / max(1e-9, sum(x[0] for x in prof.values())),
@@ -254,7 +262,9 @@ def run(args):
     assert int(enc["status"].item()) == 0, "encoder status"
     if not args.no_autotune:
         dec.tmd_autotune([fin], [fout], stream)
-    tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "decode_blocks_per_sm",
+    _apply_tune(dec, args.tune)
+    tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
+                                              "scatter_variant", "decode_blocks_per_sm",
                                               "unatt_blocks_per_sm")}
     for _ in range(args.warmup):
         dec.tmd_decode_frame(fin, fout, stream)
@@ -413,6 +423,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     if not args.no_autotune:
         dec.tmd_autotune(fins[:8], fouts[:8], stream)
+    _apply_tune(dec, args.tune)
 
     def timeit(fn, reps):
         for _ in range(3):
@@ -553,6 +564,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune", action="append", metavar="KEY=VALUE",
+                    help="set a tuning parameter (after autotuning), e.g. decode_variant=2")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling runs only; the bench line uses 1.0)")
     args = ap.parse_args()

@@ -238,9 +238,19 @@ int tmd_poll(tmd_handle* h, uint64_t req_id, uint32_t timeout_us, tmd_frame_out*
 /* Free the buffers of a finished request. */
 int tmd_release(tmd_handle* h, uint64_t req_id);
 
-/* Tuning.  Parameters change launch shapes only, never results:
- *   "decode_variant"      0..3  register budget of the track decoder
- *                               (at least 3, 4, 5, 6 resident blocks per SM)
+/* Tuning.  Parameters change how work is laid out, never results:
+ *   "decode_variant"      0..3  staging of the track decoder: rounds of 32 or
+ *                               16 model steps staged synchronously (0, 1), or
+ *                               rounds of 8 or 16 steps double-buffered with
+ *                               asynchronous copies (2, 3)
+ *   "rank_variant"        0..1  ranking of equal keys: match.any on every
+ *                               step (0) or only on steps with repeated keys,
+ *                               found with a shared-memory bitmap (1)
+ *   "scatter_variant"     0..2  loads of the record scatter: clusters at a
+ *                               stride of the block (0), 8 consecutive
+ *                               clusters per thread with vector loads and the
+ *                               bin bases in shared memory (1) or read
+ *                               through L1 (2)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
  * tmd_autotune times the decode chain on the given frames (device buffers,

@@ -100,7 +100,6 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
   L.n_chunks = ceil_div(nu, kChunk);
   auto z = [&](size_t bytes) { size_t o = zoff; zoff = align_up(zoff + bytes, 256); return o; };
   auto p = [&](size_t bytes) { size_t o = poff; poff = align_up(poff + bytes, 256); return o; };
-  L.z_heads = z(((size_t)na / 32 + 32) * 4);
   L.z_len = z((size_t)kLenBuckets * 4);
   L.z_lb = z((size_t)L.n_chunks * 8 + 8);
   L.track_start = p(((size_t)nt + 1) * 4);
@@ -191,9 +190,7 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
   int rc = TMD_OK;
   if ((rc = tmd_cuda_check(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount,
                                                     h->device), "sm count")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, cudaFuncSetAttribute(k_count_rank,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kCountRankSmem), "smem attribute")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, prepare_count_rank(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(0, &h->occ_decode_v[0]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(2, &h->occ_decode_v[2]), "occupancy")) != TMD_OK ||
@@ -420,7 +417,6 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     }
     F.n_tblocks = l.n_tblocks; F.n_tiles = l.n_tiles; F.n_groups = l.n_groups;
     F.n_chunks = l.n_chunks;
-    F.heads = reinterpret_cast<uint32_t*>(zb + l.z_heads);
     F.len_cursor = reinterpret_cast<uint32_t*>(zb + l.z_len);
     F.lookback = reinterpret_cast<unsigned long long*>(zb + l.z_lb);
     F.track_start = reinterpret_cast<uint32_t*>(pb + l.track_start);
@@ -492,13 +488,13 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt); });
     }
     if (n_tile)
-      timed(kKCountRank, [&] { k_count_rank<<<n_tile, 256, kCountRankSmem, st>>>(dframes, P); });
+      timed(kKCountRank, [&] { launch_count_rank(h->tune_rank_variant, n_tile, st, dframes, P); });
     if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
     if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     if (n_tile)
       timed(kKAttScatter, [&] {
-        k_att_scatter<<<n_tile * kScatBlocksPerTile, kScatThreads, 0, st>>>(dframes, P);
+        launch_att_scatter(h->tune_scatter_variant, n_tile * kScatBlocksPerTile, st, dframes, P);
       });
     if (n_chunk) {
       int bps = h->occ_unatt;

@@ -45,7 +45,9 @@ struct tmd_handle {
   int occ_decode = 1, occ_unatt = 1, occ_encode = 1;
   int occ_decode_v[4] = {1, 1, 1, 1};  // resident blocks per SM of each decoder variant
   // tuning parameters (launch shapes only; results never depend on them)
-  int tune_decode_variant = 1;   // register-budget variant of the track decoder
+  int tune_decode_variant = 1;   // staging-round variant of the track decoder
+  int tune_rank_variant = 1;     // duplicate-key handling of the ranking kernel
+  int tune_scatter_variant = 0;  // load pattern of the record scatter
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;
@@ -76,7 +78,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
 // Scratch layout of one frame.  The zeroed part of all frames is contiguous.
 struct FrameLayout {
   uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
-  size_t z_heads, z_len, z_lb;                    // offsets in the zeroed part
+  size_t z_len, z_lb;                             // offsets in the zeroed part
   size_t track_start, order, keys, kf_pad, kf_time, rank, tile_hist, group_sum, tile_base,
       unatt_start, blk_sum, att_count;            // offsets in the plain part
 };

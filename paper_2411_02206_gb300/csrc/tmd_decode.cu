@@ -22,12 +22,14 @@
 // The lane-per-track walk reads each stream at 32 unrelated positions per
 // warp.  Read directly, every lane pulls whole sectors for a few bytes and
 // the L2 has to hold one line per lane and stream until the lane has walked
-// past it.  k_track_decode therefore moves data in rounds of kRound steps:
-// the warp stages the differences of the next kRound clusters of each of its
-// 32 tracks in shared memory with coalesced loads (one instruction loads 32
-// consecutive elements of one track), the lanes run the model from shared
-// memory, and the round's outputs leave through the same buffer with
-// coalesced stores.
+// past it.  k_track_decode therefore moves data in rounds of R steps (R = 32,
+// 16 or 8, a tuning variant): the warp stages the differences of the next R
+// clusters of each of its 32 tracks in shared memory with coalesced loads
+// (one instruction loads R consecutive elements of each of 32 / R tracks),
+// the lanes run the model from shared memory, and the round's outputs leave
+// through the same buffer with coalesced stores.  Shorter rounds need less
+// shared memory (more resident warps) but pay the staging overhead more
+// often.
 //
 // Encoder: the same walk with the truth as measurement; it writes the header
 // and the residual streams (the synchronous side of the method).
@@ -44,32 +46,37 @@ __device__ __forceinline__ uint32_t next_task(uint32_t* counter) {
 }
 
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr int kRound = 32;        // model steps per staging round
-constexpr int kPitch = kRound + 1;  // words per track row of a staging buffer
 
-// Staging buffers of one warp: for track-lane i and step q of the round,
+// Staging buffers of one warp for rounds of R steps: for track-lane i and
+// step q of the round,
 //   a[i][q] = row_diff | sld << 8 | pad_res << 16   (in)
 //             key | pad << 16                        (out)
 //   b[i][q] = time_res (in) / time (out)
-// Rows are padded to kPitch words: the coalesced fill (fixed i, q = lane)
-// and the model's reads (fixed q, i = lane) are both free of bank conflicts.
+// Rows are padded to R + 1 words: the coalesced fill (32 / R tracks per
+// instruction, consecutive q in consecutive lanes) and the model's reads
+// (fixed q, i = lane) are free of bank conflicts.
+template <int R>
 struct WarpStage {
-  uint32_t a[32 * kPitch];
-  uint32_t b[32 * kPitch];
+  uint32_t a[32 * (R + 1)];
+  uint32_t b[32 * (R + 1)];
 };
 
 }  // namespace
 
-template <int MINB>
+template <int R, int MINB>
 __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const FrameDev* frames,
                                                                        PlanDev plan,
                                                                        uint32_t n_tasks) {
+  static_assert(R == 8 || R == 16 || R == 32, "round length divides the warp");
+  constexpr int P = R + 1;   // pitch of a staging row
+  constexpr int G = 32 / R;  // tracks per staging instruction
   __shared__ RowGeo geo;
-  __shared__ WarpStage stage[kDecodeThreads / 32];
+  __shared__ WarpStage<R> stage[kDecodeThreads / 32];
   fill_row_geo(&geo);
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31;
-  WarpStage& W = stage[threadIdx.x >> 5];
+  const uint32_t sq = lane % R, sg = lane / R;  // staging: step and track offset of the lane
+  WarpStage<R>& W = stage[threadIdx.x >> 5];
   for (;;) {
     const uint32_t task = next_task(&plan.counters[0]);
     if (task >= n_tasks) break;
@@ -77,6 +84,15 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const Fra
     const FrameDev& F = frames[f];
     if (*F.status & kStCount) continue;
     const uint32_t idx = (task - plan.pre_kt[f]) * 32u + lane;
+    // the frame's streams, held in registers for the task (the stores below
+    // cannot alias them)
+    const uint8_t* __restrict__ rd_s = F.row_diff;
+    const uint8_t* __restrict__ sld_s = F.sld;
+    const uint16_t* __restrict__ pr_s = F.pad_res;
+    const uint32_t* __restrict__ tr_s = F.time_res;
+    uint16_t* __restrict__ key_o = F.keys;
+    uint16_t* __restrict__ pad_o = F.kf_pad;
+    uint32_t* __restrict__ time_o = F.kf_time;
     // the lane's track: first cluster j0, n clusters, differences from d0
     uint32_t j0 = 0, n = 0, dm1 = 0, pad0 = 0, time0 = 0, st = 0;
     Track s;
@@ -95,18 +111,19 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const Fra
     const uint32_t nmax = __reduce_max_sync(kFull, n);
     // stage round 0 (cluster 0 is stored absolute: differences from k = 1)
 #pragma unroll 4
-    for (int i = 0; i < 32; i++) {
+    for (int i0 = 0; i0 < 32; i0 += G) {
+      const uint32_t i = i0 + sg;
       const uint32_t ni = __shfl_sync(kFull, n, i), di = __shfl_sync(kFull, dm1, i);
-      if (lane >= 1 && lane < ni) {
-        const uint32_t d = di + lane;
-        W.a[i * kPitch + lane] = (uint32_t)F.row_diff[d] | ((uint32_t)F.sld[d] << 8) |
-                                 ((uint32_t)F.pad_res[d] << 16);
-        W.b[i * kPitch + lane] = F.time_res[d];
+      if (sq >= 1 && sq < ni) {
+        const uint32_t d = di + sq;
+        W.a[i * P + sq] = (uint32_t)rd_s[d] | ((uint32_t)sld_s[d] << 8) |
+                          ((uint32_t)pr_s[d] << 16);
+        W.b[i * P + sq] = tr_s[d];
       }
     }
     __syncwarp();
-    for (uint32_t k0 = 0; k0 < nmax; k0 += kRound) {
-      const uint32_t qn = nmax - k0 < (uint32_t)kRound ? nmax - k0 : (uint32_t)kRound;
+    for (uint32_t k0 = 0; k0 < nmax; k0 += R) {
+      const uint32_t qn = nmax - k0 < (uint32_t)R ? nmax - k0 : (uint32_t)R;
       const uint32_t rem = n > k0 ? n - k0 : 0u;  // steps of this lane in the round
       for (uint32_t q = 0; q < qn; q++) {
         if (q < rem) {
@@ -115,7 +132,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const Fra
             padq = pad0;
             timeq = time0;
           } else {
-            const uint32_t a = W.a[lane * kPitch + q], tr = W.b[lane * kPitch + q];
+            const uint32_t a = W.a[lane * P + q], tr = W.b[lane * P + q];
             st |= key_step(s, a & 255u, (a >> 8) & 255u);
             uint32_t ppad, ptime;
             propagate_predict(&geo, s, ppad, ptime);
@@ -124,43 +141,252 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const Fra
             update(&geo, s, padq, timeq);
           }
           if (timeq > 0xFFFFFFu) st |= kStTime;
-          W.a[lane * kPitch + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
-          W.b[lane * kPitch + q] = timeq;
+          W.a[lane * P + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
+          W.b[lane * P + q] = timeq;
         }
       }
       __syncwarp();
       // write this round's outputs and stage the next round's differences
-      const uint32_t k = k0 + lane, kn = k + kRound;
-      const bool more = k0 + kRound < nmax;
+      const uint32_t k = k0 + sq, kn = k + R;
+      const bool more = k0 + R < nmax;
 #pragma unroll 4
-      for (int i = 0; i < 32; i++) {
+      for (int i0 = 0; i0 < 32; i0 += G) {
+        const uint32_t i = i0 + sg;
         const uint32_t ni = __shfl_sync(kFull, n, i), ji = __shfl_sync(kFull, j0, i);
         const uint32_t di = __shfl_sync(kFull, dm1, i);
         if (k < ni) {
-          const uint32_t a = W.a[i * kPitch + lane];
-          F.keys[ji + k] = (uint16_t)(a & 0xFFFFu);
-          F.kf_pad[ji + k] = (uint16_t)(a >> 16);
-          F.kf_time[ji + k] = W.b[i * kPitch + lane];
+          const uint32_t a = W.a[i * P + sq];
+          key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
+          pad_o[ji + k] = (uint16_t)(a >> 16);
+          time_o[ji + k] = W.b[i * P + sq];
         }
         if (more && kn < ni) {
           const uint32_t d = di + kn;
-          W.a[i * kPitch + lane] = (uint32_t)F.row_diff[d] | ((uint32_t)F.sld[d] << 8) |
-                                   ((uint32_t)F.pad_res[d] << 16);
-          W.b[i * kPitch + lane] = F.time_res[d];
+          W.a[i * P + sq] = (uint32_t)rd_s[d] | ((uint32_t)sld_s[d] << 8) |
+                            ((uint32_t)pr_s[d] << 16);
+          W.b[i * P + sq] = tr_s[d];
         }
       }
       __syncwarp();
     }
     st = __reduce_or_sync(kFull, st);
-    if (st && lane == 0) atomicOr(F.status, st);
+    if (st && lane == 0) atomicOr(frames[f].status, st);
   }
 }
 
-// One thread per attached cluster, kScatPerThread clusters per thread at a
-// stride of the block size (coalesced reads).  Blocks cover kTile /
-// kScatBlocksPerTile consecutive clusters of one ranking tile.
-__global__ void __launch_bounds__(kScatThreads) k_att_scatter(const FrameDev* frames,
-                                                              PlanDev plan) {
+// ---------------------------------------------------------------------------
+// Asynchronous staging.  Each lane copies its own track's next round of
+// differences into its own part of a double buffer with cp.async (4-byte
+// copies of the aligned words that hold the round's elements, which lie in
+// the caller's allocation), so the copies of round r + 1 are in flight while
+// the lane runs the model through round r, and no lane waits for another
+// lane's copies.  The round's outputs still leave through shared memory with
+// coalesced stores.
+namespace {
+
+__device__ __forceinline__ void cp_word(const uint32_t* dst_smem, uintptr_t src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Words per lane and buffer: row_diff and sld (R bytes at any alignment),
+// pad_res (R u16 at any 2-byte alignment), time_res (R words, one per step).
+template <int R>
+struct AsyncLayout {
+  static constexpr int kRd = R / 4 + 1;
+  static constexpr int kPr = R / 2 + 1;
+  static constexpr int kTr0 = 2 * kRd + kPr;   // first time_res word
+  static constexpr int kLane = kTr0 + R;       // odd: lanes hit distinct banks
+};
+
+template <int R>
+struct AsyncStage {
+  uint32_t buf[2][32 * AsyncLayout<R>::kLane];
+  uint32_t kp[32 * (R + 1)];  // outputs key | pad << 16 of the round
+};
+
+// Element offsets of step 0 of a round inside a lane's buffer (negative in
+// round 0, whose step 0 has no difference).
+struct RoundBase {
+  int rd, sl, pr;
+};
+
+// Issue the copies of the differences of steps [k0, k0 + R) of one track
+// (cluster k uses difference dm1 + k; cluster 0 has none) into lane buffer lb.
+template <int R>
+__device__ __forceinline__ RoundBase issue_round(uint32_t* lb, uint32_t k0, uint32_t n,
+                                                 uint32_t dm1, const uint8_t* rd_s,
+                                                 const uint8_t* sld_s, const uint16_t* pr_s,
+                                                 const uint32_t* tr_s) {
+  using Lay = AsyncLayout<R>;
+  RoundBase rb{0, 0, 0};
+  const uint32_t k_lo = k0 > 1u ? k0 : 1u;
+  const uint32_t k_hi = k0 + R < n ? k0 + R : n;
+  if (k_lo >= k_hi) return rb;
+  const uint32_t x_lo = dm1 + k_lo, x_hi = dm1 + k_hi;  // differences [x_lo, x_hi)
+  const int skip = (int)(k_lo - k0);                    // 1 in round 0, else 0
+  {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(rd_s + x_lo);
+    const uintptr_t e = reinterpret_cast<uintptr_t>(rd_s + x_hi);
+    const uintptr_t w = a & ~(uintptr_t)3;
+#pragma unroll
+    for (int c = 0; c < Lay::kRd; c++)
+      if (w + 4 * c < e) cp_word(lb + c, w + 4 * c);
+    rb.rd = (int)(a - w) - skip;
+  }
+  {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(sld_s + x_lo);
+    const uintptr_t e = reinterpret_cast<uintptr_t>(sld_s + x_hi);
+    const uintptr_t w = a & ~(uintptr_t)3;
+#pragma unroll
+    for (int c = 0; c < Lay::kRd; c++)
+      if (w + 4 * c < e) cp_word(lb + Lay::kRd + c, w + 4 * c);
+    rb.sl = (int)(a - w) - skip;
+  }
+  {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(pr_s + x_lo);
+    const uintptr_t e = reinterpret_cast<uintptr_t>(pr_s + x_hi);
+    const uintptr_t w = a & ~(uintptr_t)3;
+#pragma unroll
+    for (int c = 0; c < Lay::kPr; c++)
+      if (w + 4 * c < e) cp_word(lb + 2 * Lay::kRd + c, w + 4 * c);
+    rb.pr = (int)((a - w) >> 1) - skip;
+  }
+#pragma unroll
+  for (int c = 0; c < R; c++)
+    if (x_lo + c < x_hi)
+      cp_word(lb + Lay::kTr0 + skip + c, reinterpret_cast<uintptr_t>(tr_s + x_lo + c));
+  return rb;
+}
+
+}  // namespace
+
+template <int R, int MINB>
+__global__ void __launch_bounds__(kDecodeThreads, MINB)
+    k_track_decode_async(const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
+  static_assert(R == 8 || R == 16, "round length");
+  using Lay = AsyncLayout<R>;
+  constexpr int P = R + 1;   // pitch of the output rows
+  constexpr int G = 32 / R;  // tracks per write-out instruction
+  __shared__ RowGeo geo;
+  __shared__ AsyncStage<R> stage[kDecodeThreads / 32];
+  fill_row_geo(&geo);
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t sq = lane % R, sg = lane / R;
+  AsyncStage<R>& S = stage[threadIdx.x >> 5];
+  for (;;) {
+    const uint32_t task = next_task(&plan.counters[0]);
+    if (task >= n_tasks) break;
+    const uint32_t f = find_frame(plan.pre_kt, plan.n_frames, task);
+    const FrameDev& F = frames[f];
+    if (*F.status & kStCount) continue;
+    const uint32_t idx = (task - plan.pre_kt[f]) * 32u + lane;
+    const uint8_t* __restrict__ rd_s = F.row_diff;
+    const uint8_t* __restrict__ sld_s = F.sld;
+    const uint16_t* __restrict__ pr_s = F.pad_res;
+    const uint32_t* __restrict__ tr_s = F.time_res;
+    uint16_t* __restrict__ key_o = F.keys;
+    uint16_t* __restrict__ pad_o = F.kf_pad;
+    uint32_t* __restrict__ time_o = F.kf_time;
+    uint32_t j0 = 0, n = 0, dm1 = 0, pad0 = 0, time0 = 0, st = 0;
+    Track s;
+    if (idx < F.n_tracks) {
+      const uint32_t t = F.order[idx];
+      j0 = F.track_start[t];
+      n = F.ncl[t];
+      dm1 = j0 - t - 1u;
+      pad0 = F.pad[t];
+      time0 = F.time[t];
+      const uint32_t raw = F.row[t], sec = F.slice[t];
+      if (raw >= (uint32_t)kNRow || sec >= (uint32_t)kNSec) st |= kStRow;
+      seed(&geo, s, F.qpt[t], (int)raw, sec < (uint32_t)kNSec ? (int)sec : kNSec - 1, pad0,
+           time0);
+    }
+    const uint32_t nmax = __reduce_max_sync(kFull, n);
+    const uint32_t n_rounds = (nmax + R - 1) / R;
+    uint32_t* lb0 = S.buf[0] + lane * Lay::kLane;
+    uint32_t* lb1 = S.buf[1] + lane * Lay::kLane;
+    RoundBase cur = issue_round<R>(lb0, 0u, n, dm1, rd_s, sld_s, pr_s, tr_s);
+    cp_commit();
+    for (uint32_t r = 0; r < n_rounds; r++) {
+      const uint32_t k0 = r * R;
+      uint32_t* lb = (r & 1) ? lb1 : lb0;
+      RoundBase nxt{0, 0, 0};
+      if (r + 1 < n_rounds) {
+        nxt = issue_round<R>((r & 1) ? lb0 : lb1, k0 + R, n, dm1, rd_s, sld_s, pr_s, tr_s);
+        cp_commit();
+        cp_wait<1>();
+      } else {
+        cp_wait<0>();
+      }
+      const uint32_t rem = n > k0 ? n - k0 : 0u;
+#pragma unroll 1
+      for (uint32_t q = 0; q < (uint32_t)R; q++) {
+        if (q < rem) {
+          uint32_t padq, timeq;
+          if (k0 + q == 0) {
+            padq = pad0;
+            timeq = time0;
+          } else {
+            const int prd = cur.rd + (int)q, psl = cur.sl + (int)q, ppr = cur.pr + (int)q;
+            const uint32_t rdv = (lb[prd >> 2] >> (8 * (prd & 3))) & 255u;
+            const uint32_t slv = (lb[Lay::kRd + (psl >> 2)] >> (8 * (psl & 3))) & 255u;
+            const uint32_t prv = (lb[2 * Lay::kRd + (ppr >> 1)] >> (16 * (ppr & 1))) & 0xFFFFu;
+            st |= key_step(s, rdv, slv);
+            uint32_t ppad, ptime;
+            propagate_predict(&geo, s, ppad, ptime);
+            padq = (ppad + prv) & 0xFFFFu;
+            timeq = ptime + lb[Lay::kTr0 + q];
+            update(&geo, s, padq, timeq);
+          }
+          if (timeq > 0xFFFFFFu) st |= kStTime;
+          S.kp[lane * P + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
+          lb[Lay::kTr0 + q] = timeq;
+        }
+      }
+      __syncwarp();
+      const uint32_t k = k0 + sq;
+      const uint32_t* bb = (r & 1) ? S.buf[1] : S.buf[0];
+#pragma unroll
+      for (int i0 = 0; i0 < 32; i0 += G) {
+        const uint32_t i = i0 + sg;
+        const uint32_t ni = __shfl_sync(kFull, n, i), ji = __shfl_sync(kFull, j0, i);
+        if (k < ni) {
+          const uint32_t a = S.kp[i * P + sq];
+          key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
+          pad_o[ji + k] = (uint16_t)(a >> 16);
+          time_o[ji + k] = bb[i * Lay::kLane + Lay::kTr0 + sq];
+        }
+      }
+      __syncwarp();
+      cur = nxt;
+    }
+    st = __reduce_or_sync(kFull, st);
+    if (st && lane == 0) atomicOr(frames[f].status, st);
+  }
+}
+
+// k_att_scatter: kScatPerThread = 8 attached clusters per thread.  Variants
+// (identical results):
+//   V = 0  clusters at a stride of the block size (one scalar load per stream
+//          and cluster, consecutive lanes on consecutive clusters); bin bases
+//          read through L1;
+//   V = 1  8 consecutive clusters per thread, one vector load per stream
+//          (scalar loads when a caller array is not aligned for it); the
+//          tile's row of bin bases copied to shared memory first;
+//   V = 2  as V = 1, bin bases read through L1.
+// A block covers kScatThreads * 8 consecutive clusters of one ranking tile.
+template <int V>
+__global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev* frames,
+                                                                 PlanDev plan) {
+  static_assert(kScatPerThread == 8, "one 16-byte load per u16 stream");
+  __shared__ uint32_t s_tb[V == 1 ? kNBin : 1];
   const uint32_t gtile = blockIdx.x / kScatBlocksPerTile;
   const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
   const FrameDev& F = frames[f];
@@ -168,61 +394,146 @@ __global__ void __launch_bounds__(kScatThreads) k_att_scatter(const FrameDev* fr
   const uint32_t tile = gtile - plan.pre_tile[f];
   const uint32_t jb = tile * (uint32_t)kTile +
                       (blockIdx.x % kScatBlocksPerTile) * (uint32_t)(kTile / kScatBlocksPerTile);
-  const uint32_t* tb = F.tile_base + (size_t)tile * kNBin;
   const uint32_t n_att = F.n_att, n_total = F.n_att + F.n_unatt;
-  uint32_t st = 0;
-  uint32_t w0[kScatPerThread], w1[kScatPerThread], w2[kScatPerThread], pos[kScatPerThread];
+  const uint16_t* __restrict__ keys = F.keys;
+  const uint16_t* __restrict__ rank = F.rank;
+  const uint16_t* __restrict__ kpad = F.kf_pad;
+  const uint32_t* __restrict__ ktime = F.kf_time;
+  const uint16_t* __restrict__ qtot = F.qtot_a;
+  const uint16_t* __restrict__ qmax = F.qmax_a;
+  const uint8_t* __restrict__ flags = F.flags_a;
+  const uint8_t* __restrict__ sigp = F.sigp_a;
+  const uint8_t* __restrict__ sigt = F.sigt_a;
+  const uint32_t* __restrict__ tbase = F.tile_base + (size_t)tile * kNBin;
+  uint8_t* __restrict__ native = F.native;
+  if constexpr (V == 1) {
+    const uint4* tb = reinterpret_cast<const uint4*>(tbase);
+    for (int i = threadIdx.x; i < kNBin / 4; i += kScatThreads)
+      reinterpret_cast<uint4*>(s_tb)[i] = __ldg(tb + i);
+  }
+  // cluster u of this thread
+  auto cl = [&](int u) -> uint32_t {
+    return V == 0 ? jb + u * kScatThreads + threadIdx.x : jb + threadIdx.x * 8 + u;
+  };
+  // 8 clusters: keys, ranks, pad codes, charges as packed u16 pairs; time
+  // codes; flags and sigmas as packed bytes
+  uint32_t kw[4], rw[4], pw[4], tw[8], qtw[4], qmw[4], flw[2], spw[2], sgw[2];
+  const uint32_t j0 = jb + threadIdx.x * 8;
+  const bool full = V != 0 && j0 + 8 <= n_att;
+  const bool vec = full &&
+      ((reinterpret_cast<uintptr_t>(qtot) | reinterpret_cast<uintptr_t>(qmax)) & 15) == 0 &&
+      ((reinterpret_cast<uintptr_t>(flags) | reinterpret_cast<uintptr_t>(sigp) |
+        reinterpret_cast<uintptr_t>(sigt)) & 7) == 0;
+  if (full) {  // the scratch streams are always aligned
+    const uint4 a = *reinterpret_cast<const uint4*>(keys + j0);
+    const uint4 b = *reinterpret_cast<const uint4*>(rank + j0);
+    const uint4 c = *reinterpret_cast<const uint4*>(kpad + j0);
+    const uint4 d = *reinterpret_cast<const uint4*>(ktime + j0);
+    const uint4 e = *reinterpret_cast<const uint4*>(ktime + j0 + 4);
+    kw[0] = a.x; kw[1] = a.y; kw[2] = a.z; kw[3] = a.w;
+    rw[0] = b.x; rw[1] = b.y; rw[2] = b.z; rw[3] = b.w;
+    pw[0] = c.x; pw[1] = c.y; pw[2] = c.z; pw[3] = c.w;
+    tw[0] = d.x; tw[1] = d.y; tw[2] = d.z; tw[3] = d.w;
+    tw[4] = e.x; tw[5] = e.y; tw[6] = e.z; tw[7] = e.w;
+  } else {
 #pragma unroll
-  for (int u = 0; u < kScatPerThread; u++) {
-    const uint32_t j = jb + u * kScatThreads + threadIdx.x;
-    pos[u] = 0xFFFFFFFFu;
-    if (j < n_att) {
-      const uint32_t key = __ldg(F.keys + j);
-      const uint32_t rk = __ldg(F.rank + j);
-      w0[u] = (__ldg(F.kf_time + j) & 0xFFFFFFu) | ((uint32_t)__ldg(F.flags_a + j) << 24);
-      w1[u] = (uint32_t)__ldg(F.kf_pad + j) | ((uint32_t)__ldg(F.sigt_a + j) << 16) |
-              ((uint32_t)__ldg(F.sigp_a + j) << 24);
-      w2[u] = (uint32_t)__ldg(F.qmax_a + j) | ((uint32_t)__ldg(F.qtot_a + j) << 16);
-      pos[u] = __ldg(tb + key) + rk;
+    for (int h = 0; h < 4; h++) { kw[h] = 0u; rw[h] = 0u; pw[h] = 0u; }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint32_t j = cl(u);
+      tw[u] = 0u;
+      if (j < n_att) {
+        kw[u >> 1] |= (uint32_t)keys[j] << (16 * (u & 1));
+        rw[u >> 1] |= (uint32_t)rank[j] << (16 * (u & 1));
+        pw[u >> 1] |= (uint32_t)kpad[j] << (16 * (u & 1));
+        tw[u] = ktime[j];
+      }
     }
   }
+  if (vec) {
+    const uint4 a = *reinterpret_cast<const uint4*>(qtot + j0);
+    const uint4 b = *reinterpret_cast<const uint4*>(qmax + j0);
+    const uint2 c = *reinterpret_cast<const uint2*>(flags + j0);
+    const uint2 d = *reinterpret_cast<const uint2*>(sigp + j0);
+    const uint2 e = *reinterpret_cast<const uint2*>(sigt + j0);
+    qtw[0] = a.x; qtw[1] = a.y; qtw[2] = a.z; qtw[3] = a.w;
+    qmw[0] = b.x; qmw[1] = b.y; qmw[2] = b.z; qmw[3] = b.w;
+    flw[0] = c.x; flw[1] = c.y; spw[0] = d.x; spw[1] = d.y; sgw[0] = e.x; sgw[1] = e.y;
+  } else {
 #pragma unroll
-  for (int u = 0; u < kScatPerThread; u++) {
-    const uint32_t j = jb + u * kScatThreads + threadIdx.x;
+    for (int h = 0; h < 4; h++) { qtw[h] = 0u; qmw[h] = 0u; }
+#pragma unroll
+    for (int h = 0; h < 2; h++) { flw[h] = 0u; spw[h] = 0u; sgw[h] = 0u; }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint32_t j = cl(u);
+      if (j < n_att) {
+        qtw[u >> 1] |= (uint32_t)qtot[j] << (16 * (u & 1));
+        qmw[u >> 1] |= (uint32_t)qmax[j] << (16 * (u & 1));
+        flw[u >> 2] |= (uint32_t)flags[j] << (8 * (u & 3));
+        spw[u >> 2] |= (uint32_t)sigp[j] << (8 * (u & 3));
+        sgw[u >> 2] |= (uint32_t)sigt[j] << (8 * (u & 3));
+      }
+    }
+  }
+  if constexpr (V == 1) __syncthreads();
+  uint32_t st = 0;
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    const uint32_t j = cl(u);
     if (j < n_att) {
-      if (pos[u] < n_total) {
-        uint32_t* dst = reinterpret_cast<uint32_t*>(F.native + (size_t)pos[u] * kRecBytes);
-        if ((pos[u] & 1u) == 0) {  // record starts on an 8-byte boundary
-          *reinterpret_cast<uint2*>(dst) = make_uint2(w0[u], w1[u]);
-          dst[2] = w2[u];
+      const uint32_t h16 = 16 * (u & 1), h8 = 8 * (u & 3);
+      const uint32_t key = (kw[u >> 1] >> h16) & 0xFFFFu;
+      const uint32_t base = V == 1 ? s_tb[key] : __ldg(tbase + key);
+      const uint32_t p = base + ((rw[u >> 1] >> h16) & 0xFFFFu);
+      const uint32_t w0 = (tw[u] & 0xFFFFFFu) | (((flw[u >> 2] >> h8) & 0xFFu) << 24);
+      const uint32_t w1 = ((pw[u >> 1] >> h16) & 0xFFFFu) | (((sgw[u >> 2] >> h8) & 0xFFu) << 16) |
+                          (((spw[u >> 2] >> h8) & 0xFFu) << 24);
+      const uint32_t w2 = ((qmw[u >> 1] >> h16) & 0xFFFFu) | (((qtw[u >> 1] >> h16) & 0xFFFFu) << 16);
+      if (p < n_total) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(native + (size_t)p * kRecBytes);
+        if ((p & 1u) == 0) {  // record starts on an 8-byte boundary
+          *reinterpret_cast<uint2*>(dst) = make_uint2(w0, w1);
+          dst[2] = w2;
         } else {
-          dst[0] = w0[u];
-          *reinterpret_cast<uint2*>(dst + 1) = make_uint2(w1[u], w2[u]);
+          dst[0] = w0;
+          *reinterpret_cast<uint2*>(dst + 1) = make_uint2(w1, w2);
         }
       } else {
         st |= kStLimit;
       }
     }
   }
-  if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(F.status, kStLimit);
+  if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(frames[f].status, kStLimit);
 }
 
+void launch_att_scatter(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+                        PlanDev plan) {
+  switch (variant) {
+    case 1: k_att_scatter<1><<<grid, kScatThreads, 0, st>>>(frames, plan); break;
+    case 2: k_att_scatter<2><<<grid, kScatThreads, 0, st>>>(frames, plan); break;
+    default: k_att_scatter<0><<<grid, kScatThreads, 0, st>>>(frames, plan); break;
+  }
+}
+
+// Variants: 0 -> R = 32, 1 -> R = 16 (synchronous staging), 2 -> R = 8,
+// 3 -> R = 16 (asynchronous double-buffered staging).
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                          PlanDev plan, uint32_t n_tasks) {
   switch (variant) {
-    case 0: k_track_decode<3><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    case 2: k_track_decode<5><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    case 3: k_track_decode<6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    default: k_track_decode<4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 0: k_track_decode<32, 1><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 2: k_track_decode_async<8, 6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 3: k_track_decode_async<16, 4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    default: k_track_decode<16, 1><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
   }
 }
 
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm) {
   switch (variant) {
-    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<3>, kDecodeThreads, 0);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<5>, kDecodeThreads, 0);
-    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<6>, kDecodeThreads, 0);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<4>, kDecodeThreads, 0);
+    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<32, 1>, kDecodeThreads, 0);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<8, 6>, kDecodeThreads, 0);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<16, 4>, kDecodeThreads, 0);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<16, 1>, kDecodeThreads, 0);
   }
 }
 

@@ -63,7 +63,6 @@ struct FrameDev {
   // scratch
   uint32_t* track_start;   // n_tracks + 1
   uint32_t* order;         // n_tracks, longest tracks first
-  uint32_t* heads;         // bit j set iff a track starts at attached cluster j
   uint16_t* keys;          // n_att: (sector,row) bin of every attached cluster
   uint16_t* kf_pad;        // n_att: decoded pad code of every attached cluster
   uint32_t* kf_time;       // n_att: decoded time code of every attached cluster
@@ -138,23 +137,31 @@ __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames);
 __global__ void k_track_scan1(const FrameDev* frames, PlanDev plan);
 __global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);
 __global__ void k_track_scan2(const FrameDev* frames, PlanDev plan);
-__global__ void k_count_rank(const FrameDev* frames, PlanDev plan);
+// Ranking variants (identical results): 0 orders equal keys of a step with
+// match.any, 1 detects duplicate keys with a shared-memory bitmap and falls
+// back to match.any only for steps that have some.
+void launch_count_rank(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+                       PlanDev plan);
+cudaError_t prepare_count_rank();
 __global__ void k_group_sum(const FrameDev* frames, PlanDev plan);
 __global__ void k_row_offsets(const FrameDev* frames, PlanDev plan);
 __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
-// The track decoder is instantiated for four register budgets (variant 0..3:
-// at least 3, 4, 5, 6 resident blocks per SM; a tuning parameter, every
+// The track decoder is instantiated in four variants (staging rounds of 32,
+// 16, 8 steps, and 16 steps under a register cap; a tuning parameter, every
 // instance computes identical results); host code launches it through these
 // two functions.  Its warps take tasks of 32 tracks (pre_kt of the plan) from
 // counters[0].
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                          PlanDev plan, uint32_t n_tasks);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
-__global__ void k_att_scatter(const FrameDev* frames, PlanDev plan);
+// Record scatter variants 0..2 (identical results; see tmd_decode.cu).
+void launch_att_scatter(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+                        PlanDev plan);
 __global__ void k_unatt_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tickets);
 __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
                                uint32_t n_tasks);
 
-constexpr int kCountRankSmem = kTileWarps * kNBin * 2;
+constexpr int kRankBitmapWords = (kNBin + 31) / 32;
+constexpr int kCountRankSmem = kTileWarps * kNBin * 2 + kTileWarps * kRankBitmapWords * 4;
 
 }  // namespace tmd

@@ -101,8 +101,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
       }
       int sms = 0, od = 0, ou = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          cudaFuncSetAttribute(k_count_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kCountRankSmem) != cudaSuccess ||
+          prepare_count_rank() != cudaSuccess ||
           occupancy_track_decode(0, &od) != cudaSuccess ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_unatt_decode, 256, 0) != cudaSuccess) {
         set_err(err, err_len, "device set-up failed");
@@ -133,7 +132,6 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.att_count = out->att_count ? out->att_count : reinterpret_cast<uint32_t*>(pb + L.att_count);
   F.n_tblocks = L.n_tblocks; F.n_tiles = L.n_tiles; F.n_groups = L.n_groups;
   F.n_chunks = L.n_chunks;
-  F.heads = reinterpret_cast<uint32_t*>(zb + L.z_heads);
   F.len_cursor = reinterpret_cast<uint32_t*>(zb + L.z_len);
   F.lookback = reinterpret_cast<unsigned long long*>(zb + L.z_lb);
   F.track_start = reinterpret_cast<uint32_t*>(pb + L.track_start);
@@ -177,11 +175,11 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     const uint32_t want = (n_kt + kDecodeThreads / 32 - 1) / (kDecodeThreads / 32);
     launch_track_decode(0, want < cap ? want : cap, st, dframe, P, n_kt);
   }
-  if (n_tile) k_count_rank<<<n_tile, 256, kCountRankSmem, st>>>(dframe, P);
+  if (n_tile) launch_count_rank(1, n_tile, st, dframe, P);
   if (n_grp) k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
   k_row_offsets<<<1, 1024, 0, st>>>(dframe, P);
   if (n_grp) k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
-  if (n_tile) k_att_scatter<<<n_tile * kScatBlocksPerTile, kScatThreads, 0, st>>>(dframe, P);
+  if (n_tile) launch_att_scatter(0, n_tile * kScatBlocksPerTile, st, dframe, P);
   if (n_chunk) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_unatt);
     k_unatt_decode<<<n_chunk < cap ? n_chunk : cap, 256, 0, st>>>(dframe, P, n_chunk);

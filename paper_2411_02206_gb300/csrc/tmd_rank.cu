@@ -13,25 +13,38 @@
 //                 in stream order (32 consecutive clusters per step) and gives
 //                 every cluster its rank among the tile's clusters of the same
 //                 bin, equal keys of one step ordered by lane (match.any).
+//                 Variant 1 first tests the step for repeated keys with a
+//                 per-warp bitmap (atom.or returns the bit's old value) and
+//                 takes the match.any path only when some key repeats;
+//                 consecutive clusters mostly belong to one track and lie in
+//                 distinct rows, so most steps take the short path.
 //
 // The native index of cluster j is then tileBase[tile][key] + rank[j].
 #include "tmd_internal.cuh"
 
 namespace tmd {
 
+template <int V>
 __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, PlanDev plan) {
-  extern __shared__ uint32_t s_mem[];  // [kTileWarps][kNBin/2] packed u16 counts
+  // [kTileWarps][kNBin/2] packed u16 counts, then [kTileWarps][kRankBitmapWords]
+  extern __shared__ uint32_t s_mem[];
   const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
   if (*F.status & kStCount) return;
   const uint32_t tile = blockIdx.x - plan.pre_tile[f];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint16_t* __restrict__ keys = F.keys;
+  uint16_t* __restrict__ rank = F.rank;
+  uint16_t* __restrict__ tile_hist = F.tile_hist;
+  const uint32_t n_att = F.n_att;
   uint32_t* hist32 = s_mem + wid * (kNBin / 2);
   uint16_t* hist = reinterpret_cast<uint16_t*>(hist32);
+  uint32_t* bm = s_mem + kTileWarps * (kNBin / 2) + wid * kRankBitmapWords;
   for (int i = lane; i < kNBin / 2; i += 32) hist32[i] = 0u;
+  for (int i = lane; i < kRankBitmapWords; i += 32) bm[i] = 0u;
   __syncwarp();
   const uint32_t j_begin = tile * (uint32_t)kTile + wid * (uint32_t)kTileSub;
-  const uint32_t j_end = min(j_begin + (uint32_t)kTileSub, F.n_att);
+  const uint32_t j_end = min(j_begin + (uint32_t)kTileSub, n_att);
   // pass 1: counts per warp; 8 keys per lane per 16-byte load, 8 loads in
   // flight per lane
   for (uint32_t jb = j_begin; jb < j_end; jb += 8u * 256u) {
@@ -39,7 +52,7 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       const uint32_t j = jb + 256u * u + 8u * lane;
-      v[u] = j + 8 <= j_end ? *reinterpret_cast<const uint4*>(F.keys + j) : make_uint4(0, 0, 0, 0);
+      v[u] = j + 8 <= j_end ? *reinterpret_cast<const uint4*>(keys + j) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < 8; u++) {
@@ -53,7 +66,7 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
         }
       } else {
         for (uint32_t q = j; q < j_end; q++) {
-          const uint32_t k = F.keys[q];
+          const uint32_t k = keys[q];
           atomicAdd(&hist32[k >> 1], (k & 1u) ? 0x10000u : 1u);
         }
       }
@@ -70,7 +83,7 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
       hall[ww * kNBin + b] = (uint16_t)run;
       run += c;
     }
-    F.tile_hist[(size_t)tile * kNBin + b] = (uint16_t)run;
+    tile_hist[(size_t)tile * kNBin + b] = (uint16_t)run;
   }
   __syncthreads();
   // pass 2: stable ranks in stream order, the keys of 8 steps in flight
@@ -79,25 +92,61 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       const uint32_t j = b0 + 32u * u + lane;
-      kk[u] = j < j_end ? (uint32_t)F.keys[j] : 0xFFFFFFFFu;
+      kk[u] = j < j_end ? (uint32_t)keys[j] : 0xFFFFFFFFu;
     }
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       const uint32_t j = b0 + 32u * u + lane;
       const bool in = j < j_end;
-      const uint32_t act = __ballot_sync(0xffffffffu, in);
-      if (in) {
-        const uint32_t k = kk[u];
-        const uint32_t peers = __match_any_sync(act, k);
-        const uint32_t base = hist[k];
-        const uint32_t r = base + __popc(peers & lanemask_lt());
-        __syncwarp(act);
-        if (lane == __ffs(peers) - 1) hist[k] = (uint16_t)(base + __popc(peers));
-        F.rank[j] = (uint16_t)r;
+      const uint32_t k = kk[u];
+      bool slow = true;
+      if constexpr (V == 1) {
+        // a lane whose bit was already set shares its key with an earlier
+        // lane of the step; without such a lane every key is new to the step
+        uint32_t dup = 0;
+        if (in) dup = atomicOr(&bm[k >> 5], 1u << (k & 31)) & (1u << (k & 31));
+        slow = __any_sync(0xffffffffu, dup != 0);
+        if (!slow && in) {
+          const uint32_t base = hist[k];
+          hist[k] = (uint16_t)(base + 1);
+          rank[j] = (uint16_t)base;
+        }
+      }
+      if (slow) {
+        const uint32_t act = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const uint32_t peers = __match_any_sync(act, k);
+          const uint32_t base = hist[k];
+          const uint32_t r = base + __popc(peers & lanemask_lt());
+          __syncwarp(act);
+          if (lane == __ffs(peers) - 1) hist[k] = (uint16_t)(base + __popc(peers));
+          rank[j] = (uint16_t)r;
+        }
       }
       __syncwarp();
+      if constexpr (V == 1) {
+        if (in) bm[k >> 5] = 0u;  // every bit of the word was set in this step
+        __syncwarp();
+      }
     }
   }
+}
+
+void launch_count_rank(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+                       PlanDev plan) {
+  if (variant == 1)
+    k_count_rank<1><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
+  else
+    k_count_rank<0><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
+}
+
+cudaError_t prepare_count_rank() {
+  cudaError_t e = cudaFuncSetAttribute(k_count_rank<0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kCountRankSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_count_rank<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kCountRankSmem);
+  return e;
 }
 
 }  // namespace tmd

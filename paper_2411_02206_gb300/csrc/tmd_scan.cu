@@ -2,9 +2,9 @@
 //
 // Track preparation (replaces the CPU-precomputed SoA indices of Sec. 3 of
 // arXiv:2411.02206 with device scans): trackStart = exclusive scan of the
-// track lengths, a bitmap of track starts, and a decode order with the longest
-// tracks first (bucketed by length), so that warps of the persistent decoder
-// take similar tracks and the tail is short.
+// track lengths, and a decode order with the longest tracks first (bucketed by
+// length), so that warps of the persistent decoder take similar tracks and
+// the tail is short.
 //
 // Row offsets: per (sector,row) bin the attached count (summed from the
 // per-tile histograms of k_count_rank) plus the unattached count, exclusive
@@ -117,33 +117,48 @@ __global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, Pla
   }
 }
 
-// trackStart, start bitmap and decode order.
+// trackStart and decode order.  A block first counts its tracks per length
+// bucket in shared memory and reserves each bucket's range of the order with
+// one global atomic per bucket; the order of tracks of equal length is
+// arbitrary (it only changes which warp decodes a track, not a result).
 __global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, PlanDev plan) {
+  __shared__ uint32_t s_cnt[kLenBuckets];
   uint32_t tot;
   const uint32_t f = find_frame(plan.pre_tblk, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
   if (*F.status & kStCount) return;
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) s_cnt[i] = 0u;
   const uint32_t lb = blockIdx.x - plan.pre_tblk[f];
   const uint32_t t0 = lb * kTrackBlk + threadIdx.x * 8;
-  uint32_t n[8];
+  const uint32_t nt = F.n_tracks;
+  uint32_t n[8], slot[8];
   uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     const uint32_t t = t0 + k;
-    n[k] = t < F.n_tracks ? (uint32_t)F.ncl[t] : 0u;
+    n[k] = t < nt ? (uint32_t)F.ncl[t] : 0u;
     sum += n[k];
   }
-  uint32_t start = F.blk_sum[lb] + block_excl_scan<256>(sum, tot);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 8; k++)
+    if (t0 + k < nt) slot[k] = atomicAdd(&s_cnt[n[k] < kLenBuckets ? n[k] : kLenBuckets - 1], 1u);
+  uint32_t start = F.blk_sum[lb] + block_excl_scan<256>(sum, tot);  // synchronises the block
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) {
+    const uint32_t c = s_cnt[i];
+    if (c) s_cnt[i] = atomicAdd(&F.len_cursor[i], c);
+  }
+  __syncthreads();
+  uint32_t* __restrict__ track_start = F.track_start;
+  uint32_t* __restrict__ order = F.order;
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     const uint32_t t = t0 + k;
-    if (t < F.n_tracks) {
-      F.track_start[t] = start;
-      atomicOr(&F.heads[start >> 5], 1u << (start & 31));
-      const uint32_t b = n[k] < kLenBuckets ? n[k] : kLenBuckets - 1;
-      F.order[atomicAdd(&F.len_cursor[b], 1u)] = t;
+    if (t < nt) {
+      track_start[t] = start;
+      order[s_cnt[n[k] < kLenBuckets ? n[k] : kLenBuckets - 1] + slot[k]] = t;
       start += n[k];
-      if (t == F.n_tracks - 1) F.track_start[F.n_tracks] = start;
+      if (t == nt - 1) track_start[nt] = start;
     }
   }
 }
@@ -163,25 +178,25 @@ __global__ void __launch_bounds__(kBinBlk) k_group_sum(const FrameDev* frames, P
   F.group_sum[(size_t)g * kNBin + b] = s;
 }
 
-// Per frame: attached count per bin, group offsets, rowStart.
+// Per frame: attached count per bin (sum over the groups), rowStart.
 __global__ void __launch_bounds__(1024) k_row_offsets(const FrameDev* frames, PlanDev plan) {
   uint32_t tot;
   const FrameDev& F = frames[blockIdx.x];
   if (*F.status & kStCount) return;
+  const uint32_t* __restrict__ gsum = F.group_sum;
+  uint32_t* __restrict__ att_count = F.att_count;
+  const uint32_t ng = F.n_groups;
   for (uint32_t b = threadIdx.x; b < (uint32_t)kNBin; b += blockDim.x) {
     uint32_t run = 0;
-    for (uint32_t g = 0; g < F.n_groups; g++) {
-      const uint32_t c = F.group_sum[(size_t)g * kNBin + b];
-      F.group_sum[(size_t)g * kNBin + b] = run;
-      run += c;
-    }
-    F.att_count[b] = run;
+#pragma unroll 8
+    for (uint32_t g = 0; g < ng; g++) run += gsum[(size_t)g * kNBin + b];
+    att_count[b] = run;
   }
   __syncthreads();
   uint32_t carry = 0;
   for (uint32_t base = 0; base < (uint32_t)kNBin; base += 1024) {
     const uint32_t i = base + threadIdx.x;
-    const uint32_t v = i < (uint32_t)kNBin ? F.att_count[i] + F.n_unatt_bin[i] : 0u;
+    const uint32_t v = i < (uint32_t)kNBin ? att_count[i] + F.n_unatt_bin[i] : 0u;
     const uint32_t e = block_excl_scan<1024>(v, tot);
     if (i < (uint32_t)kNBin) F.row_start[i] = carry + e;
     carry += tot;
@@ -189,7 +204,8 @@ __global__ void __launch_bounds__(1024) k_row_offsets(const FrameDev* frames, Pl
   if (threadIdx.x == 0) F.row_start[kNBin] = carry;
 }
 
-// First native index of every (tile, bin).
+// First native index of every (tile, bin): rowStart plus the counts of the
+// bin in the groups and tiles before.
 __global__ void __launch_bounds__(kBinBlk) k_tile_base(const FrameDev* frames, PlanDev plan) {
   const uint32_t f = find_frame(plan.pre_grp, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
@@ -198,11 +214,16 @@ __global__ void __launch_bounds__(kBinBlk) k_tile_base(const FrameDev* frames, P
   const uint32_t g = lb / kBinBlocks;
   const uint32_t b = (lb % kBinBlocks) * kBinBlk + threadIdx.x;
   if (b >= (uint32_t)kNBin) return;
+  const uint32_t* __restrict__ gsum = F.group_sum;
+  const uint16_t* __restrict__ hist = F.tile_hist;
+  uint32_t* __restrict__ tbase = F.tile_base;
   const uint32_t te = min((g + 1) * kGroup, F.n_tiles);
-  uint32_t run = F.row_start[b] + F.group_sum[(size_t)g * kNBin + b];
+  uint32_t run = F.row_start[b];
+#pragma unroll 8
+  for (uint32_t gg = 0; gg < g; gg++) run += gsum[(size_t)gg * kNBin + b];
   for (uint32_t tile = g * kGroup; tile < te; tile++) {
-    F.tile_base[(size_t)tile * kNBin + b] = run;
-    run += F.tile_hist[(size_t)tile * kNBin + b];
+    tbase[(size_t)tile * kNBin + b] = run;
+    run += hist[(size_t)tile * kNBin + b];
   }
 }
 

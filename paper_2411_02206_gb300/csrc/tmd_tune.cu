@@ -1,14 +1,16 @@
 // tmd_tune.cu -- tuning parameters and the autotuner.
 //
-// The parameters only change launch shapes (which register-allocation instance
-// of the track decoder runs, and how many blocks per SM the persistent
-// decoders start); every setting produces identical output.  tmd_autotune
+// The parameters only change how the work is laid out (the staging-round
+// variant of the track decoder, the duplicate-key handling of the ranking
+// kernel, and how many blocks per SM the persistent decoders start); every
+// setting produces identical output.  tmd_autotune
 // times the decode chain on the caller's frames for each candidate, keeps the
 // fastest, and stores it in the autotune cache (a small JSON file keyed by the
 // GPU name and SM count) when the handle was created with one.
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "tmd_api_internal.h"
 
@@ -21,6 +23,8 @@ struct Param {
 };
 const Param kParams[] = {
     {"decode_variant", &tmd_handle::tune_decode_variant, 0, 3},
+    {"rank_variant", &tmd_handle::tune_rank_variant, 0, 1},
+    {"scatter_variant", &tmd_handle::tune_scatter_variant, 0, 2},
     {"decode_blocks_per_sm", &tmd_handle::tune_decode_bps, 0, 64},
     {"unatt_blocks_per_sm", &tmd_handle::tune_unatt_bps, 0, 64},
 };
@@ -107,35 +111,42 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool prof = h->prof.on;
   h->prof.on = false;
-  int best_var = h->tune_decode_variant, best_ubps = h->tune_unatt_bps;
-  float best = 1e30f;
-  int rc = TMD_OK;
+  // coordinate descent: each parameter in turn, the others at their best
+  struct Axis {
+    int tmd_handle::*field;
+    std::vector<int> values;
+  };
+  const Axis axes[] = {
+      {&tmd_handle::tune_decode_variant, {0, 1, 2, 3}},
+      {&tmd_handle::tune_rank_variant, {0, 1}},
+      {&tmd_handle::tune_scatter_variant, {0, 1, 2}},
+      {&tmd_handle::tune_unatt_bps, {0, 2, 3, 4}},
+  };
   h->tune_decode_bps = 0;
-  for (int var = 0; var < 4 && rc == TMD_OK; var++) {
-    h->tune_decode_variant = var;
-    float ms = 0;
-    rc = time_chain(h, n, in, out, st, &ms);
-    if (rc == TMD_OK && ms < best) { best = ms; best_var = var; }
+  float best = 1e30f;
+  int rc = time_chain(h, n, in, out, st, &best);
+  for (const Axis& ax : axes) {
+    int keep = h->*(ax.field);
+    for (int v : ax.values) {
+      if (rc != TMD_OK) break;
+      if (v == keep) continue;
+      h->*(ax.field) = v;
+      float ms = 0;
+      rc = time_chain(h, n, in, out, st, &ms);
+      if (rc == TMD_OK && ms < best) { best = ms; keep = v; }
+    }
+    h->*(ax.field) = keep;
   }
-  h->tune_decode_variant = best_var;
-  const int ubps[] = {0, 2, 4, 8};
-  for (int u : ubps) {
-    if (rc != TMD_OK) break;
-    h->tune_unatt_bps = u;
-    float ms = 0;
-    rc = time_chain(h, n, in, out, st, &ms);
-    if (rc == TMD_OK && ms < best) { best = ms; best_ubps = u; }
-  }
-  h->tune_unatt_bps = best_ubps;
   h->prof.on = prof;
   if (rc != TMD_OK) return rc;
   if (!h->autotune_cache.empty()) {
     FILE* f = fopen(h->autotune_cache.c_str(), "w");
     if (f) {
-      fprintf(f, "{\"%s\": {\"decode_variant\": %d, \"decode_blocks_per_sm\": %d, "
+      fprintf(f, "{\"%s\": {\"decode_variant\": %d, \"rank_variant\": %d, "
+                 "\"scatter_variant\": %d, \"decode_blocks_per_sm\": %d, "
                  "\"unatt_blocks_per_sm\": %d, \"chain_ms\": %.4f}}\n",
-              device_key(h).c_str(), h->tune_decode_variant, h->tune_decode_bps,
-              h->tune_unatt_bps, best);
+              device_key(h).c_str(), h->tune_decode_variant, h->tune_rank_variant,
+              h->tune_scatter_variant, h->tune_decode_bps, h->tune_unatt_bps, best);
       fclose(f);
     }
   }

@@ -38,29 +38,56 @@ __device__ __forceinline__ Seg seg_add(const Seg& a, const Seg& b) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_unatt_decode(const FrameDev* frames, PlanDev plan,
+// Largest b in [lo, hi] with start[b] <= e (start[lo] <= e is known).
+__device__ __forceinline__ uint32_t bin_search(const uint32_t* __restrict__ start, uint32_t lo,
+                                               uint32_t hi, uint32_t e) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Shared-memory word of staged record word w: one word of padding per 32
+// spreads the stride-24 writes of the staging loop over the banks, while the
+// copy-out loop still reads 32 consecutive words per warp.
+__device__ __forceinline__ uint32_t rec_slot(uint32_t w) { return w + (w >> 5); }
+
+__global__ void __launch_bounds__(256, 4) k_unatt_decode(const FrameDev* frames, PlanDev plan,
                                                       uint32_t n_tickets) {
+  constexpr uint32_t kRecWords = 3 * kChunk;
   __shared__ uint32_t s_ticket;
+  __shared__ uint32_t s_bin[2];           // bins of the chunk's first and last cluster
   __shared__ Seg s_warp[8];
   __shared__ Seg s_carry;
-  __shared__ uint32_t s_rec[kChunk * 3];  // records of the chunk, element order
+  __shared__ uint32_t s_rec[kRecWords + kRecWords / 32];  // records, element order
   __shared__ uint32_t s_pos[kChunk];      // native index of every element
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (;;) {
     if (tid == 0) s_ticket = atomicAdd(&plan.counters[1], 1u);
     __syncthreads();
     const uint32_t ticket = s_ticket;
-    __syncthreads();
     if (ticket >= n_tickets) break;
     const uint32_t f = find_frame(plan.pre_chunk, plan.n_frames, ticket);
     const FrameDev& F = frames[f];
-    if (*F.status & kStCount) continue;
+    if (*F.status & kStCount) {
+      __syncthreads();
+      continue;
+    }
     const uint32_t c = ticket - plan.pre_chunk[f];
     const uint32_t n = F.n_unatt;
-    const uint32_t e0 = c * (uint32_t)kChunk + tid * 8u;
-    // load 8 consecutive clusters
-    uint32_t pd[8], td[8];
-    if (e0 + 8 <= n) {
+    const uint32_t* __restrict__ ustart = F.unatt_start;
+    const uint32_t c0 = c * (uint32_t)kChunk;
+    const uint32_t e0 = c0 + tid * 8u;
+    // the bins of the chunk's first and last cluster bound every search below
+    if (tid < 2) {
+      const uint32_t e = tid == 0 ? c0 : min(c0 + (uint32_t)kChunk, n) - 1u;
+      s_bin[tid] = bin_search(ustart, 0u, (uint32_t)kNBin - 1u, e);
+    }
+    // all loads of the thread's 8 clusters (vector loads when in range)
+    uint32_t pd[8], td[8], qt[4], qm[4], fl[2], sp[2], sg[2];
+    const bool full = e0 + 8 <= n;
+    if (full) {
       const uint4 p = *reinterpret_cast<const uint4*>(F.pad_diff_u + e0);
       const uint4 t0 = *reinterpret_cast<const uint4*>(F.time_diff_u + e0);
       const uint4 t1 = *reinterpret_cast<const uint4*>(F.time_diff_u + e0 + 4);
@@ -76,38 +103,67 @@ __global__ void __launch_bounds__(256) k_unatt_decode(const FrameDev* frames, Pl
         td[k] = e < n ? F.time_diff_u[e] : 0u;
       }
     }
-    // bin of every cluster, bin starts are segment heads
-    uint32_t bin = 0;
-    if (e0 < n) {
-      uint32_t lo = 0, hi = kNBin;  // largest b with unatt_start[b] <= e0
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (F.unatt_start[mid] <= e0) lo = mid; else hi = mid;
-      }
-      bin = lo;
-    }
-    uint32_t bins[8];
-    uint32_t headmask = 0;
-    uint32_t next = e0 < n ? F.unatt_start[bin + 1] : 0xFFFFFFFFu;
+    const bool vec = full &&
+        ((reinterpret_cast<uintptr_t>(F.qtot_u) | reinterpret_cast<uintptr_t>(F.qmax_u)) & 15) == 0 &&
+        ((reinterpret_cast<uintptr_t>(F.flags_u) | reinterpret_cast<uintptr_t>(F.sigp_u) |
+          reinterpret_cast<uintptr_t>(F.sigt_u)) & 7) == 0;
+    if (vec) {
+      const uint4 a = *reinterpret_cast<const uint4*>(F.qtot_u + e0);
+      const uint4 m = *reinterpret_cast<const uint4*>(F.qmax_u + e0);
+      const uint2 fa = *reinterpret_cast<const uint2*>(F.flags_u + e0);
+      const uint2 pa = *reinterpret_cast<const uint2*>(F.sigp_u + e0);
+      const uint2 ta = *reinterpret_cast<const uint2*>(F.sigt_u + e0);
+      qt[0] = a.x; qt[1] = a.y; qt[2] = a.z; qt[3] = a.w;
+      qm[0] = m.x; qm[1] = m.y; qm[2] = m.z; qm[3] = m.w;
+      fl[0] = fa.x; fl[1] = fa.y; sp[0] = pa.x; sp[1] = pa.y; sg[0] = ta.x; sg[1] = ta.y;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const uint32_t e = e0 + k;
-      if (e < n) {
-        while (e >= next) {
-          bin++;
-          next = F.unatt_start[bin + 1];
+      for (int h = 0; h < 4; h++) { qt[h] = 0u; qm[h] = 0u; }
+#pragma unroll
+      for (int h = 0; h < 2; h++) { fl[h] = 0u; sp[h] = 0u; sg[h] = 0u; }
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const uint32_t e = e0 + k;
+        if (e < n) {
+          qt[k >> 1] |= (uint32_t)F.qtot_u[e] << (16 * (k & 1));
+          qm[k >> 1] |= (uint32_t)F.qmax_u[e] << (16 * (k & 1));
+          fl[k >> 2] |= (uint32_t)F.flags_u[e] << (8 * (k & 3));
+          sp[k >> 2] |= (uint32_t)F.sigp_u[e] << (8 * (k & 3));
+          sg[k >> 2] |= (uint32_t)F.sigt_u[e] << (8 * (k & 3));
         }
-        if (e == F.unatt_start[bin]) headmask |= 1u << k;
       }
-      bins[k] = bin;
     }
-    // thread-local inclusive scan
-    Seg loc[8];
+    __syncthreads();
+    // bin of every cluster (as a position offset), bin starts are segment heads
+    uint32_t pos[8];
+    uint32_t headmask = 0;
+    if (e0 < n) {
+      uint32_t b = bin_search(ustart, s_bin[0], s_bin[1], e0);
+      uint32_t nxt = ustart[b + 1];
+      uint32_t bst = ustart[b];
+      uint32_t delta = F.row_start[b] + F.att_count[b] - bst;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const uint32_t e = e0 + k;
+        if (e < n) {
+          while (e >= nxt) {
+            b++;
+            bst = nxt;
+            nxt = ustart[b + 1];
+            delta = F.row_start[b] + F.att_count[b] - bst;
+          }
+          if (e == bst) headmask |= 1u << k;
+        }
+        pos[k] = e + delta;
+      }
+    }
+    // thread-local inclusive scan, in place
     Seg run{0u, 0u, 0u};
 #pragma unroll
     for (int k = 0; k < 8; k++) {
       run = seg_add(run, Seg{(headmask >> k) & 1u, pd[k], td[k]});
-      loc[k] = run;
+      pd[k] = run.pad;
+      td[k] = run.time;
     }
     // block exclusive scan of the thread aggregates
     Seg x = run;
@@ -174,37 +230,6 @@ __global__ void __launch_bounds__(256) k_unatt_decode(const FrameDev* frames, Pl
       const Seg wex = wid == 0 ? Seg{0u, 0u, 0u} : s_warp[wid];
       ex = seg_add(seg_add(s_carry, wex), lane_ex);
     }
-    // charges and flags of the 8 clusters (vector loads when in range)
-    uint32_t qt[8], qm[8], fl[8], sp[8], sg[8];
-    if (e0 + 8 <= n && ((reinterpret_cast<uintptr_t>(F.qtot_u) | reinterpret_cast<uintptr_t>(F.qmax_u)) & 15) == 0 &&
-        ((reinterpret_cast<uintptr_t>(F.flags_u) | reinterpret_cast<uintptr_t>(F.sigp_u) |
-          reinterpret_cast<uintptr_t>(F.sigt_u)) & 7) == 0) {
-      const uint4 a = *reinterpret_cast<const uint4*>(F.qtot_u + e0);
-      const uint4 m = *reinterpret_cast<const uint4*>(F.qmax_u + e0);
-      const uint2 fa = *reinterpret_cast<const uint2*>(F.flags_u + e0);
-      const uint2 pa = *reinterpret_cast<const uint2*>(F.sigp_u + e0);
-      const uint2 ta = *reinterpret_cast<const uint2*>(F.sigt_u + e0);
-      const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, mw[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        qt[k] = (aw[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-        qm[k] = (mw[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-        fl[k] = ((k < 4 ? fa.x : fa.y) >> ((k & 3) * 8)) & 0xFFu;
-        sp[k] = ((k < 4 ? pa.x : pa.y) >> ((k & 3) * 8)) & 0xFFu;
-        sg[k] = ((k < 4 ? ta.x : ta.y) >> ((k & 3) * 8)) & 0xFFu;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const uint32_t e = e0 + k;
-        const bool in = e < n;
-        qt[k] = in ? F.qtot_u[e] : 0u;
-        qm[k] = in ? F.qmax_u[e] : 0u;
-        fl[k] = in ? F.flags_u[e] : 0u;
-        sp[k] = in ? F.sigp_u[e] : 0u;
-        sg[k] = in ? F.sigt_u[e] : 0u;
-      }
-    }
     // stage the records and their native indices in shared memory
     const uint32_t n_total = F.n_att + F.n_unatt;
     uint32_t st = 0;
@@ -212,31 +237,36 @@ __global__ void __launch_bounds__(256) k_unatt_decode(const FrameDev* frames, Pl
     for (int k = 0; k < 8; k++) {
       const uint32_t e = e0 + k;
       const uint32_t l = tid * 8 + k;
-      uint32_t pos = 0xFFFFFFFFu;
+      uint32_t p = 0xFFFFFFFFu;
       if (e < n) {
-        const Seg v = seg_add(ex, loc[k]);
-        const uint32_t b = bins[k];
-        pos = F.row_start[b] + F.att_count[b] + (e - F.unatt_start[b]);
-        if (v.time > 0xFFFFFFu) st |= kStTime;
-        if (pos >= n_total) {
+        // a bin start at or before element k of this thread cuts off the prefix
+        const bool cut = (headmask & ((2u << k) - 1u)) != 0;
+        const uint32_t vp = cut ? pd[k] : ((ex.pad + pd[k]) & 0xFFFFu);
+        const uint32_t vt = cut ? td[k] : ex.time + td[k];
+        p = pos[k];
+        if (vt > 0xFFFFFFu) st |= kStTime;
+        if (p >= n_total) {
           st |= kStLimit;
-          pos = 0xFFFFFFFFu;
+          p = 0xFFFFFFFFu;
         }
-        s_rec[3 * l + 0] = (v.time & 0xFFFFFFu) | (fl[k] << 24);
-        s_rec[3 * l + 1] = v.pad | (sg[k] << 16) | (sp[k] << 24);
-        s_rec[3 * l + 2] = qm[k] | (qt[k] << 16);
+        const uint32_t q16 = 16 * (k & 1), q8 = 8 * (k & 3);
+        s_rec[rec_slot(3 * l + 0)] = (vt & 0xFFFFFFu) | (((fl[k >> 2] >> q8) & 0xFFu) << 24);
+        s_rec[rec_slot(3 * l + 1)] = vp | (((sg[k >> 2] >> q8) & 0xFFu) << 16) |
+                                     (((sp[k >> 2] >> q8) & 0xFFu) << 24);
+        s_rec[rec_slot(3 * l + 2)] = ((qm[k >> 1] >> q16) & 0xFFFFu) |
+                                     (((qt[k >> 1] >> q16) & 0xFFFFu) << 16);
       }
-      s_pos[l] = pos;
+      s_pos[l] = p;
     }
     __syncthreads();
     // write out word by word: consecutive threads write consecutive words of
     // consecutive records, which are contiguous in the native list within a bin
-    const uint32_t n_here = min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
+    const uint32_t n_here = min((uint32_t)kChunk, n - c0);
+    uint32_t* __restrict__ nat = reinterpret_cast<uint32_t*>(F.native);
     for (uint32_t w = tid; w < 3 * n_here; w += blockDim.x) {
       const uint32_t l = w / 3;
-      const uint32_t pos = s_pos[l];
-      if (pos != 0xFFFFFFFFu)
-        reinterpret_cast<uint32_t*>(F.native)[(size_t)pos * 3 + (w - 3 * l)] = s_rec[w];
+      const uint32_t p = s_pos[l];
+      if (p != 0xFFFFFFFFu) nat[(size_t)p * 3 + (w - 3 * l)] = s_rec[rec_slot(w)];
     }
     if (st) atomicOr(F.status, st);
     __syncthreads();

@@ -172,3 +172,59 @@ def test_full_size_pbpb_frame(dec):
     unattached): GPU encoder and decoder against the oracle on every field."""
     truth = synth.shape_truth("pbpb")
     _check_truth(dec, truth, "pbpb full size")
+
+
+def test_every_tuning_setting_gives_the_oracle_result(dec):
+    """Tuning parameters change only how work is laid out: every combination
+    of decoder, ranking and scatter variant must reproduce the oracle."""
+    from paper_2411_02206_gb300 import frames
+    truth = synth.make_truth(n_tracks=3000, n_unatt=60_000, seed=9, looper_frac=0.4,
+                             max_legs=4, pt_mean=0.3)
+    of = G.oracle_frame(truth)
+    ora = O.decode(of)
+    dev = frames.to_torch(of, "cuda:0")
+    saved = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
+                                               "scatter_variant")}
+    try:
+        for dv in range(4):
+            for rv in range(2):
+                for sv in range(3):
+                    dec.tmd_tune_set("decode_variant", dv)
+                    dec.tmd_tune_set("rank_variant", rv)
+                    dec.tmd_tune_set("scatter_variant", sv)
+                    native, rs, att, st = dec.decode(dev)
+                    gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
+                           frames.to_numpy(att, np.uint32), int(st.item()))
+                    G.assert_same_decode(gpu, ora, f"decode {dv} rank {rv} scatter {sv}")
+    finally:
+        for k, v in saved.items():
+            dec.tmd_tune_set(k, v)
+
+
+def test_unaligned_caller_arrays(dec):
+    """Caller arrays aligned only to their element size (views at an odd
+    element offset) take the scalar-load paths and give the same result."""
+    import torch
+    from paper_2411_02206_gb300 import frames
+    truth = synth.make_truth(n_tracks=1200, n_unatt=30_000, seed=10)
+    of = G.oracle_frame(truth)
+    ora = O.decode(of)
+    dev = frames.to_torch(of, "cuda:0")
+    shifted = dict(dev)
+    for k in ("qtot_a", "qmax_a", "flags_a", "sigma_pad_a", "sigma_time_a", "row_diff",
+              "slice_leg_diff", "pad_res", "time_res", "qtot_u", "qmax_u", "flags_u",
+              "sigma_pad_u", "sigma_time_u"):
+        t = dev[k]
+        buf = torch.zeros(t.numel() + 1, dtype=t.dtype, device=t.device)
+        buf[1:] = t
+        shifted[k] = buf[1:]
+    for sv in range(3):
+        dec.tmd_tune_set("scatter_variant", sv)
+        for dv in range(4):
+            dec.tmd_tune_set("decode_variant", dv)
+            native, rs, att, st = dec.decode(shifted)
+            gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
+                   frames.to_numpy(att, np.uint32), int(st.item()))
+            G.assert_same_decode(gpu, ora, f"unaligned, scatter {sv} decode {dv}")
+    dec.tmd_tune_set("scatter_variant", 0)
+    dec.tmd_tune_set("decode_variant", 1)
