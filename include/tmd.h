@@ -194,6 +194,19 @@ int tmd_batch_destroy(tmd_batch* b);
 int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out,
                           void* stream);
 
+/* Decode n frames given HOST buffers, pipelined (arXiv:2411.02206, Sec. 3 and
+ * Fig. 3: several instances on streams hide the transfers): frame i's inputs
+ * are copied to one of two handle-owned device slots on a copy stream while
+ * frame i - 1 is decoded on `stream` and frame i - 2's native list, row
+ * offsets, attached counts and status are copied back to out[i - 2] on a
+ * second copy stream.  in[i] / out[i] hold host pointers as in
+ * tmd_decode_frame_host; the device slots are sized for the largest frame
+ * and kept for later calls.  Synchronous on return; results equal those of n
+ * tmd_decode_frame_host calls.  Pinned host memory is required for the
+ * copies to overlap. */
+int tmd_decode_host_stream(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
+                           const tmd_frame_out* out, void* stream);
+
 /* Decode one frame without allocating anything (the paper has no
  * counterpart; this is an integration aid).  For callers that cannot
  * allocate device memory while they run -- code inside a memory pool it
@@ -246,11 +259,11 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *   "rank_variant"        0..1  ranking of equal keys: match.any on every
  *                               step (0) or only on steps with repeated keys,
  *                               found with a shared-memory bitmap (1)
- *   "scatter_variant"     0..2  loads of the record scatter: clusters at a
- *                               stride of the block (0), 8 consecutive
- *                               clusters per thread with vector loads and the
- *                               bin bases in shared memory (1) or read
- *                               through L1 (2)
+ *   "scatter_variant"     0..2  stores of the record scatter: one record per
+ *                               thread (0), three lanes per record in one
+ *                               store instruction (1), or a whole ranking
+ *                               tile regrouped in (bin, rank) order through
+ *                               distributed shared memory first (2)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
  * tmd_autotune times the decode chain on the given frames (device buffers,

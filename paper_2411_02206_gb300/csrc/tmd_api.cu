@@ -170,6 +170,16 @@ tmd_handle::~tmd_handle() {
   }
   if (scratch) cudaFree(scratch);
   if (stage) cudaFree(stage);
+  if (aux) cudaStreamDestroy(aux);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (h2d) cudaStreamSynchronize(h2d), cudaStreamDestroy(h2d);
+  if (d2h) cudaStreamSynchronize(d2h), cudaStreamDestroy(d2h);
+  for (int s = 0; s < 2; s++) {
+    if (pipe_buf[s]) cudaFree(pipe_buf[s]);
+    for (cudaEvent_t e : {pipe_in[s], pipe_dec[s], pipe_out[s]})
+      if (e) cudaEventDestroy(e);
+  }
 }
 
 extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
@@ -190,7 +200,14 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
   int rc = TMD_OK;
   if ((rc = tmd_cuda_check(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount,
                                                     h->device), "sm count")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking),
+                           "stream")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming),
+                           "event")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming),
+                           "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, prepare_count_rank(), "smem attribute")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, prepare_att_scatter(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(0, &h->occ_decode_v[0]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(2, &h->occ_decode_v[2]), "occupancy")) != TMD_OK ||
@@ -246,8 +263,8 @@ cudaEvent_t TmdProfile::get() {
 void TmdProfile::drain(size_t keep) {
   if (pending.size() <= keep) return;
   const size_t n = pending.size() - keep;
-  cudaEventSynchronize(pending[n - 1].second.second);
   for (size_t i = 0; i < n; i++) {
+    cudaEventSynchronize(pending[i].second.second);  // pairs on two streams end out of order
     float t = 0.0f;
     if (cudaEventElapsedTime(&t, pending[i].second.first, pending[i].second.second) == cudaSuccess) {
       ms[pending[i].first] += t;
@@ -351,7 +368,9 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   int slot = 0;
   if ((rc = h->acquire_slot(record_bytes, slot)) != TMD_OK) return rc;
   tmd_handle::Slot& S = h->slots[slot];
-  rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on);
+  const bool two = h->tune_overlap && !tin;
+  rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on,
+                   two ? h->aux : nullptr, h->fork, h->join);
   if (rc != TMD_OK) return rc;
   CK(cudaEventRecord(S.done, st));
   S.used = true;
@@ -360,7 +379,8 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
 
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                 const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
-                void* host_record, void* dev_record, cudaStream_t st, bool profile) {
+                void* host_record, void* dev_record, cudaStream_t st, bool profile,
+                cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join) {
   const bool encode = tin != nullptr;
   std::vector<FrameLayout> L;
   size_t zbytes = 0, pbytes = 0;
@@ -453,18 +473,19 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   CK(cudaMemcpyAsync(dev, host, R.bytes, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(zb, 0, zbytes, st));
   TmdProfile& prof = h->prof;
-  auto timed = [&](int id, auto&& launch) {
+  auto timed_on = [&](cudaStream_t on, int id, auto&& launch) {
     if (!profile) {
       launch();
       return;
     }
     cudaEvent_t a = prof.get(), b = prof.get();
-    cudaEventRecord(a, st);
+    cudaEventRecord(a, on);
     launch();
-    cudaEventRecord(b, st);
+    cudaEventRecord(b, on);
     prof.pending.push_back({id, {a, b}});
     if (prof.pending.size() >= 4096) prof.drain(2048);
   };
+  auto timed = [&](int id, auto&& launch) { timed_on(st, id, launch); };
   timed(kKZeroStatus, [&] { k_zero_status<<<1, 256, 0, st>>>(dframes, nf); });
   const uint32_t n_tblk = pre_tblk[nf], n_tile = pre_tile[nf], n_grp = pre_grp[nf];
   const uint32_t n_warp = pre_warp[nf], n_chunk = pre_chunk[nf];
@@ -491,16 +512,30 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       timed(kKCountRank, [&] { launch_count_rank(h->tune_rank_variant, n_tile, st, dframes, P); });
     if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
-    if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
-    if (n_tile)
-      timed(kKAttScatter, [&] {
-        launch_att_scatter(h->tune_scatter_variant, n_tile * kScatBlocksPerTile, st, dframes, P);
-      });
+    // the unattached decode needs only rowStart / attCount: with an aux
+    // stream it runs beside the tile bases and the record scatter
+    const bool two = aux && fork && join && n_chunk;
+    cudaStream_t ust = st;
+    if (two) {
+      CK(cudaEventRecord(fork, st));
+      CK(cudaStreamWaitEvent(aux, fork, 0));
+      ust = aux;
+    }
     if (n_chunk) {
       int bps = h->occ_unatt;
       if (h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;
       const uint32_t grid = std::min<uint32_t>(n_chunk, (uint32_t)(h->sms * bps));
-      timed(kKUnattDecode, [&] { k_unatt_decode<<<grid, 256, 0, st>>>(dframes, P, n_chunk); });
+      timed_on(ust, kKUnattDecode,
+               [&] { k_unatt_decode<<<grid, 256, 0, ust>>>(dframes, P, n_chunk); });
+    }
+    if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+    if (n_tile)
+      timed(kKAttScatter, [&] {
+        launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P);
+      });
+    if (two) {
+      CK(cudaEventRecord(join, aux));
+      CK(cudaStreamWaitEvent(st, join, 0));
     }
   }
   CK(cudaGetLastError());

@@ -47,7 +47,8 @@ struct tmd_handle {
   // tuning parameters (launch shapes only; results never depend on them)
   int tune_decode_variant = 1;   // staging-round variant of the track decoder
   int tune_rank_variant = 1;     // duplicate-key handling of the ranking kernel
-  int tune_scatter_variant = 0;  // load pattern of the record scatter
+  int tune_scatter_variant = 1;  // store pattern of the record scatter
+  int tune_overlap = 1;          // unattached decode on a second stream beside the scatter
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;
@@ -62,6 +63,15 @@ struct tmd_handle {
   size_t stage_bytes = 0;
   TmdServer* server = nullptr;
   TmdProfile prof;
+  cudaStream_t aux = nullptr;              // second stream of the plain decode chain
+  cudaEvent_t fork = nullptr, join = nullptr;
+  // host streaming pipeline (tmd_decode_host_stream): copy streams, two
+  // device slots and their events
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  void* pipe_buf[2] = {nullptr, nullptr};
+  size_t pipe_bytes[2] = {0, 0};
+  cudaEvent_t pipe_in[2] = {nullptr, nullptr}, pipe_dec[2] = {nullptr, nullptr},
+              pipe_out[2] = {nullptr, nullptr};
 
   int ensure_scratch(size_t bytes);
   int acquire_slot(size_t bytes, int& slot);
@@ -91,11 +101,15 @@ void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin
                     size_t* scratch_bytes, size_t* record_bytes);
 // Fill the launch record (host_record, pinned) for the given scratch and enqueue
 // the record upload and the kernel chain on st (with per-kernel events into
-// the handle's profile if `profile`; only the handle's own thread may ask).  The caller keeps scratch and
-// both record buffers alive until the stream has passed the chain.
+// the handle's profile if `profile`; only the handle's own thread may ask).
+// With an aux stream (and fork/join events), the unattached decode runs on
+// aux beside the tile bases and the record scatter, and st waits for it at
+// the end.  The caller keeps scratch and both record buffers alive until the
+// stream has passed the chain.
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                 const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
-                void* host_record, void* dev_record, cudaStream_t st, bool profile);
+                void* host_record, void* dev_record, cudaStream_t st, bool profile,
+                cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 void tmd_serve_shutdown(tmd_handle* h);
 // Read the tuning parameters for this GPU from the autotune cache, if any.
 void tmd_tune_load(tmd_handle* h);

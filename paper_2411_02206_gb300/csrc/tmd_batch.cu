@@ -18,12 +18,17 @@ struct tmd_batch {
   void* host_record = nullptr;
   void* dev_record = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t aux = nullptr;  // second branch of the captured chain
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~tmd_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
+    if (aux) cudaStreamDestroy(aux);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     if (scratch) cudaFree(scratch);
     if (dev_record) cudaFree(dev_record);
     if (host_record) cudaFreeHost(host_record);
@@ -54,12 +59,19 @@ extern "C" int tmd_batch_create(tmd_handle* h, uint32_t n, const tmd_frame_in* i
     return tmd_set_error(h, TMD_ERR_NOMEM, "batch allocation (%zu bytes) failed", scratch_bytes);
   }
   int rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking), "stream");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming), "event");
   if (rc != TMD_OK) { delete b; return rc; }
   rc = tmd_cuda_check(h, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal),
                       "begin capture");
   if (rc == TMD_OK) {
+    // no timing events inside the graph; the fork/join events become edges
     rc = tmd_enqueue(h, n, in, out, nullptr, nullptr, b->scratch, b->host_record, b->dev_record,
-                     b->cap, false);  // no event nodes inside the graph
+                     b->cap, false, h->tune_overlap ? b->aux : nullptr, b->fork, b->join);
     const int rc2 = tmd_cuda_check(h, cudaStreamEndCapture(b->cap, &b->graph), "end capture");
     if (rc == TMD_OK) rc = rc2;
   }

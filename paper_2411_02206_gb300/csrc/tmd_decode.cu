@@ -14,10 +14,11 @@
 //                   the model with the decoded cluster.  It writes, in input
 //                   order j, the cluster's (sector,row) key, pad code and time
 //                   code.
-//   k_att_scatter   one thread per attached cluster: assembles the 12-byte
-//                   native record from the decoded coordinates and the charge
-//                   streams and writes it at tileBase[tile(j)][key] + rank[j]
-//                   (k_count_rank / k_tile_base: deterministic, no atomics).
+//   k_att_scatter   (tmd_scatter.cu) assembles the 12-byte native record of
+//                   every attached cluster from the decoded coordinates and
+//                   the charge streams and writes it at
+//                   tileBase[tile(j)][key] + rank[j] (k_count_rank /
+//                   k_tile_base: deterministic, no atomics).
 //
 // The lane-per-track walk reads each stream at 32 unrelated positions per
 // warp.  Read directly, every lane pulls whole sectors for a few bytes and
@@ -135,10 +136,11 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const Fra
             const uint32_t a = W.a[lane * P + q], tr = W.b[lane * P + q];
             st |= key_step(s, a & 255u, (a >> 8) & 255u);
             uint32_t ppad, ptime;
-            propagate_predict(&geo, s, ppad, ptime);
+            const float4 G = geo.row[s.row];
+            propagate_predict(G, s, ppad, ptime);
             padq = (ppad + (a >> 16)) & 0xFFFFu;
             timeq = ptime + tr;
-            update(&geo, s, padq, timeq);
+            update(G, s, padq, timeq);
           }
           if (timeq > 0xFFFFFFu) st |= kStTime;
           W.a[lane * P + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
@@ -340,10 +342,11 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
             const uint32_t prv = (lb[2 * Lay::kRd + (ppr >> 1)] >> (16 * (ppr & 1))) & 0xFFFFu;
             st |= key_step(s, rdv, slv);
             uint32_t ppad, ptime;
-            propagate_predict(&geo, s, ppad, ptime);
+            const float4 G = geo.row[s.row];
+            propagate_predict(G, s, ppad, ptime);
             padq = (ppad + prv) & 0xFFFFu;
             timeq = ptime + lb[Lay::kTr0 + q];
-            update(&geo, s, padq, timeq);
+            update(G, s, padq, timeq);
           }
           if (timeq > 0xFFFFFFu) st |= kStTime;
           S.kp[lane * P + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
@@ -369,150 +372,6 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
     }
     st = __reduce_or_sync(kFull, st);
     if (st && lane == 0) atomicOr(frames[f].status, st);
-  }
-}
-
-// k_att_scatter: kScatPerThread = 8 attached clusters per thread.  Variants
-// (identical results):
-//   V = 0  clusters at a stride of the block size (one scalar load per stream
-//          and cluster, consecutive lanes on consecutive clusters); bin bases
-//          read through L1;
-//   V = 1  8 consecutive clusters per thread, one vector load per stream
-//          (scalar loads when a caller array is not aligned for it); the
-//          tile's row of bin bases copied to shared memory first;
-//   V = 2  as V = 1, bin bases read through L1.
-// A block covers kScatThreads * 8 consecutive clusters of one ranking tile.
-template <int V>
-__global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev* frames,
-                                                                 PlanDev plan) {
-  static_assert(kScatPerThread == 8, "one 16-byte load per u16 stream");
-  __shared__ uint32_t s_tb[V == 1 ? kNBin : 1];
-  const uint32_t gtile = blockIdx.x / kScatBlocksPerTile;
-  const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
-  const FrameDev& F = frames[f];
-  if (*F.status & kStCount) return;
-  const uint32_t tile = gtile - plan.pre_tile[f];
-  const uint32_t jb = tile * (uint32_t)kTile +
-                      (blockIdx.x % kScatBlocksPerTile) * (uint32_t)(kTile / kScatBlocksPerTile);
-  const uint32_t n_att = F.n_att, n_total = F.n_att + F.n_unatt;
-  const uint16_t* __restrict__ keys = F.keys;
-  const uint16_t* __restrict__ rank = F.rank;
-  const uint16_t* __restrict__ kpad = F.kf_pad;
-  const uint32_t* __restrict__ ktime = F.kf_time;
-  const uint16_t* __restrict__ qtot = F.qtot_a;
-  const uint16_t* __restrict__ qmax = F.qmax_a;
-  const uint8_t* __restrict__ flags = F.flags_a;
-  const uint8_t* __restrict__ sigp = F.sigp_a;
-  const uint8_t* __restrict__ sigt = F.sigt_a;
-  const uint32_t* __restrict__ tbase = F.tile_base + (size_t)tile * kNBin;
-  uint8_t* __restrict__ native = F.native;
-  if constexpr (V == 1) {
-    const uint4* tb = reinterpret_cast<const uint4*>(tbase);
-    for (int i = threadIdx.x; i < kNBin / 4; i += kScatThreads)
-      reinterpret_cast<uint4*>(s_tb)[i] = __ldg(tb + i);
-  }
-  // cluster u of this thread
-  auto cl = [&](int u) -> uint32_t {
-    return V == 0 ? jb + u * kScatThreads + threadIdx.x : jb + threadIdx.x * 8 + u;
-  };
-  // 8 clusters: keys, ranks, pad codes, charges as packed u16 pairs; time
-  // codes; flags and sigmas as packed bytes
-  uint32_t kw[4], rw[4], pw[4], tw[8], qtw[4], qmw[4], flw[2], spw[2], sgw[2];
-  const uint32_t j0 = jb + threadIdx.x * 8;
-  const bool full = V != 0 && j0 + 8 <= n_att;
-  const bool vec = full &&
-      ((reinterpret_cast<uintptr_t>(qtot) | reinterpret_cast<uintptr_t>(qmax)) & 15) == 0 &&
-      ((reinterpret_cast<uintptr_t>(flags) | reinterpret_cast<uintptr_t>(sigp) |
-        reinterpret_cast<uintptr_t>(sigt)) & 7) == 0;
-  if (full) {  // the scratch streams are always aligned
-    const uint4 a = *reinterpret_cast<const uint4*>(keys + j0);
-    const uint4 b = *reinterpret_cast<const uint4*>(rank + j0);
-    const uint4 c = *reinterpret_cast<const uint4*>(kpad + j0);
-    const uint4 d = *reinterpret_cast<const uint4*>(ktime + j0);
-    const uint4 e = *reinterpret_cast<const uint4*>(ktime + j0 + 4);
-    kw[0] = a.x; kw[1] = a.y; kw[2] = a.z; kw[3] = a.w;
-    rw[0] = b.x; rw[1] = b.y; rw[2] = b.z; rw[3] = b.w;
-    pw[0] = c.x; pw[1] = c.y; pw[2] = c.z; pw[3] = c.w;
-    tw[0] = d.x; tw[1] = d.y; tw[2] = d.z; tw[3] = d.w;
-    tw[4] = e.x; tw[5] = e.y; tw[6] = e.z; tw[7] = e.w;
-  } else {
-#pragma unroll
-    for (int h = 0; h < 4; h++) { kw[h] = 0u; rw[h] = 0u; pw[h] = 0u; }
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint32_t j = cl(u);
-      tw[u] = 0u;
-      if (j < n_att) {
-        kw[u >> 1] |= (uint32_t)keys[j] << (16 * (u & 1));
-        rw[u >> 1] |= (uint32_t)rank[j] << (16 * (u & 1));
-        pw[u >> 1] |= (uint32_t)kpad[j] << (16 * (u & 1));
-        tw[u] = ktime[j];
-      }
-    }
-  }
-  if (vec) {
-    const uint4 a = *reinterpret_cast<const uint4*>(qtot + j0);
-    const uint4 b = *reinterpret_cast<const uint4*>(qmax + j0);
-    const uint2 c = *reinterpret_cast<const uint2*>(flags + j0);
-    const uint2 d = *reinterpret_cast<const uint2*>(sigp + j0);
-    const uint2 e = *reinterpret_cast<const uint2*>(sigt + j0);
-    qtw[0] = a.x; qtw[1] = a.y; qtw[2] = a.z; qtw[3] = a.w;
-    qmw[0] = b.x; qmw[1] = b.y; qmw[2] = b.z; qmw[3] = b.w;
-    flw[0] = c.x; flw[1] = c.y; spw[0] = d.x; spw[1] = d.y; sgw[0] = e.x; sgw[1] = e.y;
-  } else {
-#pragma unroll
-    for (int h = 0; h < 4; h++) { qtw[h] = 0u; qmw[h] = 0u; }
-#pragma unroll
-    for (int h = 0; h < 2; h++) { flw[h] = 0u; spw[h] = 0u; sgw[h] = 0u; }
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint32_t j = cl(u);
-      if (j < n_att) {
-        qtw[u >> 1] |= (uint32_t)qtot[j] << (16 * (u & 1));
-        qmw[u >> 1] |= (uint32_t)qmax[j] << (16 * (u & 1));
-        flw[u >> 2] |= (uint32_t)flags[j] << (8 * (u & 3));
-        spw[u >> 2] |= (uint32_t)sigp[j] << (8 * (u & 3));
-        sgw[u >> 2] |= (uint32_t)sigt[j] << (8 * (u & 3));
-      }
-    }
-  }
-  if constexpr (V == 1) __syncthreads();
-  uint32_t st = 0;
-#pragma unroll
-  for (int u = 0; u < 8; u++) {
-    const uint32_t j = cl(u);
-    if (j < n_att) {
-      const uint32_t h16 = 16 * (u & 1), h8 = 8 * (u & 3);
-      const uint32_t key = (kw[u >> 1] >> h16) & 0xFFFFu;
-      const uint32_t base = V == 1 ? s_tb[key] : __ldg(tbase + key);
-      const uint32_t p = base + ((rw[u >> 1] >> h16) & 0xFFFFu);
-      const uint32_t w0 = (tw[u] & 0xFFFFFFu) | (((flw[u >> 2] >> h8) & 0xFFu) << 24);
-      const uint32_t w1 = ((pw[u >> 1] >> h16) & 0xFFFFu) | (((sgw[u >> 2] >> h8) & 0xFFu) << 16) |
-                          (((spw[u >> 2] >> h8) & 0xFFu) << 24);
-      const uint32_t w2 = ((qmw[u >> 1] >> h16) & 0xFFFFu) | (((qtw[u >> 1] >> h16) & 0xFFFFu) << 16);
-      if (p < n_total) {
-        uint32_t* dst = reinterpret_cast<uint32_t*>(native + (size_t)p * kRecBytes);
-        if ((p & 1u) == 0) {  // record starts on an 8-byte boundary
-          *reinterpret_cast<uint2*>(dst) = make_uint2(w0, w1);
-          dst[2] = w2;
-        } else {
-          dst[0] = w0;
-          *reinterpret_cast<uint2*>(dst + 1) = make_uint2(w1, w2);
-        }
-      } else {
-        st |= kStLimit;
-      }
-    }
-  }
-  if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(frames[f].status, kStLimit);
-}
-
-void launch_att_scatter(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                        PlanDev plan) {
-  switch (variant) {
-    case 1: k_att_scatter<1><<<grid, kScatThreads, 0, st>>>(frames, plan); break;
-    case 2: k_att_scatter<2><<<grid, kScatThreads, 0, st>>>(frames, plan); break;
-    default: k_att_scatter<0><<<grid, kScatThreads, 0, st>>>(frames, plan); break;
   }
 }
 
@@ -582,13 +441,14 @@ __global__ void __launch_bounds__(256) k_track_encode(const EncDev* enc, const F
         const uint32_t sld = legd * kNSec + sd;
         st |= key_step(s, rd, sld);
         uint32_t ppad, ptime;
-        propagate_predict(&geo, s, ppad, ptime);
+        const float4 G = geo.row[s.row];
+        propagate_predict(G, s, ppad, ptime);
         const uint32_t padq = E.pad[j], timeq = E.time[j];
         E.o_row_diff[d] = (uint8_t)rd;
         E.o_sld[d] = (uint8_t)sld;
         E.o_pad_res[d] = (uint16_t)((padq - ppad) & 0xFFFFu);
         E.o_time_res[d] = timeq - ptime;
-        update(&geo, s, padq, timeq);
+        update(G, s, padq, timeq);
       }
     }
     if (st) atomicOr(F.status, st);

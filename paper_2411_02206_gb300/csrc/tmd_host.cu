@@ -1,59 +1,77 @@
-// tmd_host.cu -- end-to-end decode from host buffers: one cudaMemcpyAsync per
-// input stream into handle-owned device memory, the decode chain, and the
-// copies of the native list, row offsets and status back to the host.
+// tmd_host.cu -- decoding from host buffers.
+//
+// tmd_decode_frame_host: one cudaMemcpyAsync per input stream into
+// handle-owned device memory, the decode chain, and the copies of the native
+// list, row offsets and status back to the host buffers; synchronous.
+//
+// tmd_decode_host_stream: the same for a sequence of frames, pipelined the
+// way Sec. 3 of arXiv:2411.02206 runs several decoding instances on streams
+// to hide the transfers (Fig. 3): two device slots; frame i's inputs go up on
+// a host-to-device copy stream while frame i - 1 is decoded on the compute
+// stream and frame i - 2's results come back on a device-to-host copy
+// stream.  A slot is refilled only after the results of the frame that last
+// used it have left.
+#include <algorithm>
 #include <cstring>
 
 #include "tmd_api_internal.h"
 
 namespace {
-size_t up(size_t x) { return (x + 255) / 256 * 256; }
-}  // namespace
 
-extern "C" int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in,
-                                     const tmd_frame_out* out, void* stream) {
-  if (!h) return TMD_ERR_ARG;
-  if (!in || !out) return tmd_set_error(h, TMD_ERR_ARG, "null descriptor");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+size_t up(size_t x) { return (x + 255) / 256 * 256; }
+
+struct Field {
+  const void* src;
+  size_t bytes;
+  const void** dst;
+};
+
+// The input streams of a frame (host pointers in `in`, device pointers to be
+// set in `d`), in tmd_frame_in order.
+int input_fields(const tmd_frame_in* in, tmd_frame_in* d, Field (&fs)[23]) {
   const size_t nt = in->n_tracks, na = in->n_attached, nu = in->n_unattached;
-  if (na < nt) return tmd_set_error(h, TMD_ERR_ARG, "n_attached < n_tracks");
-  struct Field { const void* src; size_t bytes; const void** dst; };
-  tmd_frame_in d = *in;
-  Field fs[] = {
-      {in->qpt, nt, (const void**)&d.qpt}, {in->row, nt, (const void**)&d.row},
-      {in->slice, nt, (const void**)&d.slice}, {in->pad, 2 * nt, (const void**)&d.pad},
-      {in->time, 4 * nt, (const void**)&d.time}, {in->ncl, 2 * nt, (const void**)&d.ncl},
-      {in->qtot_a, 2 * na, (const void**)&d.qtot_a}, {in->qmax_a, 2 * na, (const void**)&d.qmax_a},
-      {in->flags_a, na, (const void**)&d.flags_a}, {in->sigma_pad_a, na, (const void**)&d.sigma_pad_a},
-      {in->sigma_time_a, na, (const void**)&d.sigma_time_a},
-      {in->row_diff, na - nt, (const void**)&d.row_diff},
-      {in->slice_leg_diff, na - nt, (const void**)&d.slice_leg_diff},
-      {in->pad_res, 2 * (na - nt), (const void**)&d.pad_res},
-      {in->time_res, 4 * (na - nt), (const void**)&d.time_res},
-      {in->n_unatt, 4 * (size_t)TMD_NBIN, (const void**)&d.n_unatt},
-      {in->pad_diff_u, 2 * nu, (const void**)&d.pad_diff_u},
-      {in->time_diff_u, 4 * nu, (const void**)&d.time_diff_u},
-      {in->qtot_u, 2 * nu, (const void**)&d.qtot_u}, {in->qmax_u, 2 * nu, (const void**)&d.qmax_u},
-      {in->flags_u, nu, (const void**)&d.flags_u}, {in->sigma_pad_u, nu, (const void**)&d.sigma_pad_u},
-      {in->sigma_time_u, nu, (const void**)&d.sigma_time_u}};
+  *d = *in;
+  const Field f[23] = {
+      {in->qpt, nt, (const void**)&d->qpt}, {in->row, nt, (const void**)&d->row},
+      {in->slice, nt, (const void**)&d->slice}, {in->pad, 2 * nt, (const void**)&d->pad},
+      {in->time, 4 * nt, (const void**)&d->time}, {in->ncl, 2 * nt, (const void**)&d->ncl},
+      {in->qtot_a, 2 * na, (const void**)&d->qtot_a}, {in->qmax_a, 2 * na, (const void**)&d->qmax_a},
+      {in->flags_a, na, (const void**)&d->flags_a},
+      {in->sigma_pad_a, na, (const void**)&d->sigma_pad_a},
+      {in->sigma_time_a, na, (const void**)&d->sigma_time_a},
+      {in->row_diff, na - nt, (const void**)&d->row_diff},
+      {in->slice_leg_diff, na - nt, (const void**)&d->slice_leg_diff},
+      {in->pad_res, 2 * (na - nt), (const void**)&d->pad_res},
+      {in->time_res, 4 * (na - nt), (const void**)&d->time_res},
+      {in->n_unatt, 4 * (size_t)TMD_NBIN, (const void**)&d->n_unatt},
+      {in->pad_diff_u, 2 * nu, (const void**)&d->pad_diff_u},
+      {in->time_diff_u, 4 * nu, (const void**)&d->time_diff_u},
+      {in->qtot_u, 2 * nu, (const void**)&d->qtot_u}, {in->qmax_u, 2 * nu, (const void**)&d->qmax_u},
+      {in->flags_u, nu, (const void**)&d->flags_u},
+      {in->sigma_pad_u, nu, (const void**)&d->sigma_pad_u},
+      {in->sigma_time_u, nu, (const void**)&d->sigma_time_u}};
+  for (int i = 0; i < 23; i++) fs[i] = f[i];
+  return na < nt ? TMD_ERR_ARG : TMD_OK;
+}
+
+// Device bytes of one frame: inputs, then native, row_start, att_count, status.
+size_t frame_bytes(const tmd_frame_in* in) {
+  tmd_frame_in d;
+  Field fs[23];
+  input_fields(in, &d, fs);
   size_t need = 0;
   for (const Field& f : fs) need += up(f.bytes);
-  const size_t native_bytes = (na + nu) * TMD_REC_BYTES;
-  need += up(native_bytes) + up(4 * (TMD_NBIN + 1)) + up(4 * TMD_NBIN) + 256;
-  if (cudaSetDevice(h->device) != cudaSuccess) return tmd_set_error(h, TMD_ERR_CUDA, "cudaSetDevice");
-  if (need > h->stage_bytes) {
-    if (h->stage) {
-      cudaDeviceSynchronize();
-      cudaFree(h->stage);
-    }
-    h->stage = nullptr;
-    h->stage_bytes = 0;
-    if (cudaMalloc(&h->stage, need) != cudaSuccess) {
-      cudaGetLastError();
-      return tmd_set_error(h, TMD_ERR_NOMEM, "staging allocation of %zu bytes failed", need);
-    }
-    h->stage_bytes = need;
-  }
-  char* p = static_cast<char*>(h->stage);
+  const size_t n = (size_t)in->n_attached + in->n_unattached;
+  return need + up(n * TMD_REC_BYTES) + up(4 * (TMD_NBIN + 1)) + up(4 * TMD_NBIN) + 256;
+}
+
+// Enqueue the input copies of `in` into device memory at p (on st) and fill
+// the device-side descriptors.
+int place_frame(tmd_handle* h, const tmd_frame_in* in, char* p, cudaStream_t st,
+                tmd_frame_in* d, tmd_frame_out* o) {
+  Field fs[23];
+  if (input_fields(in, d, fs) != TMD_OK)
+    return tmd_set_error(h, TMD_ERR_ARG, "n_attached < n_tracks");
   for (const Field& f : fs) {
     *f.dst = f.bytes ? p : nullptr;
     if (f.bytes) {
@@ -63,27 +81,116 @@ extern "C" int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in,
     }
     p += up(f.bytes);
   }
-  tmd_frame_out o;
-  o.native = reinterpret_cast<uint8_t*>(p);
+  const size_t native_bytes = ((size_t)in->n_attached + in->n_unattached) * TMD_REC_BYTES;
+  o->native = reinterpret_cast<uint8_t*>(p);
   p += up(native_bytes);
-  o.row_start = reinterpret_cast<uint32_t*>(p);
+  o->row_start = reinterpret_cast<uint32_t*>(p);
   p += up(4 * (TMD_NBIN + 1));
-  o.att_count = reinterpret_cast<uint32_t*>(p);
+  o->att_count = reinterpret_cast<uint32_t*>(p);
   p += up(4 * TMD_NBIN);
-  o.status = reinterpret_cast<uint32_t*>(p);
-  int rc = tmd_validate_frame(h, &d, &o);
-  if (rc != TMD_OK) return rc;
-  rc = tmd_launch(h, 1, &d, &o, nullptr, nullptr, st);
-  if (rc != TMD_OK) return rc;
+  o->status = reinterpret_cast<uint32_t*>(p);
+  return tmd_validate_frame(h, d, o);
+}
+
+// Enqueue the result copies of a decoded frame back to the host buffers.
+int fetch_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* o,
+                const tmd_frame_out* out, cudaStream_t st) {
+  const size_t native_bytes = ((size_t)in->n_attached + in->n_unattached) * TMD_REC_BYTES;
   struct Back { void* dst; const void* src; size_t bytes; };
-  const Back bs[] = {{out->native, o.native, native_bytes},
-                     {out->row_start, o.row_start, 4 * (TMD_NBIN + 1)},
-                     {out->att_count, o.att_count, 4 * (size_t)TMD_NBIN},
-                     {out->status, o.status, 4}};
+  const Back bs[] = {{out->native, o->native, native_bytes},
+                     {out->row_start, o->row_start, 4 * (TMD_NBIN + 1)},
+                     {out->att_count, o->att_count, 4 * (size_t)TMD_NBIN},
+                     {out->status, o->status, 4}};
   for (const Back& b : bs) {
     if (!b.dst || !b.bytes) continue;
     const cudaError_t e = cudaMemcpyAsync(b.dst, b.src, b.bytes, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return tmd_cuda_check(h, e, "D2H copy");
   }
+  return TMD_OK;
+}
+
+int grow(tmd_handle* h, void** buf, size_t* have, size_t need) {
+  if (need <= *have) return TMD_OK;
+  if (*buf) {
+    cudaDeviceSynchronize();
+    cudaFree(*buf);
+  }
+  *buf = nullptr;
+  *have = 0;
+  if (cudaMalloc(buf, need) != cudaSuccess) {
+    cudaGetLastError();
+    return tmd_set_error(h, TMD_ERR_NOMEM, "staging allocation of %zu bytes failed", need);
+  }
+  *have = need;
+  return TMD_OK;
+}
+
+}  // namespace
+
+extern "C" int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in,
+                                     const tmd_frame_out* out, void* stream) {
+  if (!h) return TMD_ERR_ARG;
+  if (!in || !out) return tmd_set_error(h, TMD_ERR_ARG, "null descriptor");
+  if (in->n_attached < in->n_tracks) return tmd_set_error(h, TMD_ERR_ARG, "n_attached < n_tracks");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(h->device) != cudaSuccess) return tmd_set_error(h, TMD_ERR_CUDA, "cudaSetDevice");
+  int rc = grow(h, &h->stage, &h->stage_bytes, frame_bytes(in));
+  if (rc != TMD_OK) return rc;
+  tmd_frame_in d;
+  tmd_frame_out o;
+  if ((rc = place_frame(h, in, static_cast<char*>(h->stage), st, &d, &o)) != TMD_OK) return rc;
+  if ((rc = tmd_launch(h, 1, &d, &o, nullptr, nullptr, st)) != TMD_OK) return rc;
+  if ((rc = fetch_frame(h, in, &o, out, st)) != TMD_OK) return rc;
   return tmd_cuda_check(h, cudaStreamSynchronize(st), "stream synchronize");
+}
+
+extern "C" int tmd_decode_host_stream(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
+                                      const tmd_frame_out* out, void* stream) {
+  if (!h) return TMD_ERR_ARG;
+  if (n == 0) return TMD_OK;
+  if (!in || !out) return tmd_set_error(h, TMD_ERR_ARG, "null frame arrays");
+  for (uint32_t i = 0; i < n; i++)
+    if (in[i].n_attached < in[i].n_tracks)
+      return tmd_set_error(h, TMD_ERR_ARG, "frame %u: n_attached < n_tracks", i);
+  if (cudaSetDevice(h->device) != cudaSuccess) return tmd_set_error(h, TMD_ERR_CUDA, "cudaSetDevice");
+  cudaStream_t comp = static_cast<cudaStream_t>(stream);
+  int rc = TMD_OK;
+  if (!h->h2d) {
+    if ((rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking),
+                             "stream")) != TMD_OK ||
+        (rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking),
+                             "stream")) != TMD_OK)
+      return rc;
+    for (int s = 0; s < 2; s++)
+      for (cudaEvent_t* e : {&h->pipe_in[s], &h->pipe_dec[s], &h->pipe_out[s]})
+        if ((rc = tmd_cuda_check(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming),
+                                 "event")) != TMD_OK)
+          return rc;
+  }
+  size_t need = 0;
+  for (uint32_t i = 0; i < n; i++) need = std::max(need, frame_bytes(&in[i]));
+  for (int s = 0; s < 2; s++)
+    if ((rc = grow(h, &h->pipe_buf[s], &h->pipe_bytes[s], need)) != TMD_OK) return rc;
+  // the caller's stream sees the slots only after earlier work on it
+  if ((rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_dec[0], comp), "event")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->h2d, h->pipe_dec[0], 0), "wait")) != TMD_OK)
+    return rc;
+  for (uint32_t i = 0; i < n && rc == TMD_OK; i++) {
+    const int s = (int)(i & 1);
+    tmd_frame_in d;
+    tmd_frame_out o;
+    if (i >= 2) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->h2d, h->pipe_out[s], 0), "wait");
+    if (rc == TMD_OK)
+      rc = place_frame(h, &in[i], static_cast<char*>(h->pipe_buf[s]), h->h2d, &d, &o);
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_in[s], h->h2d), "event");
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(comp, h->pipe_in[s], 0), "wait");
+    if (rc == TMD_OK) rc = tmd_launch(h, 1, &d, &o, nullptr, nullptr, comp);
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_dec[s], comp), "event");
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->d2h, h->pipe_dec[s], 0), "wait");
+    if (rc == TMD_OK) rc = fetch_frame(h, &in[i], &o, &out[i], h->d2h);
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_out[s], h->d2h), "event");
+  }
+  const int rc2 = tmd_cuda_check(h, cudaStreamSynchronize(h->d2h), "stream synchronize");
+  const int rc3 = tmd_cuda_check(h, cudaStreamSynchronize(comp), "stream synchronize");
+  return rc != TMD_OK ? rc : (rc2 != TMD_OK ? rc2 : rc3);
 }

@@ -22,6 +22,9 @@ constexpr int kDecodeThreads = 128;      // threads per block of the track decod
 constexpr int kScatThreads = 256;        // threads per block of the record scatter
 constexpr int kScatPerThread = 8;        // clusters per thread of the record scatter
 constexpr int kScatBlocksPerTile = kTile / (kScatThreads * kScatPerThread);
+constexpr int kScatCta = 8;              // CTAs per thread-block cluster of the regrouping scatter
+constexpr int kScatThreads2 = 512;       // threads per CTA of the regrouping scatter
+constexpr int kScatClusterSmem = (kTile / kScatCta) * 16 + kNBin * 2;
 
 // One frame as the kernels see it: caller inputs, caller outputs, scratch.
 struct FrameDev {
@@ -154,9 +157,11 @@ __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                          PlanDev plan, uint32_t n_tasks);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
-// Record scatter variants 0..2 (identical results; see tmd_decode.cu).
-void launch_att_scatter(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+// Record scatter variants 0..2 (identical results; see tmd_scatter.cu),
+// launched over n_tiles ranking tiles of all frames.
+void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan);
+cudaError_t prepare_att_scatter();
 __global__ void k_unatt_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tickets);
 __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
                                uint32_t n_tasks);

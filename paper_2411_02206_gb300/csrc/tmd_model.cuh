@@ -62,11 +62,10 @@ __constant__ float c_sin20[18] = {
 
 // Per-row geometry, filled in shared memory by every block that needs it:
 // x = 85 + r cm; nPads = 66 + floor(72 r / 151); pad width w = 2 x tan10 / nPads.
+// One 16-byte entry per row {x, w, 1/w, nPads/2}: a model step reads its row
+// with a single shared-memory load.
 struct RowGeo {
-  float x[kNRow];
-  float w[kNRow];
-  float invw[kNRow];
-  float halfnp[kNRow];
+  float4 row[kNRow];
 };
 
 __device__ __forceinline__ void fill_row_geo(RowGeo* g) {
@@ -74,18 +73,17 @@ __device__ __forceinline__ void fill_row_geo(RowGeo* g) {
     const int np = 66 + (72 * r) / 151;
     const float x = 85.0f + (float)r;
     const float w = fdiv(fmul(fmul(2.0f, x), kTan10), (float)np);
-    g->x[r] = x;
-    g->w[r] = w;
-    g->invw[r] = fdiv(1.0f, w);
-    g->halfnp[r] = fmul(0.5f, (float)np);
+    g->row[r] = make_float4(x, w, fdiv(1.0f, w), fmul(0.5f, (float)np));
   }
 }
 
-// Quantiser: clamp to [lo, hi] (NaN to lo), then floor(v + 0.5).
+// Quantiser: clamp to [lo, hi] (NaN to lo), then floor(v + 0.5).  fmaxf
+// returns its non-NaN operand, so NaN clamps to lo; v + 0.5 then lies in
+// [0.5, hi + 0.5] with lo = 0, where the round-down conversion to unsigned
+// equals floor followed by conversion.
 __device__ __forceinline__ uint32_t quant(float v, float lo, float hi) {
-  v = (v >= lo) ? v : lo;
-  v = (v <= hi) ? v : hi;
-  return (uint32_t)floorf(fadd(v, 0.5f));
+  v = fminf(fmaxf(v, lo), hi);
+  return __float2uint_rd(fadd(v, 0.5f));
 }
 
 struct Track {
@@ -97,8 +95,10 @@ struct Track {
   int sec;
 };
 
-__device__ __forceinline__ float pad_to_y(const RowGeo* g, uint32_t padq, int r) {
-  return fmul(fsub(fmul((float)padq, 0.015625f), g->halfnp[r]), g->w[r]);
+// y of a pad code on a row with geometry G = {x, w, 1/w, nPads/2}:
+// (pad - nPads/2) * w.
+__device__ __forceinline__ float pad_to_y(const float4& G, uint32_t padq) {
+  return fmul(fsub(fmul((float)padq, 0.015625f), G.w), G.y);
 }
 __device__ __forceinline__ float time_to_t(uint32_t timeq) {
   return fmul((float)timeq, 0.03125f);
@@ -117,8 +117,9 @@ __device__ __forceinline__ void seed(const RowGeo* g, Track& s, uint8_t qpta, in
   s.raw_row = raw_row;
   s.row = raw_row < kNRow ? raw_row : kNRow - 1;
   s.sec = sec;
-  s.x = g->x[s.row];
-  s.y = pad_to_y(g, padq, s.row);
+  const float4 G = g->row[s.row];
+  s.x = G.x;
+  s.y = pad_to_y(G, padq);
   s.c = fmul(-kKC, qpt);
   s.ty = fadd(fdiv(s.y, s.x), fmul(fmul(s.c, s.x), 0.5f));
   s.c00 = kSY2; s.c01 = 0.0f; s.c02 = 0.0f;
@@ -178,12 +179,12 @@ __device__ __forceinline__ uint32_t key_step(Track& s, uint32_t row_diff, uint32
   return st;
 }
 
-// Propagate to the plane of the current row and return the quantised
-// prediction (pad code, time code).
-__device__ __forceinline__ void propagate_predict(const RowGeo* g, Track& s, uint32_t& ppad,
+// Propagate to the plane of the current row, whose geometry is
+// G = {x, w, 1/w, nPads/2} (RowGeo), and return the quantised prediction
+// (pad code, time code).
+__device__ __forceinline__ void propagate_predict(const float4& G, Track& s, uint32_t& ppad,
                                                   uint32_t& ptime) {
-  const int r = s.row;
-  const float xr = g->x[r];
+  const float xr = G.x;
   const float dx = fsub(xr, s.x);
   const float adx = fabsf(dx);
   const float h = fmul(fmul(0.5f, s.c), dx);
@@ -207,14 +208,14 @@ __device__ __forceinline__ void propagate_predict(const RowGeo* g, Track& s, uin
   s.d00 = fadd(e0, fmul(dx, e1));
   s.d01 = e1;
   s.d11 = fadd(s.d11, fmul(kQTT, adx));
-  const float pp = fadd(fmul(s.y, g->invw[r]), g->halfnp[r]);
+  const float pp = fadd(fmul(s.y, G.z), G.w);
   ppad = quant(fmul(pp, 64.0f), 0.0f, kPadHi);
   ptime = quant(fmul(s.t, 32.0f), 0.0f, kTimeHi);
 }
 
-// Kalman update with the measured cluster.
-__device__ __forceinline__ void update(const RowGeo* g, Track& s, uint32_t padq, uint32_t timeq) {
-  const float ym = pad_to_y(g, padq, s.row);
+// Kalman update with the measured cluster (G: geometry of the current row).
+__device__ __forceinline__ void update(const float4& G, Track& s, uint32_t padq, uint32_t timeq) {
+  const float ym = pad_to_y(G, padq);
   const float tm = time_to_t(timeq);
   const float inv = frcp(fadd(s.c00, kSY2));
   const float k0 = fmul(s.c00, inv), k1 = fmul(s.c01, inv), k2 = fmul(s.c02, inv);

@@ -179,7 +179,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   if (n_grp) k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
   k_row_offsets<<<1, 1024, 0, st>>>(dframe, P);
   if (n_grp) k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
-  if (n_tile) launch_att_scatter(0, n_tile * kScatBlocksPerTile, st, dframe, P);
+  if (n_tile) launch_att_scatter(0, n_tile, st, dframe, P);
   if (n_chunk) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_unatt);
     k_unatt_decode<<<n_chunk < cap ? n_chunk : cap, 256, 0, st>>>(dframe, P, n_chunk);

@@ -93,6 +93,8 @@ def lib():
                                      ctypes.POINTER(tmd_frame_out), _P],
                 "tmd_decode_frame_host": [H, ctypes.POINTER(tmd_frame_in),
                                           ctypes.POINTER(tmd_frame_out), _P],
+                "tmd_decode_host_stream": [H, ctypes.c_uint32, ctypes.POINTER(tmd_frame_in),
+                                           ctypes.POINTER(tmd_frame_out), _P],
                 "tmd_encode_tracks": [H, ctypes.POINTER(tmd_truth_in),
                                       ctypes.POINTER(tmd_track_out), _P],
                 "tmd_submit": [H, ctypes.POINTER(tmd_frame_in), ctypes.POINTER(ctypes.c_uint64)],
@@ -224,6 +226,13 @@ class Decoder:
     def tmd_decode_frame_host(self, fin: tmd_frame_in, fout: tmd_frame_out, stream=None) -> int:
         return self._check(self._L.tmd_decode_frame_host(
             self.h, ctypes.byref(fin), ctypes.byref(fout), _P(_stream_ptr(stream))))
+
+    def tmd_decode_host_stream(self, fins, fouts, stream=None) -> int:
+        n = len(fins)
+        ins = (tmd_frame_in * n)(*fins)
+        outs = (tmd_frame_out * n)(*fouts)
+        return self._check(self._L.tmd_decode_host_stream(self.h, n, ins, outs,
+                                                          _P(_stream_ptr(stream))))
 
     def tmd_encode_tracks(self, tin: tmd_truth_in, tout: tmd_track_out, stream=None) -> int:
         return self._check(self._L.tmd_encode_tracks(self.h, ctypes.byref(tin), ctypes.byref(tout),

@@ -184,18 +184,21 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
     ora = O.decode(of)
     dev = frames.to_torch(of, "cuda:0")
     saved = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
-                                               "scatter_variant")}
+                                               "scatter_variant", "overlap")}
     try:
-        for dv in range(4):
-            for rv in range(2):
-                for sv in range(3):
-                    dec.tmd_tune_set("decode_variant", dv)
-                    dec.tmd_tune_set("rank_variant", rv)
-                    dec.tmd_tune_set("scatter_variant", sv)
-                    native, rs, att, st = dec.decode(dev)
-                    gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
-                           frames.to_numpy(att, np.uint32), int(st.item()))
-                    G.assert_same_decode(gpu, ora, f"decode {dv} rank {rv} scatter {sv}")
+        for ov in range(2):
+            for dv in range(4):
+                for rv in range(2):
+                    for sv in range(3):
+                        dec.tmd_tune_set("overlap", ov)
+                        dec.tmd_tune_set("decode_variant", dv)
+                        dec.tmd_tune_set("rank_variant", rv)
+                        dec.tmd_tune_set("scatter_variant", sv)
+                        native, rs, att, st = dec.decode(dev)
+                        gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
+                               frames.to_numpy(att, np.uint32), int(st.item()))
+                        G.assert_same_decode(gpu, ora,
+                                             f"overlap {ov} decode {dv} rank {rv} scatter {sv}")
     finally:
         for k, v in saved.items():
             dec.tmd_tune_set(k, v)
@@ -228,3 +231,25 @@ def test_unaligned_caller_arrays(dec):
             G.assert_same_decode(gpu, ora, f"unaligned, scatter {sv} decode {dv}")
     dec.tmd_tune_set("scatter_variant", 0)
     dec.tmd_tune_set("decode_variant", 1)
+
+
+def test_host_stream_pipeline(dec):
+    """tmd_decode_host_stream over frames of different sizes (more frames than
+    device slots) gives every frame the oracle's result."""
+    from paper_2411_02206_gb300 import frames, tmd
+    ofs, fins, fouts, outs, keep = [], [], [], [], []
+    for i, (nt, nu) in enumerate(((900, 20_000), (2500, 5_000), (0, 7_000), (1700, 30_000),
+                                  (300, 0))):
+        of = G.oracle_frame(synth.make_truth(n_tracks=nt, n_unatt=nu, seed=40 + i))
+        host = frames.to_torch(of, None, pin=True)
+        keep.append(host)  # the descriptors hold raw pointers into these tensors
+        _, na, nu2 = tmd.counts(host)
+        o = (np.zeros((na + nu2, 12), np.uint8), np.zeros(5473, np.uint32),
+             np.zeros(5472, np.uint32), np.zeros(1, np.uint32))
+        ofs.append(of)
+        outs.append(o)
+        fins.append(tmd.frame_in(host))
+        fouts.append(tmd.frame_out(*o))
+    dec.tmd_decode_host_stream(fins, fouts)
+    for i, (of, o) in enumerate(zip(ofs, outs)):
+        G.assert_same_decode((o[0], o[1], o[2], int(o[3][0])), O.decode(of), f"stream frame {i}")
