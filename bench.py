@@ -58,6 +58,25 @@ def _dist():
     return world, rank, local
 
 
+def _reduce(x: float, op: str, device="cpu") -> float:
+    """x reduced over the ranks of the process group ("max" or "sum"); x
+    itself when the process runs alone."""
+    import torch
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units: float, seconds: float, device="cpu") -> float:
+    """Weak scaling: every rank decodes its own frame (units clusters in
+    `seconds`); the job's value is all ranks' units over the slowest rank's
+    time."""
+    return _reduce(units, "sum", device) / _reduce(seconds, "max", device)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling while the timed region runs."""
 
@@ -299,12 +318,8 @@ def run(args):
     dec.tmd_profile_enable(False)
     prof = dec.tmd_profile_read()
     ms = start.elapsed_time(stop)
-    if world > 1:
-        t = torch.tensor([ms], device=native.device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
-    value = world * (na + nu) / (ms_step * 1e-3)
+    ms_step = _reduce(ms, "max", native.device) / args.steps
+    value = whole_job_rate(args.steps * (na + nu), ms * 1e-3, native.device)
     launches = sum(c for _, c in prof.values())
     # roofline of the dominant kernel
     top = max(prof.items(), key=lambda kv: kv[1][0])
@@ -346,13 +361,9 @@ def run(args):
     t0 = time.perf_counter()
     dec.tmd_decode_host_stream([hin] * e2e_steps, [hout] * e2e_steps, stream)
     barrier()
-    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    e2e_dt = time.perf_counter() - t0
     assert torch.equal(h_native, native.cpu()), "host entry point disagrees with device path"
-    e2e_value = world * (na + nu) / e2e_dt
-    if world > 1:
-        t = torch.tensor([e2e_dt], device=native.device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = world * (na + nu) / float(t.item())
+    e2e_value = whole_job_rate(e2e_steps * (na + nu), e2e_dt, native.device)
     line = None
     if rank == 0:
         base = cpu_baseline(truth) if not args.no_cpu_baseline else None

@@ -196,10 +196,10 @@ int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in, const tmd_frame
 
 /* Decode n frames given HOST buffers, pipelined (arXiv:2411.02206, Sec. 3 and
  * Fig. 3: several instances on streams hide the transfers): frame i's inputs
- * are copied to one of two handle-owned device slots on a copy stream while
- * frame i - 1 is decoded on `stream` and frame i - 2's native list, row
- * offsets, attached counts and status are copied back to out[i - 2] on a
- * second copy stream.  in[i] / out[i] hold host pointers as in
+ * are copied to one of three handle-owned device slots on a copy stream while
+ * earlier frames are decoded on `stream` and their native lists, row offsets,
+ * attached counts and status are copied back to out[] on a second copy
+ * stream.  in[i] / out[i] hold host pointers as in
  * tmd_decode_frame_host; the device slots are sized for the largest frame
  * and kept for later calls.  Synchronous on return; results equal those of n
  * tmd_decode_frame_host calls.  Pinned host memory is required for the
@@ -256,13 +256,15 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *                               16 model steps staged synchronously (0, 1), or
  *                               rounds of 8 or 16 steps double-buffered with
  *                               asynchronous copies (2, 3)
- *   "rank_variant"        0..1  ranking of equal keys: match.any on every
+ *   "rank_variant"        0..2  ranking of equal keys: match.any on every
  *                               step (0) or only on steps with repeated keys,
- *                               found with a shared-memory bitmap (1)
- *   "scatter_variant"     0..2  stores of the record scatter: one record per
+ *                               found with a shared-memory bitmap per step (1)
+ *                               or per group of 8 steps (2)
+ *   "scatter_variant"     0..3  stores of the record scatter: one record per
  *                               thread (0), three lanes per record in one
- *                               store instruction (1), or a whole ranking
- *                               tile regrouped in (bin, rank) order through
+ *                               store instruction (1; 3: with 2 instead of 4
+ *                               clusters per thread), or a whole ranking tile
+ *                               regrouped in (bin, rank) order through
  *                               distributed shared memory first (2)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)

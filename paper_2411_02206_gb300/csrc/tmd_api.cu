@@ -175,7 +175,7 @@ tmd_handle::~tmd_handle() {
   if (join) cudaEventDestroy(join);
   if (h2d) cudaStreamSynchronize(h2d), cudaStreamDestroy(h2d);
   if (d2h) cudaStreamSynchronize(d2h), cudaStreamDestroy(d2h);
-  for (int s = 0; s < 2; s++) {
+  for (int s = 0; s < kPipeSlots; s++) {
     if (pipe_buf[s]) cudaFree(pipe_buf[s]);
     for (cudaEvent_t e : {pipe_in[s], pipe_dec[s], pipe_out[s]})
       if (e) cudaEventDestroy(e);

@@ -65,13 +65,13 @@ struct tmd_handle {
   TmdProfile prof;
   cudaStream_t aux = nullptr;              // second stream of the plain decode chain
   cudaEvent_t fork = nullptr, join = nullptr;
-  // host streaming pipeline (tmd_decode_host_stream): copy streams, two
-  // device slots and their events
+  // host streaming pipeline (tmd_decode_host_stream): copy streams, device
+  // slots and their events
+  static constexpr int kPipeSlots = 3;
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  void* pipe_buf[2] = {nullptr, nullptr};
-  size_t pipe_bytes[2] = {0, 0};
-  cudaEvent_t pipe_in[2] = {nullptr, nullptr}, pipe_dec[2] = {nullptr, nullptr},
-              pipe_out[2] = {nullptr, nullptr};
+  void* pipe_buf[kPipeSlots] = {};
+  size_t pipe_bytes[kPipeSlots] = {};
+  cudaEvent_t pipe_in[kPipeSlots] = {}, pipe_dec[kPipeSlots] = {}, pipe_out[kPipeSlots] = {};
 
   int ensure_scratch(size_t bytes);
   int acquire_slot(size_t bytes, int& slot);

@@ -275,10 +275,11 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
   using Lay = AsyncLayout<R>;
   constexpr int P = R + 1;   // pitch of the output rows
   constexpr int G = 32 / R;  // tracks per write-out instruction
-  __shared__ RowGeo geo;
+  __shared__ RowGeo geo_s;
   __shared__ AsyncStage<R> stage[kDecodeThreads / 32];
-  fill_row_geo(&geo);
+  fill_row_geo(&geo_s);
   __syncthreads();
+  const RowGeo* geo = &geo_s;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t sq = lane % R, sg = lane / R;
   AsyncStage<R>& S = stage[threadIdx.x >> 5];
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
       time0 = F.time[t];
       const uint32_t raw = F.row[t], sec = F.slice[t];
       if (raw >= (uint32_t)kNRow || sec >= (uint32_t)kNSec) st |= kStRow;
-      seed(&geo, s, F.qpt[t], (int)raw, sec < (uint32_t)kNSec ? (int)sec : kNSec - 1, pad0,
+      seed(geo, s, F.qpt[t], (int)raw, sec < (uint32_t)kNSec ? (int)sec : kNSec - 1, pad0,
            time0);
     }
     const uint32_t nmax = __reduce_max_sync(kFull, n);
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
             const uint32_t prv = (lb[2 * Lay::kRd + (ppr >> 1)] >> (16 * (ppr & 1))) & 0xFFFFu;
             st |= key_step(s, rdv, slv);
             uint32_t ppad, ptime;
-            const float4 G = geo.row[s.row];
+            const float4 G = geo->row[s.row];
             propagate_predict(G, s, ppad, ptime);
             padq = (ppad + prv) & 0xFFFFu;
             timeq = ptime + lb[Lay::kTr0 + q];

@@ -6,11 +6,12 @@
 //
 // tmd_decode_host_stream: the same for a sequence of frames, pipelined the
 // way Sec. 3 of arXiv:2411.02206 runs several decoding instances on streams
-// to hide the transfers (Fig. 3): two device slots; frame i's inputs go up on
-// a host-to-device copy stream while frame i - 1 is decoded on the compute
-// stream and frame i - 2's results come back on a device-to-host copy
+// to hide the transfers (Fig. 3): kPipeSlots device slots; frame i's inputs
+// go up on a host-to-device copy stream while earlier frames are decoded on
+// the compute stream and their results come back on a device-to-host copy
 // stream.  A slot is refilled only after the results of the frame that last
-// used it have left.
+// used it have left; with three slots the upload of frame i waits for the
+// download of frame i - 3, so both copy directions stay busy.
 #include <algorithm>
 #include <cstring>
 
@@ -161,7 +162,7 @@ extern "C" int tmd_decode_host_stream(tmd_handle* h, uint32_t n, const tmd_frame
         (rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking),
                              "stream")) != TMD_OK)
       return rc;
-    for (int s = 0; s < 2; s++)
+    for (int s = 0; s < tmd_handle::kPipeSlots; s++)
       for (cudaEvent_t* e : {&h->pipe_in[s], &h->pipe_dec[s], &h->pipe_out[s]})
         if ((rc = tmd_cuda_check(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming),
                                  "event")) != TMD_OK)
@@ -169,17 +170,19 @@ extern "C" int tmd_decode_host_stream(tmd_handle* h, uint32_t n, const tmd_frame
   }
   size_t need = 0;
   for (uint32_t i = 0; i < n; i++) need = std::max(need, frame_bytes(&in[i]));
-  for (int s = 0; s < 2; s++)
+  const int slots = (int)std::min<uint32_t>(n, tmd_handle::kPipeSlots);
+  for (int s = 0; s < slots; s++)
     if ((rc = grow(h, &h->pipe_buf[s], &h->pipe_bytes[s], need)) != TMD_OK) return rc;
   // the caller's stream sees the slots only after earlier work on it
   if ((rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_dec[0], comp), "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->h2d, h->pipe_dec[0], 0), "wait")) != TMD_OK)
     return rc;
   for (uint32_t i = 0; i < n && rc == TMD_OK; i++) {
-    const int s = (int)(i & 1);
+    const int s = (int)(i % slots);
     tmd_frame_in d;
     tmd_frame_out o;
-    if (i >= 2) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->h2d, h->pipe_out[s], 0), "wait");
+    if (i >= (uint32_t)slots)
+      rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->h2d, h->pipe_out[s], 0), "wait");
     if (rc == TMD_OK)
       rc = place_frame(h, &in[i], static_cast<char*>(h->pipe_buf[s]), h->h2d, &d, &o);
     if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_in[s], h->h2d), "event");

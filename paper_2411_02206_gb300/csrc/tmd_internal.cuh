@@ -20,8 +20,6 @@ constexpr int kChunk = 2048;             // unattached clusters per scan chunk
 constexpr int kLenBuckets = 1024;        // track-length buckets of the decode order
 constexpr int kDecodeThreads = 128;      // threads per block of the track decoder
 constexpr int kScatThreads = 256;        // threads per block of the record scatter
-constexpr int kScatPerThread = 8;        // clusters per thread of the record scatter
-constexpr int kScatBlocksPerTile = kTile / (kScatThreads * kScatPerThread);
 constexpr int kScatCta = 8;              // CTAs per thread-block cluster of the regrouping scatter
 constexpr int kScatThreads2 = 512;       // threads per CTA of the regrouping scatter
 constexpr int kScatClusterSmem = (kTile / kScatCta) * 16 + kNBin * 2;
@@ -142,7 +140,8 @@ __global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);
 __global__ void k_track_scan2(const FrameDev* frames, PlanDev plan);
 // Ranking variants (identical results): 0 orders equal keys of a step with
 // match.any, 1 detects duplicate keys with a shared-memory bitmap and falls
-// back to match.any only for steps that have some.
+// back to match.any only for steps that have some, 2 does the same test for
+// groups of 8 steps.
 void launch_count_rank(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                        PlanDev plan);
 cudaError_t prepare_count_rank();
@@ -157,7 +156,7 @@ __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                          PlanDev plan, uint32_t n_tasks);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
-// Record scatter variants 0..2 (identical results; see tmd_scatter.cu),
+// Record scatter variants 0..3 (identical results; see tmd_scatter.cu),
 // launched over n_tiles ranking tiles of all frames.
 void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan);

@@ -17,7 +17,10 @@
 //                 per-warp bitmap (atom.or returns the bit's old value) and
 //                 takes the match.any path only when some key repeats;
 //                 consecutive clusters mostly belong to one track and lie in
-//                 distinct rows, so most steps take the short path.
+//                 distinct rows, so most steps take the short path.  Variant
+//                 2 tests 8 steps (256 keys) at once: without a repeated key
+//                 the 8 steps' count reads and writes are independent and
+//                 issue together; a group with one runs step by step.
 //
 // The native index of cluster j is then tileBase[tile][key] + rank[j].
 #include "tmd_internal.cuh"
@@ -94,6 +97,35 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
       const uint32_t j = b0 + 32u * u + lane;
       kk[u] = j < j_end ? (uint32_t)keys[j] : 0xFFFFFFFFu;
     }
+    if constexpr (V == 2) {
+      // all 256 keys distinct: every rank is the bin's count so far, and the
+      // 8 steps' reads and writes of the counts are independent
+      uint32_t dup = 0;
+#pragma unroll
+      for (int u = 0; u < 8; u++)
+        if (kk[u] != 0xFFFFFFFFu) dup |= atomicOr(&bm[kk[u] >> 5], 1u << (kk[u] & 31)) & (1u << (kk[u] & 31));
+      const bool clash = __any_sync(0xffffffffu, dup != 0);
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 8; u++)
+        if (kk[u] != 0xFFFFFFFFu) bm[kk[u] >> 5] = 0u;  // every bit of the word was set here
+      __syncwarp();
+      if (!clash) {
+        uint32_t base[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) base[u] = kk[u] != 0xFFFFFFFFu ? hist[kk[u]] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          const uint32_t j = b0 + 32u * u + lane;
+          if (kk[u] != 0xFFFFFFFFu) {
+            hist[kk[u]] = (uint16_t)(base[u] + 1);
+            rank[j] = (uint16_t)base[u];
+          }
+        }
+        __syncwarp();
+        continue;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       const uint32_t j = b0 + 32u * u + lane;
@@ -134,7 +166,9 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
 
 void launch_count_rank(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                        PlanDev plan) {
-  if (variant == 1)
+  if (variant == 2)
+    k_count_rank<2><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
+  else if (variant == 1)
     k_count_rank<1><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
   else
     k_count_rank<0><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
@@ -145,6 +179,9 @@ cudaError_t prepare_count_rank() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kCountRankSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_count_rank<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kCountRankSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_count_rank<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kCountRankSmem);
   return e;
 }

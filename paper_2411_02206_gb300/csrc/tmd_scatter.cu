@@ -23,26 +23,27 @@ namespace cg = cooperative_groups;
 
 namespace tmd {
 
-// k_att_scatter: kScatPerThread = 8 attached clusters per thread, at a stride
-// of the block size (one scalar load per stream and cluster, consecutive
-// lanes on consecutive clusters); bin bases read through L1.  A block covers
-// kScatThreads * 8 consecutive clusters of one ranking tile.  Variants
-// (identical results):
+// k_att_scatter: U attached clusters per thread (U = 4 or 2), at a stride of
+// the block size (one scalar load per stream and cluster, consecutive lanes
+// on consecutive clusters, all loads of a thread issued before the first is
+// used); bin bases read through L1.  A block covers kScatThreads * U
+// consecutive clusters of one ranking tile.  Variants (identical results):
 //   V = 0  every thread writes its own records (an 8- and a 4-byte store);
 //   V = 1  the warp writes 10 records per store instruction: lane 3m + c
 //          writes word c of the record held by lane m of the group, so each
 //          record costs one L2 write request (two when it straddles a
 //          32-byte sector) instead of two.
-template <int V>
+template <int V, int U>
 __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev* frames,
                                                                  PlanDev plan) {
-  const uint32_t gtile = blockIdx.x / kScatBlocksPerTile;
+  constexpr uint32_t kPerBlock = kScatThreads * U;
+  constexpr uint32_t kBlocksPerTile = kTile / kPerBlock;
+  const uint32_t gtile = blockIdx.x / kBlocksPerTile;
   const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
   const FrameDev& F = frames[f];
   if (*F.status & kStCount) return;
   const uint32_t tile = gtile - plan.pre_tile[f];
-  const uint32_t jb = tile * (uint32_t)kTile +
-                      (blockIdx.x % kScatBlocksPerTile) * (uint32_t)(kTile / kScatBlocksPerTile);
+  const uint32_t jb = tile * (uint32_t)kTile + (blockIdx.x % kBlocksPerTile) * kPerBlock;
   const uint32_t n_att = F.n_att, n_total = F.n_att + F.n_unatt;
   const uint16_t* __restrict__ keys = F.keys;
   const uint16_t* __restrict__ rank = F.rank;
@@ -56,33 +57,37 @@ __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev*
   const uint32_t* __restrict__ tbase = F.tile_base + (size_t)tile * kNBin;
   uint32_t* __restrict__ nat = reinterpret_cast<uint32_t*>(F.native);
   const uint32_t lane = threadIdx.x & 31;
-  // 8 clusters per thread: keys and ranks, pad codes, time codes, charges
-  uint32_t kr[8], pd[8], tm[8], qq[8], fs[8];
+  // U clusters per thread: the raw loads first, combined afterwards
+  uint32_t ky[U], rk[U], pd[U], tm[U], qm[U], qt[U], fl[U], sg[U], sp[U];
 #pragma unroll
-  for (int u = 0; u < 8; u++) {
+  for (int u = 0; u < U; u++) {
     const uint32_t j = jb + u * kScatThreads + threadIdx.x;
-    kr[u] = 0xFFFFFFFFu;
+    ky[u] = 0xFFFFu;
     if (j < n_att) {
-      kr[u] = (uint32_t)keys[j] | ((uint32_t)rank[j] << 16);
+      ky[u] = keys[j];
+      rk[u] = rank[j];
       pd[u] = kpad[j];
       tm[u] = ktime[j];
-      qq[u] = (uint32_t)qmax[j] | ((uint32_t)qtot[j] << 16);
-      fs[u] = (uint32_t)flags[j] | ((uint32_t)sigt[j] << 8) | ((uint32_t)sigp[j] << 16);
+      qm[u] = qmax[j];
+      qt[u] = qtot[j];
+      fl[u] = flags[j];
+      sg[u] = sigt[j];
+      sp[u] = sigp[j];
     }
   }
   uint32_t st = 0;
 #pragma unroll
-  for (int u = 0; u < 8; u++) {
+  for (int u = 0; u < U; u++) {
     uint32_t p = 0xFFFFFFFFu, w0 = 0, w1 = 0, w2 = 0;
-    if (kr[u] != 0xFFFFFFFFu) {
-      p = __ldg(tbase + (kr[u] & 0xFFFFu)) + (kr[u] >> 16);
+    if (ky[u] != 0xFFFFu) {
+      p = __ldg(tbase + ky[u]) + rk[u];
       if (p >= n_total) {
         st |= kStLimit;
         p = 0xFFFFFFFFu;
       }
-      w0 = (tm[u] & 0xFFFFFFu) | ((fs[u] & 0xFFu) << 24);
-      w1 = pd[u] | ((fs[u] >> 8) << 16);
-      w2 = qq[u];
+      w0 = (tm[u] & 0xFFFFFFu) | (fl[u] << 24);
+      w1 = pd[u] | (sg[u] << 16) | (sp[u] << 24);
+      w2 = qm[u] | (qt[u] << 16);
     }
     if constexpr (V == 0) {
       if (p != 0xFFFFFFFFu) {
@@ -248,11 +253,12 @@ cudaError_t prepare_att_scatter() {
 void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan) {
   switch (variant) {
-    case 1: k_att_scatter<1><<<n_tiles * kScatBlocksPerTile, kScatThreads, 0, st>>>(frames, plan); break;
+    case 1: k_att_scatter<1, 4><<<n_tiles * (kTile / (kScatThreads * 4)), kScatThreads, 0, st>>>(frames, plan); break;
     case 2:
       k_att_scatter_cluster<<<n_tiles * kScatCta, kScatThreads2, kScatClusterSmem, st>>>(frames, plan);
       break;
-    default: k_att_scatter<0><<<n_tiles * kScatBlocksPerTile, kScatThreads, 0, st>>>(frames, plan); break;
+    case 3: k_att_scatter<1, 2><<<n_tiles * (kTile / (kScatThreads * 2)), kScatThreads, 0, st>>>(frames, plan); break;
+    default: k_att_scatter<0, 4><<<n_tiles * (kTile / (kScatThreads * 4)), kScatThreads, 0, st>>>(frames, plan); break;
   }
 }
 

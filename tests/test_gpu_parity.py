@@ -188,8 +188,8 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
     try:
         for ov in range(2):
             for dv in range(4):
-                for rv in range(2):
-                    for sv in range(3):
+                for rv in range(3):
+                    for sv in range(4):
                         dec.tmd_tune_set("overlap", ov)
                         dec.tmd_tune_set("decode_variant", dv)
                         dec.tmd_tune_set("rank_variant", rv)
@@ -221,7 +221,7 @@ def test_unaligned_caller_arrays(dec):
         buf = torch.zeros(t.numel() + 1, dtype=t.dtype, device=t.device)
         buf[1:] = t
         shifted[k] = buf[1:]
-    for sv in range(3):
+    for sv in range(4):
         dec.tmd_tune_set("scatter_variant", sv)
         for dv in range(4):
             dec.tmd_tune_set("decode_variant", dv)
@@ -253,3 +253,12 @@ def test_host_stream_pipeline(dec):
     dec.tmd_decode_host_stream(fins, fouts)
     for i, (of, o) in enumerate(zip(ofs, outs)):
         G.assert_same_decode((o[0], o[1], o[2], int(o[3][0])), O.decode(of), f"stream frame {i}")
+
+
+@pytest.mark.slow
+def test_full_size_stress_frame(dec):
+    """The full stress configuration (1 M tracks with mean pT 0.2 GeV/c, many
+    multi-leg loopers, 40 % of rows empty, 60 M unattached clusters in 10 % of
+    the bins): GPU encoder and decoder against the oracle on every field."""
+    truth = synth.shape_truth("stress")
+    _check_truth(dec, truth, "stress full size")
