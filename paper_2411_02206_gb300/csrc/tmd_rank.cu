@@ -89,13 +89,21 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
     tile_hist[(size_t)tile * kNBin + b] = (uint16_t)run;
   }
   __syncthreads();
-  // pass 2: stable ranks in stream order, the keys of 8 steps in flight
+  // pass 2: stable ranks in stream order; the keys of the next 8 steps are
+  // loaded while the current 8 are ranked
+  uint32_t nk[8];
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    const uint32_t j = j_begin + 32u * u + lane;
+    nk[u] = j < j_end ? (uint32_t)keys[j] : 0xFFFFFFFFu;
+  }
   for (uint32_t b0 = j_begin; b0 < j_end; b0 += 8u * 32u) {
     uint32_t kk[8];
 #pragma unroll
     for (int u = 0; u < 8; u++) {
-      const uint32_t j = b0 + 32u * u + lane;
-      kk[u] = j < j_end ? (uint32_t)keys[j] : 0xFFFFFFFFu;
+      kk[u] = nk[u];
+      const uint32_t j = b0 + 256u + 32u * u + lane;
+      nk[u] = j < j_end ? (uint32_t)keys[j] : 0xFFFFFFFFu;
     }
     if constexpr (V == 2) {
       // all 256 keys distinct: every rank is the bin's count so far, and the
