@@ -227,6 +227,26 @@ int tmd_decode_host_stream(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
 int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_out* out, void* stream,
                              char* err, size_t err_len);
 
+/* Failure detection self-test: every wait inside the kernels (the look-back
+ * of the unattached decode) polls a bounded number of times (about a second)
+ * and then sets TMD_STATUS_TIMEOUT instead of hanging.  This runs that wait
+ * on a word that nothing publishes and returns the resulting status word in
+ * *status (TMD_STATUS_TIMEOUT when the bound works); the device stays usable.
+ * Synchronous; takes about a second. */
+int tmd_selftest_wait(tmd_handle* h, uint32_t* status);
+
+/* Float-path trace (debugging; the state-level parity test): walk the tracks
+ * track_ids[0..n) of the device-resident frame `in` exactly as the decoder
+ * does and write the binary32 model state after each of their clusters to
+ * state[((i * 152) + k) * 17 + m] for track_ids[i], cluster k < min(nCl, 152):
+ * m = 0..16 is x, y, dy/dx, d2y/dx2, the y covariance (00, 01, 02, 11, 12,
+ * 22), t, dt/dx, the t covariance (00, 01, 11), row, sector (the last two as
+ * floats).  track_ids and state are device pointers (state holds n * 152 *
+ * 17 floats; entries past a track's length are left as they were).  Track ids
+ * >= n_tracks are skipped.  Asynchronous on `stream`. */
+int tmd_track_trace(tmd_handle* h, const tmd_frame_in* in, uint32_t n, const uint32_t* track_ids,
+                    float* state, void* stream);
+
 /* Track-model encoding of the attached clusters (the synchronous side of
  * Sec. 3), device buffers, asynchronous on `stream`. */
 int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,

@@ -170,6 +170,7 @@ tmd_handle::~tmd_handle() {
   }
   if (scratch) cudaFree(scratch);
   if (stage) cudaFree(stage);
+  if (trace_status) cudaFree(trace_status);
   if (aux) cudaStreamDestroy(aux);
   if (fork) cudaEventDestroy(fork);
   if (join) cudaEventDestroy(join);
@@ -200,6 +201,7 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
   int rc = TMD_OK;
   if ((rc = tmd_cuda_check(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount,
                                                     h->device), "sm count")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaMalloc(&h->trace_status, 256), "allocation")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking),
                            "stream")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming),
@@ -359,7 +361,8 @@ void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin
 }
 
 int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
-               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st) {
+               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st,
+               const TraceReq* trace) {
   CK(cudaSetDevice(h->device));
   size_t scratch_bytes = 0, record_bytes = 0;
   tmd_call_sizes(nf, in, tin, &scratch_bytes, &record_bytes);
@@ -370,7 +373,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   tmd_handle::Slot& S = h->slots[slot];
   const bool two = h->tune_overlap && !tin;
   rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on,
-                   two ? h->aux : nullptr, h->fork, h->join);
+                   two ? h->aux : nullptr, h->fork, h->join, trace);
   if (rc != TMD_OK) return rc;
   CK(cudaEventRecord(S.done, st));
   S.used = true;
@@ -380,7 +383,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                 const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
                 void* host_record, void* dev_record, cudaStream_t st, bool profile,
-                cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join) {
+                cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join, const TraceReq* trace) {
   const bool encode = tin != nullptr;
   std::vector<FrameLayout> L;
   size_t zbytes = 0, pbytes = 0;
@@ -492,7 +495,11 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   if (n_tblk) timed(kKTrackScan1, [&] { k_track_scan1<<<n_tblk, 256, 0, st>>>(dframes, P); });
   timed(kKFrameScan, [&] { k_frame_scan<<<nf, 1024, 0, st>>>(dframes, P); });
   if (n_tblk) timed(kKTrackScan2, [&] { k_track_scan2<<<n_tblk, 256, 0, st>>>(dframes, P); });
-  if (encode) {
+  if (trace) {
+    if (trace->n)
+      k_track_trace<<<(trace->n + 127) / 128, 128, 0, st>>>(dframes, trace->ids, trace->n,
+                                                            trace->state);
+  } else if (encode) {
     if (n_warp) {
       const uint32_t grid = std::min<uint32_t>(n_warp / 8 + 1, (uint32_t)(h->sms * h->occ_encode));
       timed(kKTrackEncode, [&] { k_track_encode<<<grid, 256, 0, st>>>(denc, dframes, P, n_warp); });
@@ -560,6 +567,37 @@ extern "C" int tmd_decode_batch(tmd_handle* h, uint32_t n, const tmd_frame_in* i
     if (rc != TMD_OK) return rc;
   }
   return tmd_launch(h, n, in, out, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int tmd_selftest_wait(tmd_handle* h, uint32_t* status) {
+  if (!h || !status) return TMD_ERR_ARG;
+  CK(cudaSetDevice(h->device));
+  // word 0: the status, words 2-3: the 64-bit word that nothing publishes
+  CK(cudaMemset(h->trace_status, 0, 16));
+  k_selftest_wait<<<1, 32>>>(reinterpret_cast<const unsigned long long*>(h->trace_status + 2),
+                             h->trace_status);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy(status, h->trace_status, 4, cudaMemcpyDeviceToHost));
+  return TMD_OK;
+}
+
+extern "C" int tmd_track_trace(tmd_handle* h, const tmd_frame_in* in, uint32_t n,
+                               const uint32_t* track_ids, float* state, void* stream) {
+  if (!h) return TMD_ERR_ARG;
+  if (!in) return tmd_set_error(h, TMD_ERR_ARG, "null frame descriptor");
+  if (n && (!track_ids || !state)) return tmd_set_error(h, TMD_ERR_ARG, "null trace arrays");
+  // the chain stops after the track scans, so the outputs are never written;
+  // the descriptor points them at a handle-owned word that takes the status
+  tmd_frame_out o;
+  memset(&o, 0, sizeof o);
+  o.status = h->trace_status;
+  o.native = reinterpret_cast<uint8_t*>(h->trace_status);  // never written by the trace
+  o.row_start = h->trace_status;
+  tmd_frame_in fin = *in;
+  const int rc = tmd_validate_frame(h, &fin, &o);
+  if (rc != TMD_OK) return rc;
+  TraceReq req{track_ids, n, state};
+  return tmd_launch(h, 1, &fin, &o, nullptr, nullptr, static_cast<cudaStream_t>(stream), &req);
 }
 
 extern "C" int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,

@@ -63,6 +63,7 @@ struct tmd_handle {
   size_t stage_bytes = 0;
   TmdServer* server = nullptr;
   TmdProfile prof;
+  uint32_t* trace_status = nullptr;        // status word of tmd_track_trace calls
   cudaStream_t aux = nullptr;              // second stream of the plain decode chain
   cudaEvent_t fork = nullptr, join = nullptr;
   // host streaming pipeline (tmd_decode_host_stream): copy streams, device
@@ -78,13 +79,21 @@ struct tmd_handle {
   ~tmd_handle();
 };
 
+// A float-path trace request (tmd_track_trace): the chain stops after the
+// track scans and traces the listed tracks of frame 0.
+struct TraceReq {
+  const uint32_t* ids;
+  uint32_t n;
+  float* state;
+};
 int tmd_set_error(tmd_handle* h, int code, const char* fmt, ...);
 int tmd_cuda_check(tmd_handle* h, cudaError_t e, const char* what);
 int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out);
 // Launch the decode chain for nf frames (in/out), or the encode chain for one
 // frame (tin/tout), on stream st, using the handle's scratch.
 int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
-               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st);
+               const tmd_truth_in* tin, const tmd_track_out* tout, cudaStream_t st,
+               const TraceReq* trace = nullptr);
 // Scratch layout of one frame.  The zeroed part of all frames is contiguous.
 struct FrameLayout {
   uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
@@ -109,7 +118,8 @@ void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                 const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
                 void* host_record, void* dev_record, cudaStream_t st, bool profile,
-                cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
+                cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr,
+                const TraceReq* trace = nullptr);
 void tmd_serve_shutdown(tmd_handle* h);
 // Read the tuning parameters for this GPU from the autotune cache, if any.
 void tmd_tune_load(tmd_handle* h);

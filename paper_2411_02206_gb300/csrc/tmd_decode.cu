@@ -397,6 +397,43 @@ cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm) {
   }
 }
 
+// Float-path trace: one thread per selected track walks it through the
+// compressed frame like the decoder (one global load per stream and step; a
+// debugging path, not a fast one) and writes the binary32 model state after
+// every cluster: x, y, dy/dx, d2y/dx2, the six y-covariance terms, t, dt/dx,
+// the three t-covariance terms, row and sector (as floats).
+__global__ void k_track_trace(const FrameDev* frames, const uint32_t* ids, uint32_t n_ids,
+                              float* state) {
+  __shared__ RowGeo geo;
+  fill_row_geo(&geo);
+  __syncthreads();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const FrameDev& F = frames[0];
+  if (i >= n_ids || (*F.status & kStCount)) return;
+  const uint32_t t = ids[i];
+  if (t >= F.n_tracks) return;
+  const uint32_t j0 = F.track_start[t], n = F.ncl[t], dm1 = j0 - t - 1u;
+  const uint32_t raw = F.row[t], sec = F.slice[t];
+  Track s;
+  seed(&geo, s, F.qpt[t], (int)raw, sec < (uint32_t)kNSec ? (int)sec : kNSec - 1, F.pad[t],
+       F.time[t]);
+  for (uint32_t k = 0; k < n && k < (uint32_t)kNRow; k++) {
+    if (k > 0) {
+      const uint32_t d = dm1 + k;
+      key_step(s, F.row_diff[d], F.sld[d]);
+      uint32_t ppad, ptime;
+      const float4 G = geo.row[s.row];
+      propagate_predict(G, s, ppad, ptime);
+      update(G, s, (ppad + F.pad_res[d]) & 0xFFFFu, ptime + F.time_res[d]);
+    }
+    float* o = state + ((size_t)i * kNRow + k) * 17;
+    o[0] = s.x; o[1] = s.y; o[2] = s.ty; o[3] = s.c;
+    o[4] = s.c00; o[5] = s.c01; o[6] = s.c02; o[7] = s.c11; o[8] = s.c12; o[9] = s.c22;
+    o[10] = s.t; o[11] = s.tt; o[12] = s.d00; o[13] = s.d01; o[14] = s.d11;
+    o[15] = (float)s.row; o[16] = (float)s.sec;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_track_encode(const EncDev* enc, const FrameDev* frames,
                                                       PlanDev plan, uint32_t n_tasks) {
   __shared__ RowGeo geo;

@@ -162,8 +162,11 @@ void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const Fr
                         PlanDev plan);
 cudaError_t prepare_att_scatter();
 __global__ void k_unatt_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tickets);
+__global__ void k_selftest_wait(const unsigned long long* never, uint32_t* status);
 __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
                                uint32_t n_tasks);
+__global__ void k_track_trace(const FrameDev* frames, const uint32_t* ids, uint32_t n_ids,
+                              float* state);
 
 constexpr int kRankBitmapWords = (kNBin + 31) / 32;
 constexpr int kCountRankSmem = kTileWarps * kNBin * 2 + kTileWarps * kRankBitmapWords * 4;

@@ -27,6 +27,18 @@ __device__ __forceinline__ unsigned long long lb_pack(unsigned long long st, boo
          ((unsigned long long)time << 32);
 }
 
+// The look-back word at w once it is published (its low two bits non-zero),
+// or 0 after kSpinLimit polls (each followed by a short sleep; about a second
+// in all): a wait that cannot end does not hang the kernel.
+__device__ __forceinline__ unsigned long long wait_published(const unsigned long long* w) {
+  for (uint32_t spins = 0; spins < kSpinLimit; spins++) {
+    const unsigned long long v = *(const volatile unsigned long long*)w;
+    if (v & 3ull) return v;
+    __nanosleep(64);
+  }
+  return 0ull;
+}
+
 // Segmented sum (flag = a segment starts inside the right operand).
 struct Seg {
   uint32_t flag, pad, time;
@@ -37,6 +49,14 @@ __device__ __forceinline__ Seg seg_add(const Seg& a, const Seg& b) {
 }
 
 }  // namespace
+
+// Failure detection without a fault: one thread waits, with the look-back's
+// bounded wait, on a word that nothing publishes, and records the timeout in
+// *status.
+__global__ void k_selftest_wait(const unsigned long long* never, uint32_t* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && wait_published(never) == 0ull)
+    atomicOr(status, kStTimeout);
+}
 
 // Largest b in [lo, hi] with start[b] <= e (start[lo] <= e is known).
 __device__ __forceinline__ uint32_t bin_search(const uint32_t* __restrict__ start, uint32_t lo,
@@ -195,17 +215,12 @@ __global__ void __launch_bounds__(256, 4) k_unatt_decode(const FrameDev* frames,
         atomicExch(lb + c, lb_pack(kLbAgg, false, acc.pad, acc.time));
       if (c > 0 && !first_is_head) {
         uint32_t p = c - 1;
-        uint32_t spins = 0;
         for (;;) {
-          const unsigned long long v = *(volatile unsigned long long*)(lb + p);
+          const unsigned long long v = wait_published(lb + p);
           const unsigned long long st = v & 3ull;
-          if (st == 0) {
-            if (++spins > kSpinLimit) {
-              atomicOr(F.status, kStTimeout);
-              break;
-            }
-            __nanosleep(64);
-            continue;
+          if (st == 0) {  // the predecessor never published: give up
+            atomicOr(F.status, kStTimeout);
+            break;
           }
           carry = seg_add(Seg{0u, (uint32_t)(v >> 16) & 0xFFFFu, (uint32_t)(v >> 32)}, carry);
           if (st == kLbInc || (v & kLbHead) || p == 0) break;

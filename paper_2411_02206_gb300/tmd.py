@@ -95,6 +95,8 @@ def lib():
                                           ctypes.POINTER(tmd_frame_out), _P],
                 "tmd_decode_host_stream": [H, ctypes.c_uint32, ctypes.POINTER(tmd_frame_in),
                                            ctypes.POINTER(tmd_frame_out), _P],
+                "tmd_track_trace": [H, ctypes.POINTER(tmd_frame_in), ctypes.c_uint32, _P, _P, _P],
+                "tmd_selftest_wait": [H, ctypes.POINTER(ctypes.c_uint32)],
                 "tmd_encode_tracks": [H, ctypes.POINTER(tmd_truth_in),
                                       ctypes.POINTER(tmd_track_out), _P],
                 "tmd_submit": [H, ctypes.POINTER(tmd_frame_in), ctypes.POINTER(ctypes.c_uint64)],
@@ -233,6 +235,16 @@ class Decoder:
         outs = (tmd_frame_out * n)(*fouts)
         return self._check(self._L.tmd_decode_host_stream(self.h, n, ins, outs,
                                                           _P(_stream_ptr(stream))))
+
+    def tmd_selftest_wait(self) -> int:
+        st = ctypes.c_uint32(0)
+        self._check(self._L.tmd_selftest_wait(self.h, ctypes.byref(st)))
+        return int(st.value)
+
+    def tmd_track_trace(self, fin: tmd_frame_in, n: int, track_ids, state, stream=None) -> int:
+        return self._check(self._L.tmd_track_trace(self.h, ctypes.byref(fin), n,
+                                                   _P(_ptr(track_ids)), _P(_ptr(state)),
+                                                   _P(_stream_ptr(stream))))
 
     def tmd_encode_tracks(self, tin: tmd_truth_in, tout: tmd_track_out, stream=None) -> int:
         return self._check(self._L.tmd_encode_tracks(self.h, ctypes.byref(tin), ctypes.byref(tout),

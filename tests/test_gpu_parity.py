@@ -262,3 +262,37 @@ def test_full_size_stress_frame(dec):
     the bins): GPU encoder and decoder against the oracle on every field."""
     truth = synth.shape_truth("stress")
     _check_truth(dec, truth, "stress full size")
+
+
+def test_float_path_state_matches_the_oracle(dec):
+    """The decoder's binary32 track-model state after every cluster equals the
+    oracle's, bit for bit (tracks with sector changes, side crossings and leg
+    changes included): the float path is pinned step by step, not only
+    through the final integer codes."""
+    import torch
+    from paper_2411_02206_gb300 import frames, tmd
+    truth = synth.make_truth(n_tracks=1500, n_unatt=1000, seed=23, looper_frac=0.4, max_legs=4,
+                             pt_mean=0.3)
+    of = G.oracle_frame(truth)
+    dev = frames.to_torch(of, "cuda:0")
+    ncl = truth["ncl"].astype(np.int64)
+    starts = np.concatenate([[0], np.cumsum(ncl)])
+    sec, leg = truth["sector"], truth["leg"]
+    # every track that changes sector or leg, plus a sample of the others
+    changing = [t for t in range(len(ncl))
+                if len(np.unique(sec[starts[t]:starts[t + 1]])) > 1
+                or len(np.unique(leg[starts[t]:starts[t + 1]])) > 1]
+    ids = np.array(sorted(set(changing[:400]) | set(range(0, len(ncl), 37))), np.uint32)
+    assert len(changing) > 50
+    ids_d = torch.from_numpy(ids.view(np.int32)).to("cuda:0")
+    state = torch.full((len(ids), 152, 17), float("nan"), dtype=torch.float32, device="cuda:0")
+    dec.tmd_track_trace(tmd.frame_in(dev), len(ids), ids_d, state)
+    torch.cuda.synchronize()
+    got = state.cpu().numpy()
+    for i, t in enumerate(ids):
+        a, b = starts[t], starts[t + 1]
+        ref = O.track_trace(int(truth["qpt"][t]), truth["row"][a:b], sec[a:b], leg[a:b],
+                            truth["pad"][a:b], truth["time"][a:b])
+        n = min(b - a, 152)
+        assert np.array_equal(got[i, :n].view(np.uint32), ref["state"][:n].view(np.uint32)), \
+            f"track {t}: state differs"
