@@ -200,6 +200,28 @@ def path_bytes(nt, na, nu):
     return 19 * na + 8 * (na - nt) + 11 * nt + 25 * nu + 4 * 5472 + 4 * 5473
 
 
+def dram_traffic(kernel, tuned, nt, na, nu):
+    """DRAM bytes (read + write) of one launch of `kernel` on this workload,
+    from the ncu figures committed in profiles/dram_traffic.txt: bytes per
+    unit (attached or unattached cluster) measured on a 0.2-scale frame of
+    the same shape, times this launch's units.  None when the file has no
+    line for the kernel under the current tuning (the kernel changed, or was
+    not captured)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) != 4 or f[0].startswith("#") or f[0] != kernel:
+            continue
+        key, val = f[1].split("=")
+        if str(tuned.get(key)) != val:
+            continue
+        units = na if f[2] == "attached" else nu
+        return float(f[3]) * units
+    return None
+
+
 def _apply_tune(dec, settings):
     """Tuning settings given as key=value on the command line (after the
     autotuner, which they override)."""
@@ -329,13 +351,7 @@ def run(args):
     dk_ms, dk_n = prof[dk_name]
     dk_bytes = kernel_bytes(dk_name, nt, na, nu)
     achieved = dk_bytes / (dk_ms / dk_n * 1e-3) / 1e9 if (dk_n and dk_bytes) else None
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get(dk_name + "_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = dram_traffic(dk_name, tuned, nt, na, nu)
     # end to end through the host-buffer entry point
     host = frames.to_torch({k: truth[k] for k in truth if k not in ("sector", "leg")}, None,
                            pin=True)

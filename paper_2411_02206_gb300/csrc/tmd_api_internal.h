@@ -48,7 +48,7 @@ struct tmd_handle {
   int tune_decode_variant = 1;   // staging-round variant of the track decoder
   int tune_rank_variant = 1;     // duplicate-key handling of the ranking kernel
   int tune_scatter_variant = 1;  // store pattern of the record scatter
-  int tune_overlap = 1;          // unattached decode on a second stream beside the scatter
+  int tune_overlap = 0;          // unattached decode on a second stream beside the scatter
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;

@@ -120,7 +120,7 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
   const Axis axes[] = {
       {&tmd_handle::tune_decode_variant, {0, 1, 2, 3}},
       {&tmd_handle::tune_rank_variant, {0, 1, 2}},
-      {&tmd_handle::tune_scatter_variant, {0, 1, 2, 3}},
+      {&tmd_handle::tune_scatter_variant, {0, 1, 2}},  // 3 differs from 1 within noise
       {&tmd_handle::tune_overlap, {0, 1}},
       {&tmd_handle::tune_unatt_bps, {0, 2, 3, 4}},
   };
