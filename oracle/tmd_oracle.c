@@ -531,11 +531,13 @@ int tmd_oracle_encode(const OTruth* T, OFrameOut* o) {
     }
     j0 += n;
   }
-  memcpy(o->qtot_a, T->qtot_a, 2u * T->n_attached);
-  memcpy(o->qmax_a, T->qmax_a, 2u * T->n_attached);
-  memcpy(o->flags_a, T->flags_a, T->n_attached);
-  memcpy(o->sigma_pad_a, T->sigma_pad_a, T->n_attached);
-  memcpy(o->sigma_time_a, T->sigma_time_a, T->n_attached);
+  if (T->n_attached) { /* (memcpy from or to a null pointer is undefined even for 0 bytes) */
+    memcpy(o->qtot_a, T->qtot_a, 2u * T->n_attached);
+    memcpy(o->qmax_a, T->qmax_a, 2u * T->n_attached);
+    memcpy(o->flags_a, T->flags_a, T->n_attached);
+    memcpy(o->sigma_pad_a, T->sigma_pad_a, T->n_attached);
+    memcpy(o->sigma_time_a, T->sigma_time_a, T->n_attached);
+  }
 
   /* unattached: group by bin (stable), sort each bin by (time, pad), store
    * differences to the preceding cluster (the first to zero) */

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tmd.h"
 #include "tmd_api_internal.h"
 #include "tmd_internal.cuh"
@@ -27,6 +29,14 @@ namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+// NVTX range around the enqueueing of one phase of the chain (tracing tools
+// show it on the host timeline beside the phase's kernels; without a tool
+// attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 bool misaligned(const void* p, size_t a) { return ((uintptr_t)p) % a != 0; }
 
@@ -477,6 +487,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   CK(cudaMemsetAsync(zb, 0, zbytes, st));
   TmdProfile& prof = h->prof;
   auto timed_on = [&](cudaStream_t on, int id, auto&& launch) {
+    NvtxRange kernel_range(kKernelNames[id]);
     if (!profile) {
       launch();
       return;
@@ -489,6 +500,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     if (prof.pending.size() >= 4096) prof.drain(2048);
   };
   auto timed = [&](int id, auto&& launch) { timed_on(st, id, launch); };
+  NvtxRange call_range(encode ? "tmd.encode" : (trace ? "tmd.trace" : "tmd.decode"));
   timed(kKZeroStatus, [&] { k_zero_status<<<1, 256, 0, st>>>(dframes, nf); });
   const uint32_t n_tblk = pre_tblk[nf], n_tile = pre_tile[nf], n_grp = pre_grp[nf];
   const uint32_t n_warp = pre_warp[nf], n_chunk = pre_chunk[nf];

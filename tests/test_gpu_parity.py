@@ -296,3 +296,18 @@ def test_float_path_state_matches_the_oracle(dec):
         n = min(b - a, 152)
         assert np.array_equal(got[i, :n].view(np.uint32), ref["state"][:n].view(np.uint32)), \
             f"track {t}: state differs"
+
+
+@pytest.mark.parametrize("seed", list(range(100, 116)))
+def test_random_frame_shapes(dec, seed):
+    """Property test: frames of randomly drawn shape (track count, track
+    lengths down to one cluster, loopers with up to 6 legs, secondaries,
+    empty and hot rows, unattached counts) decode to the oracle's bytes."""
+    r = np.random.default_rng(seed)
+    kw = dict(n_tracks=int(r.integers(0, 3000)), n_unatt=int(r.integers(0, 60_000)),
+              seed=seed, looper_frac=float(r.uniform(0.0, 0.6)),
+              secondary_frac=float(r.uniform(0.0, 0.95)), pt_mean=float(r.uniform(0.15, 0.8)),
+              max_legs=int(r.integers(1, 7)), min_clusters=int(r.integers(1, 25)),
+              empty_frac=float(r.choice([0.0, 0.4])), hot_frac=float(r.choice([0.0, 0.1])))
+    kw["hot_share"] = 0.9 if kw["hot_frac"] > 0 else 0.0
+    _check_truth(dec, synth.make_truth(**kw), str(kw))
