@@ -314,7 +314,7 @@ def run(args):
         dec.tmd_autotune([fin], [fout], stream)
     _apply_tune(dec, args.tune)
     tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
-                                              "scatter_variant", "overlap",
+                                              "scatter_variant", "overlap", "unatt_variant",
                                               "decode_blocks_per_sm", "unatt_blocks_per_sm")}
     for _ in range(args.warmup):
         dec.tmd_decode_frame(fin, fout, stream)

@@ -286,6 +286,11 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *                               clusters per thread), or a whole ranking tile
  *                               regrouped in (bin, rank) order through
  *                               distributed shared memory first (2)
+ *   "unatt_variant"       0..1  record write-out of the unattached decoder:
+ *                               word by word (0) or one staged 16-byte
+ *                               {record, index} entry per thread (1)
+ *   "overlap"             0..1  unattached decoder on a second stream beside
+ *                               the attached-cluster chain (1)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
  * tmd_autotune times the decode chain on the given frames (device buffers,

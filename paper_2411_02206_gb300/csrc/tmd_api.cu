@@ -224,8 +224,7 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(2, &h->occ_decode_v[2]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(3, &h->occ_decode_v[3]), "occupancy")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                  &h->occ_unatt, k_unatt_decode, 256, 0), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, occupancy_unatt_decode(&h->occ_unatt), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                   &h->occ_encode, k_track_encode, 256, 0), "occupancy")) != TMD_OK) {
     delete h;
@@ -544,8 +543,9 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       int bps = h->occ_unatt;
       if (h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;
       const uint32_t grid = std::min<uint32_t>(n_chunk, (uint32_t)(h->sms * bps));
-      timed_on(ust, kKUnattDecode,
-               [&] { k_unatt_decode<<<grid, 256, 0, ust>>>(dframes, P, n_chunk); });
+      timed_on(ust, kKUnattDecode, [&] {
+        launch_unatt_decode(h->tune_unatt_variant, grid, ust, dframes, P, n_chunk);
+      });
     }
     if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     if (n_tile)

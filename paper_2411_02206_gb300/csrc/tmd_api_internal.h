@@ -45,9 +45,10 @@ struct tmd_handle {
   int occ_decode = 1, occ_unatt = 1, occ_encode = 1;
   int occ_decode_v[4] = {1, 1, 1, 1};  // resident blocks per SM of each decoder variant
   // tuning parameters (launch shapes only; results never depend on them)
-  int tune_decode_variant = 1;   // staging-round variant of the track decoder
+  int tune_decode_variant = 3;   // staging-round variant of the track decoder
   int tune_rank_variant = 1;     // duplicate-key handling of the ranking kernel
   int tune_scatter_variant = 1;  // store pattern of the record scatter
+  int tune_unatt_variant = 1;    // record write-out of the unattached decode
   int tune_overlap = 0;          // unattached decode on a second stream beside the scatter
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)

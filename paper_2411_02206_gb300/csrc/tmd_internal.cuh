@@ -161,7 +161,11 @@ cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
 void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan);
 cudaError_t prepare_att_scatter();
-__global__ void k_unatt_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tickets);
+// Unattached decode variants 0, 1 (record write-out word by word or one
+// record per thread; identical results), launched through these functions.
+void launch_unatt_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+                         PlanDev plan, uint32_t n_tickets);
+cudaError_t occupancy_unatt_decode(int* blocks_per_sm);
 __global__ void k_selftest_wait(const unsigned long long* never, uint32_t* status);
 __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
                                uint32_t n_tasks);

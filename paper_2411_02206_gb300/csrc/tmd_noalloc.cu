@@ -103,7 +103,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
           prepare_count_rank() != cudaSuccess ||
           occupancy_track_decode(0, &od) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_unatt_decode, 256, 0) != cudaSuccess) {
+          occupancy_unatt_decode(&ou) != cudaSuccess) {
         set_err(err, err_len, "device set-up failed");
         return TMD_ERR_CUDA;
       }
@@ -182,7 +182,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   if (n_tile) launch_att_scatter(0, n_tile, st, dframe, P);
   if (n_chunk) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_unatt);
-    k_unatt_decode<<<n_chunk < cap ? n_chunk : cap, 256, 0, st>>>(dframe, P, n_chunk);
+    launch_unatt_decode(0, n_chunk < cap ? n_chunk : cap, st, dframe, P, n_chunk);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -68,20 +68,32 @@ __device__ __forceinline__ uint32_t bin_search(const uint32_t* __restrict__ star
   return lo;
 }
 
-// Shared-memory word of staged record word w: one word of padding per 32
-// spreads the stride-24 writes of the staging loop over the banks, while the
-// copy-out loop still reads 32 consecutive words per warp.
+// Variant 0: records staged word by word (one word of padding per 32 spreads
+// the stride-24 writes of the staging loop over the banks) and written word
+// by word: consecutive threads write consecutive words, contiguous in the
+// native list within a bin.
 __device__ __forceinline__ uint32_t rec_slot(uint32_t w) { return w + (w >> 5); }
 
+// Variant 1: every element staged as one 16-byte entry {record, native index}
+// at slot l ^ ((l >> 3) & 7) (the staging writes, 8 elements apart per lane,
+// and the write-out reads, consecutive per lane, both take the minimum of
+// shared-memory wavefronts) and written as one record per thread: fewer
+// instructions per record, more L2 write requests.
+__device__ __forceinline__ uint32_t rec4_slot(uint32_t l) { return l ^ ((l >> 3) & 7u); }
+
+template <int V>
 __global__ void __launch_bounds__(256, 4) k_unatt_decode(const FrameDev* frames, PlanDev plan,
                                                       uint32_t n_tickets) {
   constexpr uint32_t kRecWords = 3 * kChunk;
+  constexpr uint32_t kStageWords = V == 0 ? kRecWords + kRecWords / 32 + kChunk : 4 * kChunk;
   __shared__ uint32_t s_ticket;
   __shared__ uint32_t s_bin[2];           // bins of the chunk's first and last cluster
   __shared__ Seg s_warp[8];
   __shared__ Seg s_carry;
-  __shared__ uint32_t s_rec[kRecWords + kRecWords / 32];  // records, element order
-  __shared__ uint32_t s_pos[kChunk];      // native index of every element
+  __shared__ __align__(16) uint32_t s_stage[kStageWords];
+  uint32_t* const s_rec = s_stage;                                  // variant 0
+  uint32_t* const s_pos = s_stage + kRecWords + kRecWords / 32;     // variant 0
+  uint4* const s_rec4 = reinterpret_cast<uint4*>(s_stage);          // variant 1
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (;;) {
     if (tid == 0) s_ticket = atomicAdd(&plan.counters[1], 1u);
@@ -265,27 +277,63 @@ __global__ void __launch_bounds__(256, 4) k_unatt_decode(const FrameDev* frames,
           p = 0xFFFFFFFFu;
         }
         const uint32_t q16 = 16 * (k & 1), q8 = 8 * (k & 3);
-        s_rec[rec_slot(3 * l + 0)] = (vt & 0xFFFFFFu) | (((fl[k >> 2] >> q8) & 0xFFu) << 24);
-        s_rec[rec_slot(3 * l + 1)] = vp | (((sg[k >> 2] >> q8) & 0xFFu) << 16) |
-                                     (((sp[k >> 2] >> q8) & 0xFFu) << 24);
-        s_rec[rec_slot(3 * l + 2)] = ((qm[k >> 1] >> q16) & 0xFFFFu) |
-                                     (((qt[k >> 1] >> q16) & 0xFFFFu) << 16);
+        const uint32_t w0 = (vt & 0xFFFFFFu) | (((fl[k >> 2] >> q8) & 0xFFu) << 24);
+        const uint32_t w1 = vp | (((sg[k >> 2] >> q8) & 0xFFu) << 16) |
+                            (((sp[k >> 2] >> q8) & 0xFFu) << 24);
+        const uint32_t w2 = ((qm[k >> 1] >> q16) & 0xFFFFu) | (((qt[k >> 1] >> q16) & 0xFFFFu) << 16);
+        if constexpr (V == 0) {
+          s_rec[rec_slot(3 * l + 0)] = w0;
+          s_rec[rec_slot(3 * l + 1)] = w1;
+          s_rec[rec_slot(3 * l + 2)] = w2;
+        } else {
+          s_rec4[rec4_slot(l)] = make_uint4(w0, w1, w2, p);
+        }
       }
-      s_pos[l] = p;
+      if constexpr (V == 0) s_pos[l] = p;
     }
     __syncthreads();
-    // write out word by word: consecutive threads write consecutive words of
-    // consecutive records, which are contiguous in the native list within a bin
     const uint32_t n_here = min((uint32_t)kChunk, n - c0);
     uint32_t* __restrict__ nat = reinterpret_cast<uint32_t*>(F.native);
-    for (uint32_t w = tid; w < 3 * n_here; w += blockDim.x) {
-      const uint32_t l = w / 3;
-      const uint32_t p = s_pos[l];
-      if (p != 0xFFFFFFFFu) nat[(size_t)p * 3 + (w - 3 * l)] = s_rec[rec_slot(w)];
+    if constexpr (V == 0) {
+      // word by word: consecutive threads write consecutive words of
+      // consecutive records, which are contiguous in the native list within a bin
+      for (uint32_t w = tid; w < 3 * n_here; w += blockDim.x) {
+        const uint32_t l = w / 3;
+        const uint32_t p = s_pos[l];
+        if (p != 0xFFFFFFFFu) nat[(size_t)p * 3 + (w - 3 * l)] = s_rec[rec_slot(w)];
+      }
+    } else {
+#pragma unroll 4
+      for (uint32_t l = tid; l < n_here; l += blockDim.x) {
+        const uint4 r = s_rec4[rec4_slot(l)];
+        if (r.w != 0xFFFFFFFFu) {
+          uint32_t* d = nat + (size_t)r.w * 3;
+          d[0] = r.x;
+          d[1] = r.y;
+          d[2] = r.z;
+        }
+      }
     }
     if (st) atomicOr(F.status, st);
     __syncthreads();
   }
+}
+
+void launch_unatt_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+                         PlanDev plan, uint32_t n_tickets) {
+  if (variant == 1)
+    k_unatt_decode<1><<<grid, 256, 0, st>>>(frames, plan, n_tickets);
+  else
+    k_unatt_decode<0><<<grid, 256, 0, st>>>(frames, plan, n_tickets);
+}
+
+cudaError_t occupancy_unatt_decode(int* blocks_per_sm) {
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_unatt_decode<0>, 256, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unatt_decode<1>, 256, 0);
+  *blocks_per_sm = a < b ? a : b;
+  return e;
 }
 
 }  // namespace tmd

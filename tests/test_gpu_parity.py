@@ -184,8 +184,15 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
     ora = O.decode(of)
     dev = frames.to_torch(of, "cuda:0")
     saved = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
-                                               "scatter_variant", "overlap")}
+                                               "scatter_variant", "overlap",
+                                               "unatt_variant")}
     try:
+        for uv in range(2):
+            dec.tmd_tune_set("unatt_variant", uv)
+            native, rs, att, st = dec.decode(dev)
+            gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
+                   frames.to_numpy(att, np.uint32), int(st.item()))
+            G.assert_same_decode(gpu, ora, f"unatt {uv}")
         for ov in range(2):
             for dv in range(4):
                 for rv in range(3):
