@@ -4,12 +4,13 @@
 // the same kernel sequence; every kernel covers the work items of all frames
 // and finds its frame from a prefix table (tmd_internal.cuh).
 //
-//   k_zero_status -> k_track_scan1 -> k_frame_scan -> k_track_scan2   (a1)
-//   k_track_decode: coordinates and (sector,row) keys                  (a4, a2)
-//   k_count_rank                                                       (a2)
-//   k_group_sum -> k_row_offsets -> k_tile_base                        (a3)
-//   k_att_scatter: native records of the attached clusters             (a4)
-//   k_unatt_decode                                                     (a5)
+//   k_put_record: frame descriptors and prefix tables, scratch cleared
+//   k_zero_status -> k_track_scan1 -> k_frame_scan -> k_track_scan2   track prep
+//   k_track_decode: coordinates and (sector,row) keys                  track decode
+//   k_count_rank                                                       per-row counts
+//   k_group_sum -> k_row_offsets -> k_tile_base                        row offsets
+//   k_att_scatter: native records of the attached clusters             placement
+//   k_unatt_decode                                                     unattached clusters
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -256,7 +257,7 @@ extern "C" const char* tmd_last_error_string(const tmd_handle* h) {
 // instrumentation
 // ---------------------------------------------------------------------------
 static const char* kKernelNames[kKNum] = {
-    "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_track_decode",
+    "k_put_record", "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_track_decode",
     "k_count_rank", "k_group_sum", "k_row_offsets", "k_tile_base", "k_att_scatter",
     "k_unatt_decode", "k_track_encode"};
 
@@ -482,8 +483,6 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   const FrameDev* dframes = reinterpret_cast<const FrameDev*>(dev + R.frames);
   const EncDev* denc = reinterpret_cast<const EncDev*>(dev + R.enc);
 
-  CK(cudaMemcpyAsync(dev, host, R.bytes, cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(zb, 0, zbytes, st));
   TmdProfile& prof = h->prof;
   auto timed_on = [&](cudaStream_t on, int id, auto&& launch) {
     NvtxRange kernel_range(kKernelNames[id]);
@@ -500,6 +499,9 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   };
   auto timed = [&](int id, auto&& launch) { timed_on(st, id, launch); };
   NvtxRange call_range(encode ? "tmd.encode" : (trace ? "tmd.trace" : "tmd.decode"));
+  cudaError_t put_err = cudaSuccess;
+  timed(kKPutRecord, [&] { put_err = put_record(host, R.bytes, dev, zb, zbytes, st); });
+  CK(put_err);
   timed(kKZeroStatus, [&] { k_zero_status<<<1, 256, 0, st>>>(dframes, nf); });
   const uint32_t n_tblk = pre_tblk[nf], n_tile = pre_tile[nf], n_grp = pre_grp[nf];
   const uint32_t n_warp = pre_warp[nf], n_chunk = pre_chunk[nf];

@@ -16,7 +16,7 @@ struct TmdServer;  // serving state (tmd_serve.cu)
 
 // Kernel ids of the instrumentation.
 enum TmdKernel {
-  kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode, kKCountRank,
+  kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode, kKCountRank,
   kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode, kKNum
 };
 

@@ -134,6 +134,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // Kernels (launched by tmd_api.cu).
+// Launch-record upload as a kernel parameter (no copy engine), in chunks of
+// 2 KiB or 16 KiB; bytes and zero_bytes are multiples of 16.  Also clears
+// zero_bytes at `zero`.  Returns the launch error, if any.
+constexpr int kRecordChunkSmall = 128, kRecordChunkBig = 1024;
+template <int W>
+struct RecordChunk {
+  uint4 w[W];
+};
+cudaError_t put_record(const void* host, size_t bytes, void* dev, void* zero, size_t zero_bytes,
+                       cudaStream_t st);
 __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames);
 __global__ void k_track_scan1(const FrameDev* frames, PlanDev plan);
 __global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);

@@ -162,8 +162,8 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   P.counters = reinterpret_cast<uint32_t*>(zb);
   k_noalloc_record<<<1, 32, 0, st>>>(F, n_tblk, n_tile, n_grp, n_warp, n_chunk, n_kt, dframe,
                                      dpre);
-  if (cudaMemsetAsync(zb, 0, zbytes, st) != cudaSuccess) {
-    set_err(err, err_len, "cudaMemsetAsync failed");
+  if (put_record(nullptr, 0, nullptr, zb, zbytes, st) != cudaSuccess) {
+    set_err(err, err_len, "scratch clear failed");
     return TMD_ERR_CUDA;
   }
   k_zero_status<<<1, 256, 0, st>>>(dframe, 1);

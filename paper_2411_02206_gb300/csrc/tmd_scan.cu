@@ -10,6 +10,8 @@
 // per-tile histograms of k_count_rank) plus the unattached count, exclusive
 // scan -> rowStart; then per (tile, bin) the first native index of the tile's
 // clusters in that bin.
+#include <cstring>
+
 #include "tmd_internal.cuh"
 
 namespace tmd {
@@ -45,6 +47,56 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total)
   total = block_tot;
   __syncthreads();
   return r;
+}
+
+// The launch record (frame descriptors and prefix tables) travels to the
+// device as the parameter of this kernel, not by a host-to-device copy: a
+// copy would queue on the copy engine behind whatever bulk uploads other
+// streams have in flight (the pipelined host entry point uploads the next
+// frame's inputs while this one decodes), and the decode would wait for them.
+// The same launch clears the scratch region that must start at zero.
+template <int W>
+__global__ void k_put_record(RecordChunk<W> c, uint32_t n16, uint4* __restrict__ dst,
+                             uint4* __restrict__ zero, uint32_t zero_n16) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = c.w[i];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < zero_n16; i += stride)
+    zero[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+cudaError_t put_record(const void* host, size_t bytes, void* dev, void* zero, size_t zero_bytes,
+                       cudaStream_t st) {
+  const char* h = static_cast<const char*>(host);
+  char* d = static_cast<char*>(dev);
+  uint4* z = static_cast<uint4*>(zero);
+  uint32_t zn = (uint32_t)(zero_bytes / 16);
+  do {
+    const size_t small = sizeof(RecordChunk<kRecordChunkSmall>);
+    const size_t big = sizeof(RecordChunk<kRecordChunkBig>);
+    const size_t take = bytes <= small ? bytes : (bytes < big ? bytes : big);
+    const uint32_t n16 = (uint32_t)(take / 16);
+    const uint32_t work = n16 > zn ? n16 : zn;
+    uint32_t grid = (work + 255) / 256;
+    grid = grid < 1 ? 1 : (grid > 256 ? 256 : grid);
+    if (take <= small) {
+      RecordChunk<kRecordChunkSmall> c;
+      if (take) memcpy(c.w, h, take);
+      k_put_record<kRecordChunkSmall><<<grid, 256, 0, st>>>(c, n16, reinterpret_cast<uint4*>(d),
+                                                            z, zn);
+    } else {
+      RecordChunk<kRecordChunkBig> c;
+      memcpy(c.w, h, take);
+      k_put_record<kRecordChunkBig><<<grid, 256, 0, st>>>(c, n16, reinterpret_cast<uint4*>(d), z,
+                                                          zn);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    h += take;
+    d += take;
+    bytes -= take;
+    zn = 0;
+  } while (bytes);
+  return cudaSuccess;
 }
 
 __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames) {
