@@ -180,13 +180,22 @@ def kernel_bytes(name, nt, na, nu):
       k_count_rank    per attached cluster the 2 B key read and the 2 B rank
                       written, per ranking tile a 2 B count per bin written;
       k_unatt_decode  per unattached cluster 13 B read and 12 B written, the
-                      per-bin counts read."""
+                      per-bin counts read;
+      k_xscatter      per attached cluster 15 B read (key, pad code, time
+                      code, 7 B of charges, sigmas and flags) and the 12 B
+                      native record written;
+      k_xcount, k_seg_count, k_seg_runs
+                      per attached cluster the 2 B key read."""
     n_tiles = -(-na // 32768)
     table = {
         "k_track_decode": 8 * (na - nt) + 19 * nt + 8 * na,
         "k_att_scatter": 29 * na,
         "k_count_rank": 4 * na + 2 * 5472 * n_tiles,
         "k_unatt_decode": 25 * nu + 4 * 5472,
+        "k_xscatter": 27 * na,
+        "k_xcount": 2 * na,
+        "k_seg_count": 2 * na,
+        "k_seg_runs": 2 * na,
     }
     return table.get(name)
 
@@ -315,7 +324,8 @@ def run(args):
     _apply_tune(dec, args.tune)
     tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
                                               "scatter_variant", "overlap", "unatt_variant",
-                                              "decode_blocks_per_sm", "unatt_blocks_per_sm")}
+                                              "place", "decode_blocks_per_sm",
+                                              "unatt_blocks_per_sm")}
     for _ in range(args.warmup):
         dec.tmd_decode_frame(fin, fout, stream)
     torch.cuda.synchronize()

@@ -104,11 +104,15 @@ int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_ou
 }
 
 void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
-                FrameLayout& L) {
+                FrameLayout& L, bool xpose) {
   L.n_tblocks = ceil_div(nt, kTrackBlk);
   L.n_tiles = ceil_div(na, kTile);
   L.n_groups = ceil_div(L.n_tiles, kGroup);
   L.n_chunks = ceil_div(nu, kChunk);
+  L.n_sblk = xpose ? ceil_div(na, kSegBlk) : 0u;
+  // every sector's last tile may be partial: at most kNSec tiles more than the
+  // attached clusters fill
+  L.n_xtiles = xpose && na ? ceil_div(na, kXT) + kNSec : 0u;
   auto z = [&](size_t bytes) { size_t o = zoff; zoff = align_up(zoff + bytes, 256); return o; };
   auto p = [&](size_t bytes) { size_t o = poff; poff = align_up(poff + bytes, 256); return o; };
   L.z_len = z((size_t)kLenBuckets * 4);
@@ -125,6 +129,15 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
   L.unatt_start = p(((size_t)kNBin + 1) * 4);
   L.blk_sum = p((size_t)L.n_tblocks * 4 + 4);
   L.att_count = p((size_t)kNBin * 4);
+  L.seg_cnt = L.seg_tot = L.runs = L.xt_whist = L.xt_hist = L.xt_base = 0;
+  if (xpose) {
+    L.seg_cnt = p((size_t)2 * kNSec * L.n_sblk * 4 + 4);
+    L.seg_tot = p((size_t)2 * kNSec * 4);
+    L.runs = p((size_t)na * 8 + 8);  // a run starts at a cluster: at most na runs
+    L.xt_whist = p((size_t)L.n_xtiles * kXWarps * kNRow * 2 + 4);
+    L.xt_hist = p((size_t)L.n_xtiles * kNRow * 2 + 4);
+    L.xt_base = p((size_t)L.n_xtiles * kNRow * 4 + 4);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -221,6 +234,7 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, prepare_count_rank(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, prepare_att_scatter(), "smem attribute")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, prepare_xscatter(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(0, &h->occ_decode_v[0]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(2, &h->occ_decode_v[2]), "occupancy")) != TMD_OK ||
@@ -259,7 +273,8 @@ extern "C" const char* tmd_last_error_string(const tmd_handle* h) {
 static const char* kKernelNames[kKNum] = {
     "k_put_record", "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_track_decode",
     "k_count_rank", "k_group_sum", "k_row_offsets", "k_tile_base", "k_att_scatter",
-    "k_unatt_decode", "k_track_encode"};
+    "k_unatt_decode", "k_track_encode", "k_seg_count", "k_seg_scan", "k_seg_runs", "k_xcount",
+    "k_xrow_offsets", "k_xbase", "k_xscatter"};
 
 cudaEvent_t TmdProfile::get() {
   if (pool.empty()) {
@@ -337,7 +352,7 @@ struct RecordLayout {
 static RecordLayout record_layout(uint32_t n, bool enc) {
   RecordLayout r;
   r.pre = 0;
-  r.frames = align_up(6 * ((size_t)n + 1) * 4, 64);
+  r.frames = align_up(8 * ((size_t)n + 1) * 4, 64);
   r.enc = align_up(r.frames + (size_t)n * sizeof(FrameDev), 64);
   r.bytes = align_up(r.enc + (enc ? (size_t)n * sizeof(EncDev) : 0), 64);
   r.counters_unused = 0;
@@ -410,9 +425,12 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   uint32_t* pre_warp = pre + 3 * (nf + 1);
   uint32_t* pre_chunk = pre + 4 * (nf + 1);
   uint32_t* pre_kt = pre + 5 * (nf + 1);
+  uint32_t* pre_sblk = pre + 6 * (nf + 1);
+  uint32_t* pre_xtile = pre + 7 * (nf + 1);
   FrameDev* fd = reinterpret_cast<FrameDev*>(host + R.frames);
   EncDev* ed = reinterpret_cast<EncDev*>(host + R.enc);
   pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = pre_kt[0] = 0;
+  pre_sblk[0] = pre_xtile[0] = 0;
   uint32_t* zero_bins = reinterpret_cast<uint32_t*>(zb + 256);
   for (uint32_t f = 0; f < nf; f++) {
     FrameDev& F = fd[f];
@@ -450,6 +468,16 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     }
     F.n_tblocks = l.n_tblocks; F.n_tiles = l.n_tiles; F.n_groups = l.n_groups;
     F.n_chunks = l.n_chunks;
+    F.n_sblk = l.n_sblk;
+    F.n_xtiles = l.n_xtiles;
+    if (l.seg_tot) {
+      F.seg_cnt = reinterpret_cast<uint32_t*>(pb + l.seg_cnt);
+      F.seg_tot = reinterpret_cast<uint32_t*>(pb + l.seg_tot);
+      F.runs = reinterpret_cast<uint2*>(pb + l.runs);
+      F.xt_whist = reinterpret_cast<uint16_t*>(pb + l.xt_whist);
+      F.xt_hist = reinterpret_cast<uint16_t*>(pb + l.xt_hist);
+      F.xt_base = reinterpret_cast<uint32_t*>(pb + l.xt_base);
+    }
     F.len_cursor = reinterpret_cast<uint32_t*>(zb + l.z_len);
     F.lookback = reinterpret_cast<unsigned long long*>(zb + l.z_lb);
     F.track_start = reinterpret_cast<uint32_t*>(pb + l.track_start);
@@ -469,6 +497,8 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     pre_warp[f + 1] = pre_warp[f] + ceil_div(F.n_tracks, 32);  // encoder warp tasks
     pre_chunk[f + 1] = pre_chunk[f] + l.n_chunks;
     pre_kt[f + 1] = pre_kt[f] + ceil_div(F.n_tracks, 32);
+    pre_sblk[f + 1] = pre_sblk[f] + l.n_sblk;
+    pre_xtile[f + 1] = pre_xtile[f] + l.n_xtiles;
   }
   PlanDev P;
   const uint32_t* dpre = reinterpret_cast<const uint32_t*>(dev + R.pre);
@@ -479,6 +509,8 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   P.pre_warp = dpre + 3 * (nf + 1);
   P.pre_chunk = dpre + 4 * (nf + 1);
   P.pre_kt = dpre + 5 * (nf + 1);
+  P.pre_sblk = dpre + 6 * (nf + 1);
+  P.pre_xtile = dpre + 7 * (nf + 1);
   P.counters = reinterpret_cast<uint32_t*>(zb);
   const FrameDev* dframes = reinterpret_cast<const FrameDev*>(dev + R.frames);
   const EncDev* denc = reinterpret_cast<const EncDev*>(dev + R.enc);
@@ -528,10 +560,24 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
           (uint32_t)(h->sms * bps), (n_kt + per_block - 1) / per_block));
       timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt); });
     }
-    if (n_tile)
-      timed(kKCountRank, [&] { launch_count_rank(h->tune_rank_variant, n_tile, st, dframes, P); });
-    if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
-    timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
+    const bool xpose = h->tune_place == 1;
+    const uint32_t n_sblk = pre_sblk[nf], n_xt = pre_xtile[nf];
+    if (xpose) {
+      if (n_sblk) {
+        timed(kKSegCount, [&] { k_seg_count<<<n_sblk, kSegThreads, 0, st>>>(dframes, P); });
+        timed(kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, st>>>(dframes, P); });
+        timed(kKSegRuns, [&] { k_seg_runs<<<n_sblk, kSegThreads, 0, st>>>(dframes, P); });
+      } else {
+        timed(kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, st>>>(dframes, P); });
+      }
+      if (n_xt) timed(kKXCount, [&] { k_xcount<<<n_xt, kXThreads, 0, st>>>(dframes, P); });
+      timed(kKXRowOffsets, [&] { k_xrow_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
+    } else {
+      if (n_tile)
+        timed(kKCountRank, [&] { launch_count_rank(h->tune_rank_variant, n_tile, st, dframes, P); });
+      if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+      timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
+    }
     // the unattached decode needs only rowStart / attCount: with an aux
     // stream it runs beside the tile bases and the record scatter
     const bool two = aux && fork && join && n_chunk;
@@ -549,11 +595,18 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
         launch_unatt_decode(h->tune_unatt_variant, grid, ust, dframes, P, n_chunk);
       });
     }
-    if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
-    if (n_tile)
-      timed(kKAttScatter, [&] {
-        launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P);
-      });
+    if (xpose) {
+      if (n_xt) {
+        timed(kKXBase, [&] { k_xbase<<<nf * kNSec, kNRow * kXBaseQ, 0, st>>>(dframes, P); });
+        timed(kKXScatter, [&] { launch_xscatter(n_xt, st, dframes, P); });
+      }
+    } else {
+      if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+      if (n_tile)
+        timed(kKAttScatter, [&] {
+          launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P);
+        });
+    }
     if (two) {
       CK(cudaEventRecord(join, aux));
       CK(cudaStreamWaitEvent(st, join, 0));

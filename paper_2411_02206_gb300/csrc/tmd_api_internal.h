@@ -17,7 +17,8 @@ struct TmdServer;  // serving state (tmd_serve.cu)
 // Kernel ids of the instrumentation.
 enum TmdKernel {
   kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode, kKCountRank,
-  kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode, kKNum
+  kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode,
+  kKSegCount, kKSegScan, kKSegRuns, kKXCount, kKXRowOffsets, kKXBase, kKXScatter, kKNum
 };
 
 struct TmdProfile {
@@ -50,6 +51,7 @@ struct tmd_handle {
   int tune_scatter_variant = 1;  // store pattern of the record scatter
   int tune_unatt_variant = 1;    // record write-out of the unattached decode
   int tune_overlap = 0;          // unattached decode on a second stream beside the scatter
+  int tune_place = 0;            // placement: 0 rank + scatter in input order, 1 per-sector transpose
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;
@@ -97,14 +99,16 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
                const TraceReq* trace = nullptr);
 // Scratch layout of one frame.  The zeroed part of all frames is contiguous.
 struct FrameLayout {
-  uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
+  uint32_t n_tblocks, n_tiles, n_groups, n_chunks, n_sblk, n_xtiles;
   size_t z_len, z_lb;                             // offsets in the zeroed part
   size_t track_start, order, keys, kf_pad, kf_time, rank, tile_hist, group_sum, tile_base,
       unatt_start, blk_sum, att_count;            // offsets in the plain part
+  size_t seg_cnt, seg_tot, runs, xt_whist, xt_hist, xt_base;  // transpose placement (xpose)
 };
-// Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts.
+// Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts;
+// with xpose, also the buffers of the per-sector transpose placement.
 void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
-                FrameLayout& L);
+                FrameLayout& L, bool xpose = true);
 
 // Bytes of scratch and of launch record that a call needs.
 void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin,

@@ -23,11 +23,24 @@ constexpr int kScatThreads = 256;        // threads per block of the record scat
 constexpr int kScatCta = 8;              // CTAs per thread-block cluster of the regrouping scatter
 constexpr int kScatThreads2 = 512;       // threads per CTA of the regrouping scatter
 constexpr int kScatClusterSmem = (kTile / kScatCta) * 16 + kNBin * 2;
+// Placement by per-sector transpose (tmd_xpose.cu).
+constexpr int kSegBlk = 4096;            // attached clusters per block of the run search
+constexpr int kSegThreads = 256;         // 16 clusters per thread
+constexpr int kXT = 8192;                // sector-stream positions per transpose tile
+constexpr int kXWarps = 8;               // warps per transpose tile
+constexpr int kXSub = kXT / kXWarps;     // positions per warp
+constexpr int kXThreads = kXWarps * 32;
+constexpr int kXSteps = kXSub / 32;      // steps of 32 positions per warp
+constexpr int kXLook = 8;                // steps of loads in flight per warp (record transpose)
+constexpr int kXCountLook = 16;          // steps of key loads in flight per warp (tile counts)
+constexpr int kXBaseQ = 6;               // threads per row of the tile-base scan
+constexpr int kXScatterSmem = kXT * kRecBytes;
 
 // One frame as the kernels see it: caller inputs, caller outputs, scratch.
 struct FrameDev {
   uint32_t n_tracks, n_att, n_unatt;
   uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
+  uint32_t n_sblk, n_xtiles;  // run-search blocks, transpose tiles (upper bound)
   // per track
   const uint8_t* qpt;
   const uint8_t* row;
@@ -75,6 +88,13 @@ struct FrameDev {
   uint32_t* blk_sum;       // n_tblocks
   uint32_t* len_cursor;    // kLenBuckets (zeroed)
   unsigned long long* lookback;  // n_chunks (zeroed)
+  // placement by per-sector transpose
+  uint32_t* seg_cnt;       // [2][kNSec][n_sblk]: runs, clusters per (sector, block); scanned
+  uint32_t* seg_tot;       // [2][kNSec]: runs, clusters per sector
+  uint2* runs;             // n_att (upper bound): {stream position, first j}, sector-major
+  uint16_t* xt_whist;      // n_xtiles x kXWarps x kNRow: per-warp row counts of a tile
+  uint16_t* xt_hist;       // n_xtiles x kNRow: row counts of a tile
+  uint32_t* xt_base;       // n_xtiles x kNRow: first native index of (tile, row)
 };
 
 // Encoder view of a frame: attached truth in, compressed attached streams out.
@@ -109,6 +129,8 @@ struct PlanDev {
   const uint32_t* pre_warp;   // encoder: warp tasks of 32 tracks
   const uint32_t* pre_chunk;  // unattached chunks
   const uint32_t* pre_kt;     // decoder: warp tasks of 32 tracks
+  const uint32_t* pre_sblk = nullptr;   // run-search blocks
+  const uint32_t* pre_xtile = nullptr;  // transpose tiles (upper bound per frame)
   uint32_t* counters;         // [0] decode/encode task, [1] unattached ticket (zeroed)
 };
 
@@ -176,6 +198,17 @@ cudaError_t prepare_att_scatter();
 void launch_unatt_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                          PlanDev plan, uint32_t n_tickets);
 cudaError_t occupancy_unatt_decode(int* blocks_per_sm);
+// Placement by per-sector transpose (identical results to k_count_rank ...
+// k_att_scatter); grids: run-search blocks (pre_sblk), frames x kNSec,
+// transpose tiles (pre_xtile), frames.
+__global__ void k_seg_count(const FrameDev* frames, PlanDev plan);
+__global__ void k_seg_scan(const FrameDev* frames, PlanDev plan);
+__global__ void k_seg_runs(const FrameDev* frames, PlanDev plan);
+__global__ void k_xcount(const FrameDev* frames, PlanDev plan);
+__global__ void k_xrow_offsets(const FrameDev* frames, PlanDev plan);
+__global__ void k_xbase(const FrameDev* frames, PlanDev plan);
+cudaError_t prepare_xscatter();
+void launch_xscatter(uint32_t grid, cudaStream_t st, const FrameDev* frames, PlanDev plan);
 __global__ void k_selftest_wait(const unsigned long long* never, uint32_t* status);
 __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
                                uint32_t n_tasks);

@@ -72,7 +72,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   FrameLayout L;
   size_t zoff = 256 + ((size_t)kNBin * 4 + 255) / 256 * 256;  // counters + zero bins
   size_t poff = 0;
-  plan_frame(in->n_tracks, in->n_attached, in->n_unattached, zoff, poff, L);
+  plan_frame(in->n_tracks, in->n_attached, in->n_unattached, zoff, poff, L, false);
   const size_t zbytes = (zoff + 255) / 256 * 256;
   const size_t need = zbytes + poff;
   if (need > kScratchMax) {

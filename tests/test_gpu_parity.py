@@ -185,27 +185,32 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
     dev = frames.to_torch(of, "cuda:0")
     saved = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
                                                "scatter_variant", "overlap",
-                                               "unatt_variant")}
+                                               "unatt_variant", "place")}
+
+    def check(what):
+        native, rs, att, st = dec.decode(dev)
+        gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
+               frames.to_numpy(att, np.uint32), int(st.item()))
+        G.assert_same_decode(gpu, ora, what)
+
     try:
-        for uv in range(2):
-            dec.tmd_tune_set("unatt_variant", uv)
-            native, rs, att, st = dec.decode(dev)
-            gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
-                   frames.to_numpy(att, np.uint32), int(st.item()))
-            G.assert_same_decode(gpu, ora, f"unatt {uv}")
-        for ov in range(2):
-            for dv in range(4):
-                for rv in range(3):
-                    for sv in range(4):
-                        dec.tmd_tune_set("overlap", ov)
-                        dec.tmd_tune_set("decode_variant", dv)
-                        dec.tmd_tune_set("rank_variant", rv)
-                        dec.tmd_tune_set("scatter_variant", sv)
-                        native, rs, att, st = dec.decode(dev)
-                        gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
-                               frames.to_numpy(att, np.uint32), int(st.item()))
-                        G.assert_same_decode(gpu, ora,
-                                             f"overlap {ov} decode {dv} rank {rv} scatter {sv}")
+        for pl in range(2):
+            dec.tmd_tune_set("place", pl)
+            for uv in range(2):
+                dec.tmd_tune_set("unatt_variant", uv)
+                check(f"place {pl} unatt {uv}")
+            for ov in range(2):
+                dec.tmd_tune_set("overlap", ov)
+                for dv in range(4):
+                    dec.tmd_tune_set("decode_variant", dv)
+                    if pl == 1:  # the transpose placement has no ranking/scatter variants
+                        check(f"place 1 overlap {ov} decode {dv}")
+                        continue
+                    for rv in range(3):
+                        for sv in range(4):
+                            dec.tmd_tune_set("rank_variant", rv)
+                            dec.tmd_tune_set("scatter_variant", sv)
+                            check(f"place 0 overlap {ov} decode {dv} rank {rv} scatter {sv}")
     finally:
         for k, v in saved.items():
             dec.tmd_tune_set(k, v)
@@ -228,16 +233,19 @@ def test_unaligned_caller_arrays(dec):
         buf = torch.zeros(t.numel() + 1, dtype=t.dtype, device=t.device)
         buf[1:] = t
         shifted[k] = buf[1:]
-    for sv in range(4):
+    place = dec.tmd_tune_get("place")
+    for pl, sv in ((0, 0), (0, 1), (0, 2), (0, 3), (1, 1)):
+        dec.tmd_tune_set("place", pl)
         dec.tmd_tune_set("scatter_variant", sv)
         for dv in range(4):
             dec.tmd_tune_set("decode_variant", dv)
             native, rs, att, st = dec.decode(shifted)
             gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
                    frames.to_numpy(att, np.uint32), int(st.item()))
-            G.assert_same_decode(gpu, ora, f"unaligned, scatter {sv} decode {dv}")
-    dec.tmd_tune_set("scatter_variant", 0)
-    dec.tmd_tune_set("decode_variant", 1)
+            G.assert_same_decode(gpu, ora, f"unaligned, place {pl} scatter {sv} decode {dv}")
+    dec.tmd_tune_set("scatter_variant", 1)
+    dec.tmd_tune_set("decode_variant", 3)
+    dec.tmd_tune_set("place", place)
 
 
 def test_host_stream_pipeline(dec):
