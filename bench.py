@@ -185,7 +185,11 @@ def kernel_bytes(name, nt, na, nu):
                       code, 7 B of charges, sigmas and flags) and the 12 B
                       native record written;
       k_xcount, k_seg_count, k_seg_runs
-                      per attached cluster the 2 B key read."""
+                      per attached cluster the 2 B key read;
+      k_track_keys    per cluster after the first of its track the 2 B of row
+                      and sector/leg differences read, per cluster the 2 B key
+                      written, per track 10 B (row, slice, length, start,
+                      order)."""
     n_tiles = -(-na // 32768)
     table = {
         "k_track_decode": 8 * (na - nt) + 19 * nt + 8 * na,
@@ -196,6 +200,7 @@ def kernel_bytes(name, nt, na, nu):
         "k_xcount": 2 * na,
         "k_seg_count": 2 * na,
         "k_seg_runs": 2 * na,
+        "k_track_keys": 2 * (na - nt) + 2 * na + 10 * nt,
     }
     return table.get(name)
 
@@ -324,7 +329,7 @@ def run(args):
     _apply_tune(dec, args.tune)
     tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
                                               "scatter_variant", "overlap", "unatt_variant",
-                                              "place", "decode_blocks_per_sm",
+                                              "place", "prekey", "decode_blocks_per_sm",
                                               "unatt_blocks_per_sm")}
     for _ in range(args.warmup):
         dec.tmd_decode_frame(fin, fout, stream)

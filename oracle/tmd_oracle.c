@@ -22,8 +22,9 @@
  * reading: a linear Kalman filter in the sector-local frame, with a parabola
  * (y, dy/dx, d2y/dx2) for the bending plane and a line (t, dt/dx) for drift
  * time.  Every floating-point operation is binary32, round-to-nearest-even,
- * performed in the order written; this file must be compiled with
- * -ffp-contract=off so that no multiply-add is fused.
+ * performed in the order written; the model's multiply-adds are written as
+ * explicit fmaf calls (one rounding each, C99 7.12.13), and this file must be
+ * compiled with -ffp-contract=off so that the compiler fuses nothing else.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
  */
@@ -130,7 +131,7 @@ static uint32_t o_quant(float v, float lo, float hi) {
 
 /* pad code (1/64 pad) -> y [cm] on row r */
 static float o_pad_to_y(uint32_t padq, int r) {
-  return ((float)padq * 0.015625f - g_halfnp[r]) * g_w[r];
+  return fmaf((float)padq, 0.015625f, -g_halfnp[r]) * g_w[r];
 }
 /* time code (1/32 bin) -> t [bin] */
 static float o_time_to_t(uint32_t timeq) { return (float)timeq * 0.03125f; }
@@ -203,30 +204,30 @@ static void o_propagate(const OModel* m, OState* s, int r) {
   float dx = g_x[r] - s->x;
   float adx = fabsf(dx);
   float h = (0.5f * s->c) * dx;
-  s->y = s->y + dx * (s->ty + h);
-  s->ty = s->ty + s->c * dx;
-  s->t = s->t + s->tt * dx;
+  s->y = fmaf(dx, s->ty + h, s->y);
+  s->ty = fmaf(s->c, dx, s->ty);
+  s->t = fmaf(s->tt, dx, s->t);
   s->x = g_x[r];
   s->row = r;
   /* y-block: C' = F C F^T + diag(0, qty |dx|, 0) */
   float h2 = (0.5f * dx) * dx;
-  float a0 = (s->c00 + dx * s->c01) + h2 * s->c02;
-  float a1 = (s->c01 + dx * s->c11) + h2 * s->c12;
-  float a2 = (s->c02 + dx * s->c12) + h2 * s->c22;
-  float b1 = s->c11 + dx * s->c12;
-  float b2 = s->c12 + dx * s->c22;
-  s->c00 = (a0 + dx * a1) + h2 * a2;
-  s->c01 = a1 + dx * a2;
+  float a0 = fmaf(h2, s->c02, fmaf(dx, s->c01, s->c00));
+  float a1 = fmaf(h2, s->c12, fmaf(dx, s->c11, s->c01));
+  float a2 = fmaf(h2, s->c22, fmaf(dx, s->c12, s->c02));
+  float b1 = fmaf(dx, s->c12, s->c11);
+  float b2 = fmaf(dx, s->c22, s->c12);
+  s->c00 = fmaf(h2, a2, fmaf(dx, a1, a0));
+  s->c01 = fmaf(dx, a2, a1);
   s->c02 = a2;
-  s->c11 = (b1 + dx * b2) + m->qty * adx;
+  s->c11 = fmaf(m->qty, adx, fmaf(dx, b2, b1));
   s->c12 = b2;
   /* c22 unchanged */
   /* t-block: D' = G D G^T + diag(0, qtt |dx|) */
-  float e0 = s->d00 + dx * s->d01;
-  float e1 = s->d01 + dx * s->d11;
-  s->d00 = e0 + dx * e1;
+  float e0 = fmaf(dx, s->d01, s->d00);
+  float e1 = fmaf(dx, s->d11, s->d01);
+  s->d00 = fmaf(dx, e1, e0);
   s->d01 = e1;
-  s->d11 = s->d11 + m->qtt * adx;
+  s->d11 = fmaf(m->qtt, adx, s->d11);
 }
 
 /* Kalman update of both blocks with a measured (y, t). */
@@ -234,25 +235,25 @@ static void o_update(const OModel* m, OState* s, float ym, float tm) {
   float inv = 1.0f / (s->c00 + m->sy2);
   float k0 = s->c00 * inv, k1 = s->c01 * inv, k2 = s->c02 * inv;
   float r = ym - s->y;
-  s->y = s->y + k0 * r;
-  s->ty = s->ty + k1 * r;
-  s->c = s->c + k2 * r;
+  s->y = fmaf(k0, r, s->y);
+  s->ty = fmaf(k1, r, s->ty);
+  s->c = fmaf(k2, r, s->c);
   float c00 = s->c00, c01 = s->c01, c02 = s->c02;
-  s->c00 = c00 - k0 * c00;
-  s->c01 = c01 - k0 * c01;
-  s->c02 = c02 - k0 * c02;
-  s->c11 = s->c11 - k1 * c01;
-  s->c12 = s->c12 - k1 * c02;
-  s->c22 = s->c22 - k2 * c02;
+  s->c00 = fmaf(-k0, c00, c00);
+  s->c01 = fmaf(-k0, c01, c01);
+  s->c02 = fmaf(-k0, c02, c02);
+  s->c11 = fmaf(-k1, c01, s->c11);
+  s->c12 = fmaf(-k1, c02, s->c12);
+  s->c22 = fmaf(-k2, c02, s->c22);
   float invt = 1.0f / (s->d00 + m->st2);
   float g0 = s->d00 * invt, g1 = s->d01 * invt;
   float rt = tm - s->t;
-  s->t = s->t + g0 * rt;
-  s->tt = s->tt + g1 * rt;
+  s->t = fmaf(g0, rt, s->t);
+  s->tt = fmaf(g1, rt, s->tt);
   float d00 = s->d00, d01 = s->d01;
-  s->d00 = d00 - g0 * d00;
-  s->d01 = d01 - g0 * d01;
-  s->d11 = s->d11 - g1 * d01;
+  s->d00 = fmaf(-g0, d00, d00);
+  s->d01 = fmaf(-g0, d01, d01);
+  s->d11 = fmaf(-g1, d01, s->d11);
 }
 
 /* Apply the key step (row difference, sector/leg difference) of one cluster,
@@ -270,7 +271,7 @@ static uint32_t o_step_predict(const OModel* m, OState* s, uint8_t row_diff,
   if (leg != 0) o_leg_change(m, s);
   if (sd != 0) o_sector_change(m, s, (s->sec + sd) % O_NSEC);
   o_propagate(m, s, row);
-  float pp = s->y * g_invw[row] + g_halfnp[row];
+  float pp = fmaf(s->y, g_invw[row], g_halfnp[row]);
   *pred_padq = o_quant(pp * 64.0f, 0.0f, O_PAD_HI);
   *pred_timeq = o_quant(s->t * 32.0f, 0.0f, O_TIME_HI);
   if (pred_y) *pred_y = s->y;

@@ -274,7 +274,7 @@ static const char* kKernelNames[kKNum] = {
     "k_put_record", "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_track_decode",
     "k_count_rank", "k_group_sum", "k_row_offsets", "k_tile_base", "k_att_scatter",
     "k_unatt_decode", "k_track_encode", "k_seg_count", "k_seg_scan", "k_seg_runs", "k_xcount",
-    "k_xrow_offsets", "k_xbase", "k_xscatter"};
+    "k_xrow_offsets", "k_xbase", "k_xscatter", "k_track_keys"};
 
 cudaEvent_t TmdProfile::get() {
   if (pool.empty()) {
@@ -352,7 +352,7 @@ struct RecordLayout {
 static RecordLayout record_layout(uint32_t n, bool enc) {
   RecordLayout r;
   r.pre = 0;
-  r.frames = align_up(8 * ((size_t)n + 1) * 4, 64);
+  r.frames = align_up(9 * ((size_t)n + 1) * 4, 64);
   r.enc = align_up(r.frames + (size_t)n * sizeof(FrameDev), 64);
   r.bytes = align_up(r.enc + (enc ? (size_t)n * sizeof(EncDev) : 0), 64);
   r.counters_unused = 0;
@@ -396,7 +396,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   int slot = 0;
   if ((rc = h->acquire_slot(record_bytes, slot)) != TMD_OK) return rc;
   tmd_handle::Slot& S = h->slots[slot];
-  const bool two = h->tune_overlap && !tin;
+  const bool two = (h->tune_overlap || h->tune_prekey) && !tin;
   rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on,
                    two ? h->aux : nullptr, h->fork, h->join, trace);
   if (rc != TMD_OK) return rc;
@@ -427,10 +427,11 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   uint32_t* pre_kt = pre + 5 * (nf + 1);
   uint32_t* pre_sblk = pre + 6 * (nf + 1);
   uint32_t* pre_xtile = pre + 7 * (nf + 1);
+  uint32_t* pre_kblk = pre + 8 * (nf + 1);
   FrameDev* fd = reinterpret_cast<FrameDev*>(host + R.frames);
   EncDev* ed = reinterpret_cast<EncDev*>(host + R.enc);
   pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = pre_kt[0] = 0;
-  pre_sblk[0] = pre_xtile[0] = 0;
+  pre_sblk[0] = pre_xtile[0] = pre_kblk[0] = 0;
   uint32_t* zero_bins = reinterpret_cast<uint32_t*>(zb + 256);
   for (uint32_t f = 0; f < nf; f++) {
     FrameDev& F = fd[f];
@@ -499,6 +500,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     pre_kt[f + 1] = pre_kt[f] + ceil_div(F.n_tracks, 32);
     pre_sblk[f + 1] = pre_sblk[f] + l.n_sblk;
     pre_xtile[f + 1] = pre_xtile[f] + l.n_xtiles;
+    pre_kblk[f + 1] = pre_kblk[f] + ceil_div(F.n_tracks, kKeyTracks);
   }
   PlanDev P;
   const uint32_t* dpre = reinterpret_cast<const uint32_t*>(dev + R.pre);
@@ -511,6 +513,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   P.pre_kt = dpre + 5 * (nf + 1);
   P.pre_sblk = dpre + 6 * (nf + 1);
   P.pre_xtile = dpre + 7 * (nf + 1);
+  P.pre_kblk = dpre + 8 * (nf + 1);
   P.counters = reinterpret_cast<uint32_t*>(zb);
   const FrameDev* dframes = reinterpret_cast<const FrameDev*>(dev + R.frames);
   const EncDev* denc = reinterpret_cast<const EncDev*>(dev + R.enc);
@@ -532,9 +535,12 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   auto timed = [&](int id, auto&& launch) { timed_on(st, id, launch); };
   NvtxRange call_range(encode ? "tmd.encode" : (trace ? "tmd.trace" : "tmd.decode"));
   cudaError_t put_err = cudaSuccess;
-  timed(kKPutRecord, [&] { put_err = put_record(host, R.bytes, dev, zb, zbytes, st); });
+  const bool zs = put_record_zeroes_status(R.frames, nf);
+  timed(kKPutRecord, [&] {
+    put_err = put_record(host, R.bytes, dev, zb, zbytes, st, R.frames, zs ? nf : 0u);
+  });
   CK(put_err);
-  timed(kKZeroStatus, [&] { k_zero_status<<<1, 256, 0, st>>>(dframes, nf); });
+  if (!zs) timed(kKZeroStatus, [&] { k_zero_status<<<1, 256, 0, st>>>(dframes, nf); });
   const uint32_t n_tblk = pre_tblk[nf], n_tile = pre_tile[nf], n_grp = pre_grp[nf];
   const uint32_t n_warp = pre_warp[nf], n_chunk = pre_chunk[nf];
   if (n_tblk) timed(kKTrackScan1, [&] { k_track_scan1<<<n_tblk, 256, 0, st>>>(dframes, P); });
@@ -551,65 +557,99 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     }
   } else {
     const uint32_t n_kt = pre_kt[nf];
-    if (n_kt) {  // warp tasks of 32 tracks, taken from counters[0]
+    const bool xpose = h->tune_place == 1;
+    const bool prekey = h->tune_prekey == 1;
+    const uint32_t n_sblk = pre_sblk[nf], n_xt = pre_xtile[nf];
+    const bool two = aux && fork && join;
+    // the phases of the chain, each on a given stream
+    auto decode = [&](bool keys) {  // warp tasks of 32 tracks, taken from counters[0]
+      if (!n_kt) return;
       const int var = h->tune_decode_variant;
       int bps = h->occ_decode_v[var];
       if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
       const uint32_t per_block = kDecodeThreads / 32;
       const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
           (uint32_t)(h->sms * bps), (n_kt + per_block - 1) / per_block));
-      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt); });
-    }
-    const bool xpose = h->tune_place == 1;
-    const uint32_t n_sblk = pre_sblk[nf], n_xt = pre_xtile[nf];
-    if (xpose) {
-      if (n_sblk) {
-        timed(kKSegCount, [&] { k_seg_count<<<n_sblk, kSegThreads, 0, st>>>(dframes, P); });
-        timed(kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, st>>>(dframes, P); });
-        timed(kKSegRuns, [&] { k_seg_runs<<<n_sblk, kSegThreads, 0, st>>>(dframes, P); });
+      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt, keys); });
+    };
+    auto counts = [&](cudaStream_t s_) {  // per-row counts, row offsets (keys only)
+      if (xpose) {
+        if (n_sblk) {
+          timed_on(s_, kKSegCount, [&] { k_seg_count<<<n_sblk, kSegThreads, 0, s_>>>(dframes, P); });
+          timed_on(s_, kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, s_>>>(dframes, P); });
+          timed_on(s_, kKSegRuns, [&] { k_seg_runs<<<n_sblk, kSegThreads, 0, s_>>>(dframes, P); });
+        } else {
+          timed_on(s_, kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, s_>>>(dframes, P); });
+        }
+        if (n_xt) timed_on(s_, kKXCount, [&] { k_xcount<<<n_xt, kXThreads, 0, s_>>>(dframes, P); });
+        timed_on(s_, kKXRowOffsets, [&] { k_xrow_offsets<<<nf, 1024, 0, s_>>>(dframes, P); });
       } else {
-        timed(kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, st>>>(dframes, P); });
+        if (n_tile)
+          timed_on(s_, kKCountRank, [&] { launch_count_rank(h->tune_rank_variant, n_tile, s_, dframes, P); });
+        if (n_grp) timed_on(s_, kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, s_>>>(dframes, P); });
+        timed_on(s_, kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, s_>>>(dframes, P); });
       }
-      if (n_xt) timed(kKXCount, [&] { k_xcount<<<n_xt, kXThreads, 0, st>>>(dframes, P); });
-      timed(kKXRowOffsets, [&] { k_xrow_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
-    } else {
-      if (n_tile)
-        timed(kKCountRank, [&] { launch_count_rank(h->tune_rank_variant, n_tile, st, dframes, P); });
-      if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
-      timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
-    }
-    // the unattached decode needs only rowStart / attCount: with an aux
-    // stream it runs beside the tile bases and the record scatter
-    const bool two = aux && fork && join && n_chunk;
-    cudaStream_t ust = st;
-    if (two) {
-      CK(cudaEventRecord(fork, st));
-      CK(cudaStreamWaitEvent(aux, fork, 0));
-      ust = aux;
-    }
-    if (n_chunk) {
+    };
+    auto bases = [&](cudaStream_t s_) {  // first native index of every tile and row
+      if (xpose) {
+        if (n_xt) timed_on(s_, kKXBase, [&] { k_xbase<<<nf * kNSec, kNRow * kXBaseQ, 0, s_>>>(dframes, P); });
+      } else if (n_grp) {
+        timed_on(s_, kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, s_>>>(dframes, P); });
+      }
+    };
+    auto unatt = [&](cudaStream_t s_) {  // needs rowStart and the attached counts
+      if (!n_chunk) return;
       int bps = h->occ_unatt;
       if (h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;
       const uint32_t grid = std::min<uint32_t>(n_chunk, (uint32_t)(h->sms * bps));
-      timed_on(ust, kKUnattDecode, [&] {
-        launch_unatt_decode(h->tune_unatt_variant, grid, ust, dframes, P, n_chunk);
+      timed_on(s_, kKUnattDecode, [&] {
+        launch_unatt_decode(h->tune_unatt_variant, grid, s_, dframes, P, n_chunk);
       });
-    }
-    if (xpose) {
-      if (n_xt) {
-        timed(kKXBase, [&] { k_xbase<<<nf * kNSec, kNRow * kXBaseQ, 0, st>>>(dframes, P); });
-        timed(kKXScatter, [&] { launch_xscatter(n_xt, st, dframes, P); });
+    };
+    auto place = [&]() {  // native records of the attached clusters
+      if (xpose) {
+        if (n_xt) timed(kKXScatter, [&] { launch_xscatter(n_xt, st, dframes, P); });
+      } else if (n_tile) {
+        timed(kKAttScatter, [&] { launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P); });
       }
+    };
+    if (prekey) {
+      // keys first; with a second stream everything that needs only keys runs
+      // beside the track decoder
+      const uint32_t n_kblk = pre_kblk[nf];
+      if (n_kblk) timed(kKTrackKeys, [&] { k_track_keys<<<n_kblk, kKeyTracks, 0, st>>>(dframes, P); });
+      cudaStream_t ks = st;
+      if (two) {
+        CK(cudaEventRecord(fork, st));
+        CK(cudaStreamWaitEvent(aux, fork, 0));
+        ks = aux;
+      }
+      counts(ks);
+      bases(ks);
+      unatt(ks);
+      decode(false);
+      if (two) {
+        CK(cudaEventRecord(join, aux));
+        CK(cudaStreamWaitEvent(st, join, 0));
+      }
+      place();
     } else {
-      if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
-      if (n_tile)
-        timed(kKAttScatter, [&] {
-          launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P);
-        });
-    }
-    if (two) {
-      CK(cudaEventRecord(join, aux));
-      CK(cudaStreamWaitEvent(st, join, 0));
+      decode(true);
+      counts(st);
+      // the unattached decode needs only rowStart / attCount: with an aux
+      // stream it runs beside the tile bases and the record scatter
+      const bool fork_u = two && n_chunk;
+      if (fork_u) {
+        CK(cudaEventRecord(fork, st));
+        CK(cudaStreamWaitEvent(aux, fork, 0));
+      }
+      unatt(fork_u ? aux : st);
+      bases(st);
+      place();
+      if (fork_u) {
+        CK(cudaEventRecord(join, aux));
+        CK(cudaStreamWaitEvent(st, join, 0));
+      }
     }
   }
   CK(cudaGetLastError());

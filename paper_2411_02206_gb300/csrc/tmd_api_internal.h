@@ -18,7 +18,8 @@ struct TmdServer;  // serving state (tmd_serve.cu)
 enum TmdKernel {
   kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode, kKCountRank,
   kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode,
-  kKSegCount, kKSegScan, kKSegRuns, kKXCount, kKXRowOffsets, kKXBase, kKXScatter, kKNum
+  kKSegCount, kKSegScan, kKSegRuns, kKXCount, kKXRowOffsets, kKXBase, kKXScatter, kKTrackKeys,
+  kKNum
 };
 
 struct TmdProfile {
@@ -52,6 +53,7 @@ struct tmd_handle {
   int tune_unatt_variant = 1;    // record write-out of the unattached decode
   int tune_overlap = 0;          // unattached decode on a second stream beside the scatter
   int tune_place = 0;            // placement: 0 rank + scatter in input order, 1 per-sector transpose
+  int tune_prekey = 0;           // 1: key walk first, key-only work beside the track decoder
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;

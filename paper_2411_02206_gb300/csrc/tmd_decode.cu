@@ -64,7 +64,7 @@ struct WarpStage {
 
 }  // namespace
 
-template <int R, int MINB>
+template <int R, int MINB, bool KEYS>
 __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const FrameDev* frames,
                                                                        PlanDev plan,
                                                                        uint32_t n_tasks) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const Fra
         const uint32_t di = __shfl_sync(kFull, dm1, i);
         if (k < ni) {
           const uint32_t a = W.a[i * P + sq];
-          key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
+          if (KEYS) key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
           pad_o[ji + k] = (uint16_t)(a >> 16);
           time_o[ji + k] = W.b[i * P + sq];
         }
@@ -268,7 +268,7 @@ __device__ __forceinline__ RoundBase issue_round(uint32_t* lb, uint32_t k0, uint
 
 }  // namespace
 
-template <int R, int MINB>
+template <int R, int MINB, bool KEYS>
 __global__ void __launch_bounds__(kDecodeThreads, MINB)
     k_track_decode_async(const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
   static_assert(R == 8 || R == 16, "round length");
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
         const uint32_t ni = __shfl_sync(kFull, n, i), ji = __shfl_sync(kFull, j0, i);
         if (k < ni) {
           const uint32_t a = S.kp[i * P + sq];
-          key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
+          if (KEYS) key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
           pad_o[ji + k] = (uint16_t)(a >> 16);
           time_o[ji + k] = bb[i * Lay::kLane + Lay::kTr0 + sq];
         }
@@ -377,24 +377,116 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
 }
 
 // Variants: 0 -> R = 32, 1 -> R = 16 (synchronous staging), 2 -> R = 8,
-// 3 -> R = 16 (asynchronous double-buffered staging).
-void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_tasks) {
+// 3 -> R = 16 (asynchronous double-buffered staging).  With keys == false the
+// (sector,row) keys are not written (k_track_keys wrote them before).
+template <bool KEYS>
+static void launch_track_decode_t(int variant, uint32_t grid, cudaStream_t st,
+                                  const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
   switch (variant) {
-    case 0: k_track_decode<32, 1><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    case 2: k_track_decode_async<8, 6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    case 3: k_track_decode_async<16, 4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    default: k_track_decode<16, 1><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 0: k_track_decode<32, 1, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 2: k_track_decode_async<8, 6, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 3: k_track_decode_async<16, 4, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    default: k_track_decode<16, 1, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
   }
+}
+
+void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
+                         PlanDev plan, uint32_t n_tasks, bool keys) {
+  if (keys) launch_track_decode_t<true>(variant, grid, st, frames, plan, n_tasks);
+  else launch_track_decode_t<false>(variant, grid, st, frames, plan, n_tasks);
 }
 
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm) {
   switch (variant) {
-    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<32, 1>, kDecodeThreads, 0);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<8, 6>, kDecodeThreads, 0);
-    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<16, 4>, kDecodeThreads, 0);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<16, 1>, kDecodeThreads, 0);
+    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<32, 1, true>, kDecodeThreads, 0);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<8, 6, true>, kDecodeThreads, 0);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<16, 4, true>, kDecodeThreads, 0);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<16, 1, true>, kDecodeThreads, 0);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Key walk.  The (sector,row) key of every attached cluster depends only on
+// the row and sector/leg differences (the track model never feeds back into
+// the walk), so this integer-only pass can run before the track decoder and
+// everything that needs only keys -- per-row counts and ranks, row offsets,
+// the unattached decode -- can run beside the decoder.
+//
+// A block takes kKeyTracks consecutive tracks: their clusters and their
+// differences are contiguous ranges.  The block moves through its cluster
+// range in windows of kKeyWin clusters: it loads the differences the window
+// needs into shared memory with aligned word loads, each thread walks the
+// part of its track inside the window (carrying row and sector from the
+// previous window), and the window's keys leave with word stores.
+__global__ void __launch_bounds__(kKeyTracks) k_track_keys(const FrameDev* frames, PlanDev plan) {
+  __shared__ __align__(16) uint8_t s_rd[kKeyWin + kKeyTracks + 8];
+  __shared__ __align__(16) uint8_t s_sl[kKeyWin + kKeyTracks + 8];
+  __shared__ __align__(16) uint16_t s_key[kKeyWin];
+  const uint32_t f = find_frame(plan.pre_kblk, plan.n_frames, blockIdx.x);
+  const FrameDev& F = frames[f];
+  if (*F.status & kStCount) return;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t t0 = (blockIdx.x - plan.pre_kblk[f]) * (uint32_t)kKeyTracks;
+  const uint32_t tend = min(t0 + (uint32_t)kKeyTracks, F.n_tracks);
+  const uint32_t j_lo = F.track_start[t0], j_hi = F.track_start[tend];
+  const uint32_t d_lo = j_lo - t0, d_hi = j_hi - tend;  // differences of the block's tracks
+  const uint32_t t = t0 + tid;
+  uint32_t st = 0, j0 = 0, n = 0, raw = 0, sec = 0;
+  if (t < tend) {
+    j0 = F.track_start[t];
+    n = F.ncl[t];
+    raw = F.row[t];
+    sec = F.slice[t];
+    if (raw >= (uint32_t)kNRow || sec >= (uint32_t)kNSec) st |= kStRow;
+    if (sec >= (uint32_t)kNSec) sec = kNSec - 1;
+  }
+  const uint32_t dm1 = j0 - t - 1u;  // difference of cluster j of the track: j - t - 1
+  uint16_t* __restrict__ ko = F.keys;
+  for (uint32_t J = j_lo; J < j_hi; J += kKeyWin) {
+    const uint32_t Jend = min(J + (uint32_t)kKeyWin, j_hi);
+    // differences of the window's clusters: j - t - 1 for t in [t0, tend)
+    const uint32_t dA = max(J > tend ? J - tend : 0u, d_lo);
+    const uint32_t dB = min(Jend - t0, d_hi);
+    const uintptr_t rd_a = reinterpret_cast<uintptr_t>(F.row_diff + dA);
+    const uintptr_t sl_a = reinterpret_cast<uintptr_t>(F.sld + dA);
+    const uint32_t rd_off = (uint32_t)(rd_a & 3u), sl_off = (uint32_t)(sl_a & 3u);
+    if (dB > dA) {
+      // aligned words covering [dA, dB): inside the pages that hold the range
+      const uint32_t nrd = (rd_off + (dB - dA) + 3) / 4, nsl = (sl_off + (dB - dA) + 3) / 4;
+      const uint32_t* rw = reinterpret_cast<const uint32_t*>(rd_a - rd_off);
+      const uint32_t* sw = reinterpret_cast<const uint32_t*>(sl_a - sl_off);
+      uint32_t* srd = reinterpret_cast<uint32_t*>(s_rd);
+      uint32_t* ssl = reinterpret_cast<uint32_t*>(s_sl);
+      for (uint32_t i = tid; i < nrd; i += kKeyTracks) srd[i] = __ldg(rw + i);
+      for (uint32_t i = tid; i < nsl; i += kKeyTracks) ssl[i] = __ldg(sw + i);
+    }
+    __syncthreads();
+    const uint32_t ja = max(j0, J), jb = min(j0 + n, Jend);
+    for (uint32_t j = ja; j < jb; j++) {
+      if (j != j0) {
+        const uint32_t d = dm1 + (j - j0);
+        const uint32_t rd = s_rd[rd_off + d - dA], sld = s_sl[sl_off + d - dA];
+        const uint32_t leg = sld / kNSec, sd = sld - leg * kNSec;
+        raw = (raw + rd) & 255u;
+        if (sd != 0) sec = sec + sd >= (uint32_t)kNSec ? sec + sd - kNSec : sec + sd;
+      }
+      uint32_t row = raw;
+      if (row >= (uint32_t)kNRow) { st |= kStRow; row = kNRow - 1; }
+      s_key[j - J] = (uint16_t)(sec * kNRow + row);
+    }
+    __syncthreads();
+    // keys out: one key to a 4-byte boundary, then words, then the last key
+    const uint32_t nk = Jend - J;
+    const uint32_t head = min(J & 1u, nk);
+    if (tid < head) ko[J] = s_key[0];
+    const uint32_t nw = (nk - head) / 2;
+    uint32_t* kw = reinterpret_cast<uint32_t*>(ko + J + head);
+    for (uint32_t i = tid; i < nw; i += kKeyTracks)
+      kw[i] = (uint32_t)s_key[head + 2 * i] | ((uint32_t)s_key[head + 2 * i + 1] << 16);
+    if (((nk - head) & 1u) && tid == 0) ko[Jend - 1] = s_key[nk - 1];
+    __syncthreads();
+  }
+  if (__syncthreads_or(st != 0) && tid == 0) atomicOr(F.status, st);
 }
 
 // Float-path trace: one thread per selected track walks it through the

@@ -131,6 +131,7 @@ struct PlanDev {
   const uint32_t* pre_kt;     // decoder: warp tasks of 32 tracks
   const uint32_t* pre_sblk = nullptr;   // run-search blocks
   const uint32_t* pre_xtile = nullptr;  // transpose tiles (upper bound per frame)
+  const uint32_t* pre_kblk = nullptr;   // key-walk blocks
   uint32_t* counters;         // [0] decode/encode task, [1] unattached ticket (zeroed)
 };
 
@@ -165,7 +166,10 @@ struct RecordChunk {
   uint4 w[W];
 };
 cudaError_t put_record(const void* host, size_t bytes, void* dev, void* zero, size_t zero_bytes,
-                       cudaStream_t st);
+                       cudaStream_t st, size_t frames_off = 0, uint32_t n_status = 0);
+// Whether put_record(..., frames_off, n_frames) clears the frames' status
+// words itself (all descriptors in its first launch).
+bool put_record_zeroes_status(size_t frames_off, uint32_t n_frames);
 __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames);
 __global__ void k_track_scan1(const FrameDev* frames, PlanDev plan);
 __global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);
@@ -186,7 +190,12 @@ __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
 // two functions.  Its warps take tasks of 32 tracks (pre_kt of the plan) from
 // counters[0].
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_tasks);
+                         PlanDev plan, uint32_t n_tasks, bool keys = true);
+// Key walk of the attached clusters (keys only, integer): one block per
+// kKeyTracks consecutive tracks (pre_kblk), in windows of kKeyWin clusters.
+constexpr int kKeyTracks = 128;
+constexpr int kKeyWin = 12288;
+__global__ void k_track_keys(const FrameDev* frames, PlanDev plan);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
 // Record scatter variants 0..3 (identical results; see tmd_scatter.cu),
 // launched over n_tiles ranking tiles of all frames.

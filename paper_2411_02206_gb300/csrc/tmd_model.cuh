@@ -8,8 +8,10 @@
 //   y-block (y, ty = dy/dx, c = d2y/dx2), a parabola in x, 3x3 covariance;
 //   t-block (t, tt = dt/dx), a line in drift time, 2x2 covariance.
 // Encoder and decoder run the same sequence of binary32 operations; every
-// operation below is an explicit round-to-nearest intrinsic so that no
-// multiply-add can be contracted, whatever the compiler flags.
+// operation below is an explicit round-to-nearest intrinsic, the model's
+// multiply-adds are explicit fused multiply-adds (one rounding each), and the
+// compiler contracts nothing else (-fmad=false): the arithmetic is fixed
+// whatever the compiler does with the rest of the code.
 #pragma once
 #include <cstdint>
 
@@ -31,6 +33,8 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+// a * b + c with a single rounding
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 // 1/x correctly rounded: the same value as the division 1.0f / x.
 __device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
 
@@ -96,9 +100,9 @@ struct Track {
 };
 
 // y of a pad code on a row with geometry G = {x, w, 1/w, nPads/2}:
-// (pad - nPads/2) * w.
+// (pad / 64 - nPads/2) * w.
 __device__ __forceinline__ float pad_to_y(const float4& G, uint32_t padq) {
-  return fmul(fsub(fmul((float)padq, 0.015625f), G.w), G.y);
+  return fmul(ffma((float)padq, 0.015625f, -G.w), G.y);
 }
 __device__ __forceinline__ float time_to_t(uint32_t timeq) {
   return fmul((float)timeq, 0.03125f);
@@ -188,27 +192,27 @@ __device__ __forceinline__ void propagate_predict(const float4& G, Track& s, uin
   const float dx = fsub(xr, s.x);
   const float adx = fabsf(dx);
   const float h = fmul(fmul(0.5f, s.c), dx);
-  s.y = fadd(s.y, fmul(dx, fadd(s.ty, h)));
-  s.ty = fadd(s.ty, fmul(s.c, dx));
-  s.t = fadd(s.t, fmul(s.tt, dx));
+  s.y = ffma(dx, fadd(s.ty, h), s.y);
+  s.ty = ffma(s.c, dx, s.ty);
+  s.t = ffma(s.tt, dx, s.t);
   s.x = xr;
   const float h2 = fmul(fmul(0.5f, dx), dx);
-  const float a0 = fadd(fadd(s.c00, fmul(dx, s.c01)), fmul(h2, s.c02));
-  const float a1 = fadd(fadd(s.c01, fmul(dx, s.c11)), fmul(h2, s.c12));
-  const float a2 = fadd(fadd(s.c02, fmul(dx, s.c12)), fmul(h2, s.c22));
-  const float b1 = fadd(s.c11, fmul(dx, s.c12));
-  const float b2 = fadd(s.c12, fmul(dx, s.c22));
-  s.c00 = fadd(fadd(a0, fmul(dx, a1)), fmul(h2, a2));
-  s.c01 = fadd(a1, fmul(dx, a2));
+  const float a0 = ffma(h2, s.c02, ffma(dx, s.c01, s.c00));
+  const float a1 = ffma(h2, s.c12, ffma(dx, s.c11, s.c01));
+  const float a2 = ffma(h2, s.c22, ffma(dx, s.c12, s.c02));
+  const float b1 = ffma(dx, s.c12, s.c11);
+  const float b2 = ffma(dx, s.c22, s.c12);
+  s.c00 = ffma(h2, a2, ffma(dx, a1, a0));
+  s.c01 = ffma(dx, a2, a1);
   s.c02 = a2;
-  s.c11 = fadd(fadd(b1, fmul(dx, b2)), fmul(kQTY, adx));
+  s.c11 = ffma(kQTY, adx, ffma(dx, b2, b1));
   s.c12 = b2;
-  const float e0 = fadd(s.d00, fmul(dx, s.d01));
-  const float e1 = fadd(s.d01, fmul(dx, s.d11));
-  s.d00 = fadd(e0, fmul(dx, e1));
+  const float e0 = ffma(dx, s.d01, s.d00);
+  const float e1 = ffma(dx, s.d11, s.d01);
+  s.d00 = ffma(dx, e1, e0);
   s.d01 = e1;
-  s.d11 = fadd(s.d11, fmul(kQTT, adx));
-  const float pp = fadd(fmul(s.y, G.z), G.w);
+  s.d11 = ffma(kQTT, adx, s.d11);
+  const float pp = ffma(s.y, G.z, G.w);
   ppad = quant(fmul(pp, 64.0f), 0.0f, kPadHi);
   ptime = quant(fmul(s.t, 32.0f), 0.0f, kTimeHi);
 }
@@ -220,25 +224,25 @@ __device__ __forceinline__ void update(const float4& G, Track& s, uint32_t padq,
   const float inv = frcp(fadd(s.c00, kSY2));
   const float k0 = fmul(s.c00, inv), k1 = fmul(s.c01, inv), k2 = fmul(s.c02, inv);
   const float r = fsub(ym, s.y);
-  s.y = fadd(s.y, fmul(k0, r));
-  s.ty = fadd(s.ty, fmul(k1, r));
-  s.c = fadd(s.c, fmul(k2, r));
+  s.y = ffma(k0, r, s.y);
+  s.ty = ffma(k1, r, s.ty);
+  s.c = ffma(k2, r, s.c);
   const float c00 = s.c00, c01 = s.c01, c02 = s.c02;
-  s.c00 = fsub(c00, fmul(k0, c00));
-  s.c01 = fsub(c01, fmul(k0, c01));
-  s.c02 = fsub(c02, fmul(k0, c02));
-  s.c11 = fsub(s.c11, fmul(k1, c01));
-  s.c12 = fsub(s.c12, fmul(k1, c02));
-  s.c22 = fsub(s.c22, fmul(k2, c02));
+  s.c00 = ffma(-k0, c00, c00);
+  s.c01 = ffma(-k0, c01, c01);
+  s.c02 = ffma(-k0, c02, c02);
+  s.c11 = ffma(-k1, c01, s.c11);
+  s.c12 = ffma(-k1, c02, s.c12);
+  s.c22 = ffma(-k2, c02, s.c22);
   const float invt = frcp(fadd(s.d00, kST2));
   const float g0 = fmul(s.d00, invt), g1 = fmul(s.d01, invt);
   const float rt = fsub(tm, s.t);
-  s.t = fadd(s.t, fmul(g0, rt));
-  s.tt = fadd(s.tt, fmul(g1, rt));
+  s.t = ffma(g0, rt, s.t);
+  s.tt = ffma(g1, rt, s.tt);
   const float d00 = s.d00, d01 = s.d01;
-  s.d00 = fsub(d00, fmul(g0, d00));
-  s.d01 = fsub(d01, fmul(g0, d01));
-  s.d11 = fsub(s.d11, fmul(g1, d01));
+  s.d00 = ffma(-g0, d00, d00);
+  s.d01 = ffma(-g0, d01, d01);
+  s.d11 = ffma(-g1, d01, s.d11);
 }
 
 }  // namespace tmd

@@ -55,17 +55,30 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total)
 // streams have in flight (the pipelined host entry point uploads the next
 // frame's inputs while this one decodes), and the decode would wait for them.
 // The same launch clears the scratch region that must start at zero.
+// With n_status > 0 the chunk holds the n_status frame descriptors at byte
+// offset frames_off, and the launch also clears their status words (the
+// chain's first write to them).
 template <int W>
 __global__ void k_put_record(RecordChunk<W> c, uint32_t n16, uint4* __restrict__ dst,
-                             uint4* __restrict__ zero, uint32_t zero_n16) {
+                             uint4* __restrict__ zero, uint32_t zero_n16, uint32_t frames_off,
+                             uint32_t n_status) {
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = c.w[i];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < zero_n16; i += stride)
     zero[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (blockIdx.x == 0) {
+    const FrameDev* fd =
+        reinterpret_cast<const FrameDev*>(reinterpret_cast<const char*>(c.w) + frames_off);
+    for (uint32_t f = threadIdx.x; f < n_status; f += blockDim.x) *fd[f].status = 0u;
+  }
+}
+
+bool put_record_zeroes_status(size_t frames_off, uint32_t n_frames) {
+  return frames_off + (size_t)n_frames * sizeof(FrameDev) <= sizeof(RecordChunk<kRecordChunkBig>);
 }
 
 cudaError_t put_record(const void* host, size_t bytes, void* dev, void* zero, size_t zero_bytes,
-                       cudaStream_t st) {
+                       cudaStream_t st, size_t frames_off, uint32_t n_status) {
   const char* h = static_cast<const char*>(host);
   char* d = static_cast<char*>(dev);
   uint4* z = static_cast<uint4*>(zero);
@@ -78,17 +91,21 @@ cudaError_t put_record(const void* host, size_t bytes, void* dev, void* zero, si
     const uint32_t work = n16 > zn ? n16 : zn;
     uint32_t grid = (work + 255) / 256;
     grid = grid < 1 ? 1 : (grid > 256 ? 256 : grid);
+    // the first chunk clears the status words if it holds every descriptor
+    const uint32_t ns = (n_status && frames_off + (size_t)n_status * sizeof(FrameDev) <= take)
+                            ? n_status : 0u;
     if (take <= small) {
       RecordChunk<kRecordChunkSmall> c;
       if (take) memcpy(c.w, h, take);
       k_put_record<kRecordChunkSmall><<<grid, 256, 0, st>>>(c, n16, reinterpret_cast<uint4*>(d),
-                                                            z, zn);
+                                                            z, zn, (uint32_t)frames_off, ns);
     } else {
       RecordChunk<kRecordChunkBig> c;
       memcpy(c.w, h, take);
       k_put_record<kRecordChunkBig><<<grid, 256, 0, st>>>(c, n16, reinterpret_cast<uint4*>(d), z,
-                                                          zn);
+                                                          zn, (uint32_t)frames_off, ns);
     }
+    n_status = 0;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     h += take;
@@ -167,6 +184,10 @@ __global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, Pla
     F.unatt_start[kNBin] = (uint32_t)carry;
     if (carry != F.n_unatt) atomicOr(F.status, kStCount);
   }
+  // attached counts per bin: summed into by k_group_sum or k_xcount (an
+  // encoding call has none)
+  if (F.att_count)
+    for (uint32_t b = tid; b < (uint32_t)kNBin; b += 1024) F.att_count[b] = 0u;
 }
 
 // trackStart and decode order.  A block first counts its tracks per length
@@ -215,7 +236,8 @@ __global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, Pla
   }
 }
 
-// Sum of the tile histograms over groups of kGroup tiles, per bin.
+// Sum of the tile histograms over groups of kGroup tiles, per bin; the group
+// sums are also added into the bin's attached count (cleared by k_frame_scan).
 __global__ void __launch_bounds__(kBinBlk) k_group_sum(const FrameDev* frames, PlanDev plan) {
   const uint32_t f = find_frame(plan.pre_grp, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
@@ -226,34 +248,39 @@ __global__ void __launch_bounds__(kBinBlk) k_group_sum(const FrameDev* frames, P
   if (b >= (uint32_t)kNBin) return;
   const uint32_t te = min((g + 1) * kGroup, F.n_tiles);
   uint32_t s = 0;
+#pragma unroll 8
   for (uint32_t tile = g * kGroup; tile < te; tile++) s += F.tile_hist[(size_t)tile * kNBin + b];
   F.group_sum[(size_t)g * kNBin + b] = s;
+  if (s) atomicAdd(&F.att_count[b], s);
 }
 
-// Per frame: attached count per bin (sum over the groups), rowStart.
+// rowStart = exclusive scan of attached + unattached counts per bin, one block
+// of 1024 threads per frame, kBinPerThread consecutive bins per thread.
+constexpr int kBinPerThread = (kNBin + 1023) / 1024;
+__device__ __forceinline__ void row_start_scan(const FrameDev& F) {
+  uint32_t v[kBinPerThread], sum = 0, tot;
+  const uint32_t b0 = threadIdx.x * kBinPerThread;
+#pragma unroll
+  for (int q = 0; q < kBinPerThread; q++) {
+    const uint32_t b = b0 + q;
+    v[q] = b < (uint32_t)kNBin ? F.att_count[b] + F.n_unatt_bin[b] : 0u;
+    sum += v[q];
+  }
+  uint32_t run = block_excl_scan<1024>(sum, tot);
+#pragma unroll
+  for (int q = 0; q < kBinPerThread; q++) {
+    const uint32_t b = b0 + q;
+    if (b < (uint32_t)kNBin) F.row_start[b] = run;
+    run += v[q];
+  }
+  if (threadIdx.x == 0) F.row_start[kNBin] = tot;
+}
+
+// Per frame: rowStart (the attached counts were summed by k_group_sum).
 __global__ void __launch_bounds__(1024) k_row_offsets(const FrameDev* frames, PlanDev plan) {
-  uint32_t tot;
   const FrameDev& F = frames[blockIdx.x];
   if (*F.status & kStCount) return;
-  const uint32_t* __restrict__ gsum = F.group_sum;
-  uint32_t* __restrict__ att_count = F.att_count;
-  const uint32_t ng = F.n_groups;
-  for (uint32_t b = threadIdx.x; b < (uint32_t)kNBin; b += blockDim.x) {
-    uint32_t run = 0;
-#pragma unroll 8
-    for (uint32_t g = 0; g < ng; g++) run += gsum[(size_t)g * kNBin + b];
-    att_count[b] = run;
-  }
-  __syncthreads();
-  uint32_t carry = 0;
-  for (uint32_t base = 0; base < (uint32_t)kNBin; base += 1024) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t v = i < (uint32_t)kNBin ? att_count[i] + F.n_unatt_bin[i] : 0u;
-    const uint32_t e = block_excl_scan<1024>(v, tot);
-    if (i < (uint32_t)kNBin) F.row_start[i] = carry + e;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) F.row_start[kNBin] = carry;
+  row_start_scan(F);
 }
 
 // First native index of every (tile, bin): rowStart plus the counts of the

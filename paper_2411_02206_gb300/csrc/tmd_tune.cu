@@ -27,6 +27,7 @@ const Param kParams[] = {
     {"scatter_variant", &tmd_handle::tune_scatter_variant, 0, 3},
     {"overlap", &tmd_handle::tune_overlap, 0, 1},
     {"place", &tmd_handle::tune_place, 0, 1},
+    {"prekey", &tmd_handle::tune_prekey, 0, 1},
     {"unatt_variant", &tmd_handle::tune_unatt_variant, 0, 1},
     {"decode_blocks_per_sm", &tmd_handle::tune_decode_bps, 0, 64},
     {"unatt_blocks_per_sm", &tmd_handle::tune_unatt_bps, 0, 64},
@@ -121,6 +122,7 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
   };
   const Axis axes[] = {
       {&tmd_handle::tune_place, {0, 1}},
+      {&tmd_handle::tune_prekey, {0, 1}},
       {&tmd_handle::tune_decode_variant, {0, 1, 2, 3}},
       {&tmd_handle::tune_rank_variant, {0, 1, 2}},
       {&tmd_handle::tune_scatter_variant, {0, 1, 2}},  // 3 differs from 1 within noise
@@ -149,12 +151,13 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
     FILE* f = fopen(h->autotune_cache.c_str(), "w");
     if (f) {
       fprintf(f, "{\"%s\": {\"decode_variant\": %d, \"rank_variant\": %d, "
-                 "\"scatter_variant\": %d, \"overlap\": %d, \"place\": %d, "
+                 "\"scatter_variant\": %d, \"overlap\": %d, \"place\": %d, \"prekey\": %d, "
                  "\"unatt_variant\": %d, "
                  "\"decode_blocks_per_sm\": %d, \"unatt_blocks_per_sm\": %d, "
                  "\"chain_ms\": %.4f}}\n",
               device_key(h).c_str(), h->tune_decode_variant, h->tune_rank_variant,
-              h->tune_scatter_variant, h->tune_overlap, h->tune_place, h->tune_unatt_variant,
+              h->tune_scatter_variant, h->tune_overlap, h->tune_place, h->tune_prekey,
+              h->tune_unatt_variant,
               h->tune_decode_bps, h->tune_unatt_bps, best);
       fclose(f);
     }

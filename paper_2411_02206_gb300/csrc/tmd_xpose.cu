@@ -395,15 +395,23 @@ __global__ void __launch_bounds__(1024) k_xrow_offsets(const FrameDev* frames, P
   __shared__ uint32_t s_w[33];
   const FrameDev& F = frames[blockIdx.x];
   if (*F.status & kStCount) return;
-  uint32_t carry = 0, tot;
-  for (uint32_t base = 0; base < (uint32_t)kNBin; base += 1024) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t v = i < (uint32_t)kNBin ? F.att_count[i] + F.n_unatt_bin[i] : 0u;
-    const uint32_t e = xblock_scan<1024>(v, tot, s_w);
-    if (i < (uint32_t)kNBin) F.row_start[i] = carry + e;
-    carry += tot;
+  constexpr int Q = (kNBin + 1023) / 1024;
+  uint32_t v[Q], sum = 0, tot;
+  const uint32_t b0 = threadIdx.x * Q;
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const uint32_t b = b0 + q;
+    v[q] = b < (uint32_t)kNBin ? F.att_count[b] + F.n_unatt_bin[b] : 0u;
+    sum += v[q];
   }
-  if (threadIdx.x == 0) F.row_start[kNBin] = carry;
+  uint32_t run = xblock_scan<1024>(sum, tot, s_w);
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const uint32_t b = b0 + q;
+    if (b < (uint32_t)kNBin) F.row_start[b] = run;
+    run += v[q];
+  }
+  if (threadIdx.x == 0) F.row_start[kNBin] = tot;
 }
 
 // One block per (frame, sector), kXBaseQ threads per row: tile bases of the

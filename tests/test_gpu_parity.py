@@ -185,7 +185,7 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
     dev = frames.to_torch(of, "cuda:0")
     saved = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
                                                "scatter_variant", "overlap",
-                                               "unatt_variant", "place")}
+                                               "unatt_variant", "place", "prekey")}
 
     def check(what):
         native, rs, att, st = dec.decode(dev)
@@ -194,23 +194,26 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
         G.assert_same_decode(gpu, ora, what)
 
     try:
-        for pl in range(2):
-            dec.tmd_tune_set("place", pl)
-            for uv in range(2):
-                dec.tmd_tune_set("unatt_variant", uv)
-                check(f"place {pl} unatt {uv}")
-            for ov in range(2):
-                dec.tmd_tune_set("overlap", ov)
-                for dv in range(4):
-                    dec.tmd_tune_set("decode_variant", dv)
-                    if pl == 1:  # the transpose placement has no ranking/scatter variants
-                        check(f"place 1 overlap {ov} decode {dv}")
-                        continue
-                    for rv in range(3):
-                        for sv in range(4):
-                            dec.tmd_tune_set("rank_variant", rv)
-                            dec.tmd_tune_set("scatter_variant", sv)
-                            check(f"place 0 overlap {ov} decode {dv} rank {rv} scatter {sv}")
+        for pk in range(2):
+            dec.tmd_tune_set("prekey", pk)
+            for pl in range(2):
+                dec.tmd_tune_set("place", pl)
+                for uv in range(2):
+                    dec.tmd_tune_set("unatt_variant", uv)
+                    check(f"prekey {pk} place {pl} unatt {uv}")
+                for ov in range(2):
+                    dec.tmd_tune_set("overlap", ov)
+                    for dv in range(4):
+                        dec.tmd_tune_set("decode_variant", dv)
+                        what = f"prekey {pk} place {pl} overlap {ov} decode {dv}"
+                        if pl == 1:  # the transpose placement has no ranking/scatter variants
+                            check(what)
+                            continue
+                        for rv in range(3):
+                            for sv in range(4):
+                                dec.tmd_tune_set("rank_variant", rv)
+                                dec.tmd_tune_set("scatter_variant", sv)
+                                check(f"{what} rank {rv} scatter {sv}")
     finally:
         for k, v in saved.items():
             dec.tmd_tune_set(k, v)

@@ -12,15 +12,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "tmd_oracle.c")
 
 MUTANTS = {
-    "drop_h2_term_in_c00": ("s->c00 = (a0 + dx * a1) + h2 * a2;", "s->c00 = a0 + dx * a1;"),
+    "drop_h2_term_in_c00": ("s->c00 = fmaf(h2, a2, fmaf(dx, a1, a0));", "s->c00 = fmaf(dx, a1, a0);"),
     "rotation_sign": ("float b = s->ty * ca - sa;", "float b = s->ty * ca + sa;"),
     "rotation_transposed": ("float ny = s->y * ca - s->x * sa;", "float ny = s->x * ca - s->y * sa;"),
-    "drop_process_noise": ("s->c11 = (b1 + dx * b2) + m->qty * adx;", "s->c11 = b1 + dx * b2;"),
+    "drop_process_noise": ("s->c11 = fmaf(m->qty, adx, fmaf(dx, b2, b1));", "s->c11 = fmaf(dx, b2, b1);"),
     "wrong_gain_operand": ("k1 = s->c01 * inv", "k1 = s->c02 * inv"),
-    "no_slope_propagation": ("s->ty = s->ty + s->c * dx;", "s->ty = s->ty;"),
+    "no_slope_propagation": ("s->ty = fmaf(s->c, dx, s->ty);", "s->ty = s->ty;"),
     "missing_half": ("float h = (0.5f * s->c) * dx;", "float h = s->c * dx;"),
-    "cov_update_index": ("s->c12 = s->c12 - k1 * c02;", "s->c12 = s->c12 - k1 * c01;"),
-    "time_cov_gain": ("s->d11 = s->d11 - g1 * d01;", "s->d11 = s->d11 - g0 * d01;"),
+    "cov_update_index": ("s->c12 = fmaf(-k1, c02, s->c12);", "s->c12 = fmaf(-k1, c01, s->c12);"),
+    "time_cov_gain": ("s->d11 = fmaf(-g1, d01, s->d11);", "s->d11 = fmaf(-g0, d01, s->d11);"),
     "rotation_curvature_power": ("s->c = s->c * ((ia * ia) * ia);", "s->c = s->c * (ia * ia);"),
     "no_side_flip": ("if ((s->sec < 18) != (nsec < 18)) {", "if (0) {"),
     "unattached_no_running_sum": ("padq = (padq + f->pad_diff_u[u]) & 0xFFFFu;",
@@ -28,8 +28,8 @@ MUTANTS = {
     "record_sigma_swap": ("dst[6] = sig_time; dst[7] = sig_pad;", "dst[6] = sig_pad; dst[7] = sig_time;"),
     "quant_truncates": ("return (uint32_t)floorf(v + 0.5f);", "return (uint32_t)floorf(v);"),
     "seed_slope_no_curvature": ("s->ty = s->y / s->x + (s->c * s->x) * 0.5f;", "s->ty = s->y / s->x;"),
-    "pad_to_y_inverse_width": ("* 0.015625f - g_halfnp[r]) * g_w[r];",
-                               "* 0.015625f - g_halfnp[r]) * g_invw[r];"),
+    "pad_to_y_inverse_width": ("0.015625f, -g_halfnp[r]) * g_w[r];",
+                               "0.015625f, -g_halfnp[r]) * g_invw[r];"),
     "unattached_sort_pad_first": ("if (T->time_u[a] != T->time_u[b]) return T->time_u[a] < T->time_u[b] ? -1 : 1;",
                                   "if (T->pad_u[a] != T->pad_u[b]) return T->pad_u[a] < T->pad_u[b] ? -1 : 1;"),
     "time_residual_sign": ("o->time_res[d] = T->time[j] - ptime;", "o->time_res[d] = ptime - T->time[j];"),
