@@ -239,13 +239,14 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(2, &h->occ_decode_v[2]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(3, &h->occ_decode_v[3]), "occupancy")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, occupancy_track_decode(4, &h->occ_decode_v[4]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_unatt_decode(&h->occ_unatt), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                   &h->occ_encode, k_track_encode, 256, 0), "occupancy")) != TMD_OK) {
     delete h;
     return rc;
   }
-  for (int v = 0; v < 4; v++)
+  for (int v = 0; v < 5; v++)
     if (h->occ_decode_v[v] < 1) h->occ_decode_v[v] = 1;
   h->occ_decode = h->occ_decode_v[h->tune_decode_variant];
   if (!h->autotune_cache.empty()) tmd_tune_load(h);
@@ -274,7 +275,7 @@ static const char* kKernelNames[kKNum] = {
     "k_put_record", "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_track_decode",
     "k_count_rank", "k_group_sum", "k_row_offsets", "k_tile_base", "k_att_scatter",
     "k_unatt_decode", "k_track_encode", "k_seg_count", "k_seg_scan", "k_seg_runs", "k_xcount",
-    "k_xrow_offsets", "k_xbase", "k_xscatter", "k_track_keys"};
+    "k_xrow_offsets", "k_xbase", "k_xscatter", "k_track_keys", "k_chunk_order"};
 
 cudaEvent_t TmdProfile::get() {
   if (pool.empty()) {
@@ -558,19 +559,20 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   } else {
     const uint32_t n_kt = pre_kt[nf];
     const bool xpose = h->tune_place == 1;
-    const bool prekey = h->tune_prekey == 1;
+    const bool in_decoder = h->tune_place == 2;  // records placed by the decoder
+    const bool prekey = h->tune_prekey == 1 || in_decoder;
     const uint32_t n_sblk = pre_sblk[nf], n_xt = pre_xtile[nf];
     const bool two = aux && fork && join;
     // the phases of the chain, each on a given stream
-    auto decode = [&](bool keys) {  // warp tasks of 32 tracks, taken from counters[0]
+    auto decode = [&](int out) {  // warp tasks of 32 tracks, taken from counters[0]
       if (!n_kt) return;
       const int var = h->tune_decode_variant;
-      int bps = h->occ_decode_v[var];
+      int bps = out == kOutPlace ? h->occ_decode_v[4] : h->occ_decode_v[var];
       if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
       const uint32_t per_block = kDecodeThreads / 32;
       const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
           (uint32_t)(h->sms * bps), (n_kt + per_block - 1) / per_block));
-      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt, keys); });
+      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt, out); });
     };
     auto counts = [&](cudaStream_t s_) {  // per-row counts, row offsets (keys only)
       if (xpose) {
@@ -607,6 +609,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       });
     };
     auto place = [&]() {  // native records of the attached clusters
+      if (in_decoder) return;
       if (xpose) {
         if (n_xt) timed(kKXScatter, [&] { launch_xscatter(n_xt, st, dframes, P); });
       } else if (n_tile) {
@@ -618,23 +621,42 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       // beside the track decoder
       const uint32_t n_kblk = pre_kblk[nf];
       if (n_kblk) timed(kKTrackKeys, [&] { k_track_keys<<<n_kblk, kKeyTracks, 0, st>>>(dframes, P); });
-      cudaStream_t ks = st;
-      if (two) {
-        CK(cudaEventRecord(fork, st));
-        CK(cudaStreamWaitEvent(aux, fork, 0));
-        ks = aux;
+      if (in_decoder) {
+        // the decoder places the records: ranks and tile bases first, and a
+        // decode order that goes tile by tile
+        if (n_tile) timed(kKChunkOrder, [&] { k_chunk_order<<<n_tile, 256, 0, st>>>(dframes, P); });
+        counts(st);
+        bases(st);
+        const bool fork_u = two && n_chunk;
+        if (fork_u) {
+          CK(cudaEventRecord(fork, st));
+          CK(cudaStreamWaitEvent(aux, fork, 0));
+        }
+        unatt(fork_u ? aux : st);
+        decode(kOutPlace);
+        if (fork_u) {
+          CK(cudaEventRecord(join, aux));
+          CK(cudaStreamWaitEvent(st, join, 0));
+        }
+      } else {
+        cudaStream_t ks = st;
+        if (two) {
+          CK(cudaEventRecord(fork, st));
+          CK(cudaStreamWaitEvent(aux, fork, 0));
+          ks = aux;
+        }
+        counts(ks);
+        bases(ks);
+        unatt(ks);
+        decode(kOutNoKey);
+        if (two) {
+          CK(cudaEventRecord(join, aux));
+          CK(cudaStreamWaitEvent(st, join, 0));
+        }
+        place();
       }
-      counts(ks);
-      bases(ks);
-      unatt(ks);
-      decode(false);
-      if (two) {
-        CK(cudaEventRecord(join, aux));
-        CK(cudaStreamWaitEvent(st, join, 0));
-      }
-      place();
     } else {
-      decode(true);
+      decode(kOutAll);
       counts(st);
       // the unattached decode needs only rowStart / attCount: with an aux
       // stream it runs beside the tile bases and the record scatter

@@ -19,7 +19,7 @@ enum TmdKernel {
   kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode, kKCountRank,
   kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode,
   kKSegCount, kKSegScan, kKSegRuns, kKXCount, kKXRowOffsets, kKXBase, kKXScatter, kKTrackKeys,
-  kKNum
+  kKChunkOrder, kKNum
 };
 
 struct TmdProfile {
@@ -45,17 +45,19 @@ struct tmd_handle {
   int device = 0;
   int sms = 0;
   int occ_decode = 1, occ_unatt = 1, occ_encode = 1;
-  int occ_decode_v[4] = {1, 1, 1, 1};  // resident blocks per SM of each decoder variant
+  int occ_decode_v[5] = {1, 1, 1, 1, 1};  // resident blocks per SM: decoder variants 0-3, and
+                                          // the decoder that places records (4)
   // tuning parameters (launch shapes only; results never depend on them)
   int tune_decode_variant = 3;   // staging-round variant of the track decoder
   int tune_rank_variant = 1;     // duplicate-key handling of the ranking kernel
   int tune_scatter_variant = 1;  // store pattern of the record scatter
   int tune_unatt_variant = 1;    // record write-out of the unattached decode
-  int tune_overlap = 0;          // unattached decode on a second stream beside the scatter
-  int tune_place = 0;            // placement: 0 rank + scatter in input order, 1 per-sector transpose
+  int tune_overlap = 1;          // unattached decode on a second stream beside the scatter
+  int tune_place = 0;            // placement: 0 rank + scatter in input order, 1 per-sector
+                                 // transpose, 2 records placed by the track decoder
   int tune_prekey = 0;           // 1: key walk first, key-only work beside the track decoder
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
-  int tune_unatt_bps = 0;        // unattached-decode blocks per SM (0: as many as fit)
+  int tune_unatt_bps = 2;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;
   uint32_t max_slots = 0;
   std::string autotune_cache;

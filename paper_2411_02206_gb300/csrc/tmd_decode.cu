@@ -64,10 +64,12 @@ struct WarpStage {
 
 }  // namespace
 
-template <int R, int MINB, bool KEYS>
+template <int R, int MINB, int OUT>
 __global__ void __launch_bounds__(kDecodeThreads, MINB) k_track_decode(const FrameDev* frames,
                                                                        PlanDev plan,
                                                                        uint32_t n_tasks) {
+  static_assert(OUT != kOutPlace, "record placement runs in the asynchronous variant");
+  constexpr bool KEYS = OUT == kOutAll;
   static_assert(R == 8 || R == 16 || R == 32, "round length divides the warp");
   constexpr int P = R + 1;   // pitch of a staging row
   constexpr int G = 32 / R;  // tracks per staging instruction
@@ -268,9 +270,13 @@ __device__ __forceinline__ RoundBase issue_round(uint32_t* lb, uint32_t k0, uint
 
 }  // namespace
 
-template <int R, int MINB, bool KEYS>
+// OUT: kOutAll writes key, pad code and time code per cluster; kOutNoKey
+// pad and time codes (the keys were written by k_track_keys).
+template <int R, int MINB, int OUT>
 __global__ void __launch_bounds__(kDecodeThreads, MINB)
     k_track_decode_async(const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
+  static_assert(OUT != kOutPlace, "record placement runs in k_track_decode_place");
+  constexpr bool KEYS = OUT == kOutAll;
   static_assert(R == 8 || R == 16, "round length");
   using Lay = AsyncLayout<R>;
   constexpr int P = R + 1;   // pitch of the output rows
@@ -368,6 +374,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
           time_o[ji + k] = bb[i * Lay::kLane + Lay::kTr0 + sq];
         }
       }
+
       __syncwarp();
       cur = nxt;
     }
@@ -376,32 +383,221 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Decoding with record placement interleaved into the model steps.  The
+// decoder is bound by the dependency chain of each model step, the placement
+// of a record by memory latency (its charges, rank and tile base are read from
+// memory, the record is written to a scattered place); interleaving the two
+// lets each hide the other.  Every lane places the records of its own track's
+// previous round, one per model step: the loads for the record are issued
+// before the step's model arithmetic and used after it.  A round's decoded
+// (key | pad, time) stay in the lane's own row of a double buffer until they
+// are placed (also across the warp's tasks; the last round is placed after the
+// last task).  The charge and rank ranges of a round are prefetched into L2
+// while the round is decoded.  Requires a decode order that goes tile by tile
+// (k_chunk_order), so that the records of a tile are written within a short
+// time and the partly written lines of the native list complete in L2.
+namespace {
+template <int R>
+struct PlaceStage {
+  uint32_t buf[2][32 * AsyncLayout<R>::kLane];  // residual staging (as the async decoder)
+  uint2 out[2][32 * (R + 1)];                   // {key | pad << 16, time} per lane and step
+};
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+}  // namespace
+
+template <int R, int MINB>
+__global__ void __launch_bounds__(kDecodeThreads, MINB)
+    k_track_decode_place(const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
+  using Lay = AsyncLayout<R>;
+  constexpr int P = R + 1;
+  __shared__ RowGeo geo_s;
+  __shared__ PlaceStage<R> stage[kDecodeThreads / 32];
+  fill_row_geo(&geo_s);
+  __syncthreads();
+  const RowGeo* geo = &geo_s;
+  const uint32_t lane = threadIdx.x & 31;
+  PlaceStage<R>& S = stage[threadIdx.x >> 5];
+  uint32_t rb = 0;                        // output buffer of the current round
+  uint32_t p_j = 0, p_cnt = 0, p_f = 0;   // pending records: first j, count, frame
+  for (;;) {
+    uint32_t st = 0;  // status bits of this task's frame
+    const uint32_t task = next_task(&plan.counters[0]);
+    const bool have = task < n_tasks;
+    const uint32_t f = have ? find_frame(plan.pre_kt, plan.n_frames, task) : p_f;
+    const FrameDev& F = frames[f];
+    const bool live = have && !(*F.status & kStCount);
+    uint32_t j0 = 0, n = 0, dm1 = 0, pad0 = 0, time0 = 0;
+    Track s;
+    if (live) {
+      const uint32_t idx = (task - plan.pre_kt[f]) * 32u + lane;
+      if (idx < F.n_tracks) {
+        const uint32_t t = F.order[idx];
+        j0 = F.track_start[t];
+        n = F.ncl[t];
+        dm1 = j0 - t - 1u;
+        pad0 = F.pad[t];
+        time0 = F.time[t];
+        const uint32_t raw = F.row[t], sec = F.slice[t];
+        if (raw >= (uint32_t)kNRow || sec >= (uint32_t)kNSec) st |= kStRow;
+        seed(geo, s, F.qpt[t], (int)raw, sec < (uint32_t)kNSec ? (int)sec : kNSec - 1, pad0,
+             time0);
+      }
+    }
+    const uint32_t nmax = __reduce_max_sync(kFull, n);
+    // one round more than the task's rounds when no task is left: it only
+    // places the pending records
+    const uint32_t n_rounds = live ? (nmax + R - 1) / R : (have ? 0u : 1u);
+    const uint8_t* __restrict__ rd_s = F.row_diff;
+    const uint8_t* __restrict__ sld_s = F.sld;
+    const uint16_t* __restrict__ pr_s = F.pad_res;
+    const uint32_t* __restrict__ tr_s = F.time_res;
+    uint32_t* lb0 = S.buf[0] + lane * Lay::kLane;
+    uint32_t* lb1 = S.buf[1] + lane * Lay::kLane;
+    RoundBase cur{0, 0, 0};
+    if (live) {
+      cur = issue_round<R>(lb0, 0u, n, dm1, rd_s, sld_s, pr_s, tr_s);
+      cp_commit();
+    }
+    for (uint32_t r = 0; r < n_rounds; r++) {
+      const uint32_t k0 = r * R;
+      uint32_t* lb = (r & 1) ? lb1 : lb0;
+      RoundBase nxt{0, 0, 0};
+      if (live) {
+        if (r + 1 < n_rounds) {
+          nxt = issue_round<R>((r & 1) ? lb0 : lb1, k0 + R, n, dm1, rd_s, sld_s, pr_s, tr_s);
+          cp_commit();
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+      }
+      const uint32_t rem = n > k0 ? n - k0 : 0u;
+      const uint32_t cnt = rem < (uint32_t)R ? rem : (uint32_t)R;
+      if (cnt) {  // this round's placement data, needed during the next round
+        const uint32_t ja = j0 + k0;
+        prefetch_l2(F.rank + ja);
+        prefetch_l2(F.rank + ja + cnt - 1);
+        prefetch_l2(F.qtot_a + ja);
+        prefetch_l2(F.qtot_a + ja + cnt - 1);
+        prefetch_l2(F.qmax_a + ja);
+        prefetch_l2(F.qmax_a + ja + cnt - 1);
+        prefetch_l2(F.flags_a + ja);
+        prefetch_l2(F.sigp_a + ja);
+        prefetch_l2(F.sigt_a + ja);
+      }
+      // the pending records live in frame p_f
+      const FrameDev& PF = frames[p_f];
+      const uint2* pend = S.out[rb ^ 1u] + lane * P;
+      uint2* outr = S.out[rb] + lane * P;
+#pragma unroll 1
+      for (uint32_t q = 0; q < (uint32_t)R; q++) {
+        // issue the loads of pending record q
+        const bool place = q < p_cnt;
+        uint32_t pj = 0, pk = 0, pt = 0, prk = 0, pb = 0, pfl = 0, pst = 0, psp = 0, pqm = 0, pqt = 0;
+        if (place) {
+          pj = p_j + q;
+          const uint2 o = pend[q];
+          pk = o.x;
+          pt = o.y;
+          pb = __ldg(PF.tile_base + (size_t)(pj / (uint32_t)kTile) * kNBin + (pk & 0xFFFFu));
+          prk = __ldg(PF.rank + pj);
+          pfl = __ldg(PF.flags_a + pj);
+          pst = __ldg(PF.sigt_a + pj);
+          psp = __ldg(PF.sigp_a + pj);
+          pqm = __ldg(PF.qmax_a + pj);
+          pqt = __ldg(PF.qtot_a + pj);
+        }
+        // model step q of this round
+        if (q < rem) {
+          uint32_t padq, timeq;
+          if (k0 + q == 0) {
+            padq = pad0;
+            timeq = time0;
+          } else {
+            const int prd = cur.rd + (int)q, psl = cur.sl + (int)q, ppr = cur.pr + (int)q;
+            const uint32_t rdv = (lb[prd >> 2] >> (8 * (prd & 3))) & 255u;
+            const uint32_t slv = (lb[Lay::kRd + (psl >> 2)] >> (8 * (psl & 3))) & 255u;
+            const uint32_t prv = (lb[2 * Lay::kRd + (ppr >> 1)] >> (16 * (ppr & 1))) & 0xFFFFu;
+            st |= key_step(s, rdv, slv);
+            uint32_t ppad, ptime;
+            const float4 G = geo->row[s.row];
+            propagate_predict(G, s, ppad, ptime);
+            padq = (ppad + prv) & 0xFFFFu;
+            timeq = ptime + lb[Lay::kTr0 + q];
+            update(G, s, padq, timeq);
+          }
+          if (timeq > 0xFFFFFFu) st |= kStTime;
+          outr[q] = make_uint2((uint32_t)(s.sec * kNRow + s.row) | (padq << 16), timeq);
+        }
+        // place pending record q
+        if (place) {
+          const uint32_t p = pb + prk;
+          const uint32_t w0 = (pt & 0xFFFFFFu) | (pfl << 24);
+          const uint32_t w1 = (pk >> 16) | (pst << 16) | (psp << 24);
+          const uint32_t w2 = pqm | (pqt << 16);
+          if (p < PF.n_att + PF.n_unatt) {
+            uint32_t* dst = reinterpret_cast<uint32_t*>(PF.native) + (size_t)p * 3;
+            if ((p & 1u) == 0) {  // record starts on an 8-byte boundary
+              *reinterpret_cast<uint2*>(dst) = make_uint2(w0, w1);
+              dst[2] = w2;
+            } else {
+              dst[0] = w0;
+              *reinterpret_cast<uint2*>(dst + 1) = make_uint2(w1, w2);
+            }
+          } else {
+            atomicOr(PF.status, kStLimit);  // a corrupt frame: the place is outside the list
+          }
+        }
+      }
+      // this round's records become the pending ones
+      p_j = j0 + k0;
+      p_cnt = cnt;
+      p_f = f;
+      rb ^= 1u;
+      cur = nxt;
+    }
+    st = __reduce_or_sync(kFull, st);
+    if (st && lane == 0) atomicOr(F.status, st);
+    if (!have) break;
+  }
+}
+
 // Variants: 0 -> R = 32, 1 -> R = 16 (synchronous staging), 2 -> R = 8,
 // 3 -> R = 16 (asynchronous double-buffered staging).  With keys == false the
 // (sector,row) keys are not written (k_track_keys wrote them before).
-template <bool KEYS>
+template <int OUT>
 static void launch_track_decode_t(int variant, uint32_t grid, cudaStream_t st,
                                   const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
   switch (variant) {
-    case 0: k_track_decode<32, 1, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    case 2: k_track_decode_async<8, 6, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    case 3: k_track_decode_async<16, 4, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
-    default: k_track_decode<16, 1, KEYS><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 0: k_track_decode<32, 1, OUT><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 2: k_track_decode_async<8, 6, OUT><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    case 3: k_track_decode_async<16, 4, OUT><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
+    default: k_track_decode<16, 1, OUT><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks); break;
   }
 }
 
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_tasks, bool keys) {
-  if (keys) launch_track_decode_t<true>(variant, grid, st, frames, plan, n_tasks);
-  else launch_track_decode_t<false>(variant, grid, st, frames, plan, n_tasks);
+                         PlanDev plan, uint32_t n_tasks, int out) {
+  if (out == kOutPlace) {
+    k_track_decode_place<16, 3><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks);
+  } else if (out == kOutNoKey) {
+    launch_track_decode_t<kOutNoKey>(variant, grid, st, frames, plan, n_tasks);
+  } else {
+    launch_track_decode_t<kOutAll>(variant, grid, st, frames, plan, n_tasks);
+  }
 }
 
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm) {
   switch (variant) {
-    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<32, 1, true>, kDecodeThreads, 0);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<8, 6, true>, kDecodeThreads, 0);
-    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<16, 4, true>, kDecodeThreads, 0);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<16, 1, true>, kDecodeThreads, 0);
+    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_place<16, 3>, kDecodeThreads, 0);
+    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<32, 1, kOutAll>, kDecodeThreads, 0);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<8, 6, kOutAll>, kDecodeThreads, 0);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode_async<16, 4, kOutAll>, kDecodeThreads, 0);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_track_decode<16, 1, kOutAll>, kDecodeThreads, 0);
   }
 }
 

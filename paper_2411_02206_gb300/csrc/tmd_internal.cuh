@@ -189,8 +189,15 @@ __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
 // instance computes identical results); host code launches it through these
 // two functions.  Its warps take tasks of 32 tracks (pre_kt of the plan) from
 // counters[0].
+// Decoder outputs: key + pad + time codes, pad + time codes, or the native
+// records of the attached clusters placed directly (ranks and tile bases
+// computed beforehand from k_track_keys' keys).
+constexpr int kOutAll = 0, kOutNoKey = 1, kOutPlace = 2;
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_tasks, bool keys = true);
+                         PlanDev plan, uint32_t n_tasks, int out = kOutAll);
+// Decode order for placement by the decoder: the tracks that start in each
+// ranking tile, longest first, tile after tile (grid: ranking tiles).
+__global__ void k_chunk_order(const FrameDev* frames, PlanDev plan);
 // Key walk of the attached clusters (keys only, integer): one block per
 // kKeyTracks consecutive tracks (pre_kblk), in windows of kKeyWin clusters.
 constexpr int kKeyTracks = 128;

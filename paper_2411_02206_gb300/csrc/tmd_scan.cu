@@ -236,6 +236,53 @@ __global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, Pla
   }
 }
 
+// Decode order in which the decoder can place records itself: tile by tile
+// (ranking tiles of kTile clusters), the tracks that start in the tile, longest
+// first (warps then get tracks of similar length, and all records of a tile
+// are written within a short time, so partly written lines of the native list
+// complete in L2).  One block per tile; tracks of equal length in any order.
+constexpr int kOrderBuckets = 256;
+__global__ void __launch_bounds__(256) k_chunk_order(const FrameDev* frames, PlanDev plan) {
+  __shared__ uint32_t s_cnt[kOrderBuckets];
+  __shared__ uint32_t s_lo, s_hi;
+  uint32_t tot;
+  const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, blockIdx.x);
+  const FrameDev& F = frames[f];
+  if (*F.status & kStCount) return;
+  const uint32_t c = blockIdx.x - plan.pre_tile[f];
+  const uint32_t nt = F.n_tracks;
+  const uint32_t* __restrict__ ts = F.track_start;
+  if (threadIdx.x < 2) {
+    // first track starting at or after J (track_start is non-decreasing)
+    const uint32_t J = (c + threadIdx.x) * (uint32_t)kTile;
+    uint32_t lo = 0, hi = nt;  // answer in [lo, hi]
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (ts[mid] < J) lo = mid + 1; else hi = mid;
+    }
+    if (threadIdx.x == 0) s_lo = lo; else s_hi = lo;
+  }
+  for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0u;
+  __syncthreads();
+  const uint32_t t_lo = s_lo, t_hi = s_hi;
+  // bucket kOrderBuckets - 1 - min(length, 255): longest first
+  for (uint32_t t = t_lo + threadIdx.x; t < t_hi; t += blockDim.x) {
+    const uint32_t n = F.ncl[t];
+    atomicAdd(&s_cnt[kOrderBuckets - 1 - (n < kOrderBuckets - 1 ? n : kOrderBuckets - 1)], 1u);
+  }
+  __syncthreads();
+  const uint32_t v = s_cnt[threadIdx.x];
+  const uint32_t e = block_excl_scan<256>(v, tot);
+  s_cnt[threadIdx.x] = e;
+  __syncthreads();
+  uint32_t* __restrict__ order = F.order;
+  for (uint32_t t = t_lo + threadIdx.x; t < t_hi; t += blockDim.x) {
+    const uint32_t n = F.ncl[t];
+    const uint32_t b = kOrderBuckets - 1 - (n < kOrderBuckets - 1 ? n : kOrderBuckets - 1);
+    order[t_lo + atomicAdd(&s_cnt[b], 1u)] = t;
+  }
+}
+
 // Sum of the tile histograms over groups of kGroup tiles, per bin; the group
 // sums are also added into the bin's attached count (cleared by k_frame_scan).
 __global__ void __launch_bounds__(kBinBlk) k_group_sum(const FrameDev* frames, PlanDev plan) {

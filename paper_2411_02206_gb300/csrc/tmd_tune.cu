@@ -26,7 +26,7 @@ const Param kParams[] = {
     {"rank_variant", &tmd_handle::tune_rank_variant, 0, 2},
     {"scatter_variant", &tmd_handle::tune_scatter_variant, 0, 3},
     {"overlap", &tmd_handle::tune_overlap, 0, 1},
-    {"place", &tmd_handle::tune_place, 0, 1},
+    {"place", &tmd_handle::tune_place, 0, 2},
     {"prekey", &tmd_handle::tune_prekey, 0, 1},
     {"unatt_variant", &tmd_handle::tune_unatt_variant, 0, 1},
     {"decode_blocks_per_sm", &tmd_handle::tune_decode_bps, 0, 64},
@@ -121,7 +121,7 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
     std::vector<int> values;
   };
   const Axis axes[] = {
-      {&tmd_handle::tune_place, {0, 1}},
+      {&tmd_handle::tune_place, {0, 1, 2}},
       {&tmd_handle::tune_prekey, {0, 1}},
       {&tmd_handle::tune_decode_variant, {0, 1, 2, 3}},
       {&tmd_handle::tune_rank_variant, {0, 1, 2}},

@@ -59,8 +59,8 @@ __global__ void k_selftest_wait(const unsigned long long* never, uint32_t* statu
 }
 
 // Largest b in [lo, hi] with start[b] <= e (start[lo] <= e is known).
-__device__ __forceinline__ uint32_t bin_search(const uint32_t* __restrict__ start, uint32_t lo,
-                                               uint32_t hi, uint32_t e) {
+__device__ __forceinline__ uint32_t bin_search(const uint32_t* start, uint32_t lo, uint32_t hi,
+                                               uint32_t e) {
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;
     if (start[mid] <= e) lo = mid; else hi = mid - 1;
@@ -91,10 +91,14 @@ __global__ void __launch_bounds__(256, 4) k_unatt_decode(const FrameDev* frames,
   __shared__ Seg s_warp[8];
   __shared__ Seg s_carry;
   __shared__ __align__(16) uint32_t s_stage[kStageWords];
+  // the frame's unattached bin starts: every chunk searches them for the bins
+  // of its clusters (loaded when a block's chunk comes from another frame)
+  __shared__ uint32_t s_ustart[kNBin + 1];
   uint32_t* const s_rec = s_stage;                                  // variant 0
   uint32_t* const s_pos = s_stage + kRecWords + kRecWords / 32;     // variant 0
   uint4* const s_rec4 = reinterpret_cast<uint4*>(s_stage);          // variant 1
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t cached_f = 0xFFFFFFFFu;
   for (;;) {
     if (tid == 0) s_ticket = atomicAdd(&plan.counters[1], 1u);
     __syncthreads();
@@ -106,9 +110,14 @@ __global__ void __launch_bounds__(256, 4) k_unatt_decode(const FrameDev* frames,
       __syncthreads();
       continue;
     }
+    if (f != cached_f) {  // the same for every thread of the block
+      for (uint32_t i = tid; i <= (uint32_t)kNBin; i += blockDim.x) s_ustart[i] = F.unatt_start[i];
+      cached_f = f;
+      __syncthreads();
+    }
     const uint32_t c = ticket - plan.pre_chunk[f];
     const uint32_t n = F.n_unatt;
-    const uint32_t* __restrict__ ustart = F.unatt_start;
+    const uint32_t* ustart = s_ustart;
     const uint32_t c0 = c * (uint32_t)kChunk;
     const uint32_t e0 = c0 + tid * 8u;
     // the bins of the chunk's first and last cluster bound every search below

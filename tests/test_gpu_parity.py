@@ -196,7 +196,7 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
     try:
         for pk in range(2):
             dec.tmd_tune_set("prekey", pk)
-            for pl in range(2):
+            for pl in range(3):
                 dec.tmd_tune_set("place", pl)
                 for uv in range(2):
                     dec.tmd_tune_set("unatt_variant", uv)
@@ -206,7 +206,7 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
                     for dv in range(4):
                         dec.tmd_tune_set("decode_variant", dv)
                         what = f"prekey {pk} place {pl} overlap {ov} decode {dv}"
-                        if pl == 1:  # the transpose placement has no ranking/scatter variants
+                        if pl != 0:  # only the input-order scatter has ranking/scatter variants
                             check(what)
                             continue
                         for rv in range(3):
@@ -237,7 +237,7 @@ def test_unaligned_caller_arrays(dec):
         buf[1:] = t
         shifted[k] = buf[1:]
     place = dec.tmd_tune_get("place")
-    for pl, sv in ((0, 0), (0, 1), (0, 2), (0, 3), (1, 1)):
+    for pl, sv in ((0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (2, 1)):
         dec.tmd_tune_set("place", pl)
         dec.tmd_tune_set("scatter_variant", sv)
         for dv in range(4):
