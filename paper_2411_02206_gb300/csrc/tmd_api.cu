@@ -639,17 +639,18 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
           CK(cudaStreamWaitEvent(st, join, 0));
         }
       } else {
-        cudaStream_t ks = st;
-        if (two) {
+        // counts and bases first; the unattached decode runs beside the
+        // track decoder (memory-bound beside latency-bound)
+        counts(st);
+        bases(st);
+        const bool fork_u = two && n_chunk;
+        if (fork_u) {
           CK(cudaEventRecord(fork, st));
           CK(cudaStreamWaitEvent(aux, fork, 0));
-          ks = aux;
         }
-        counts(ks);
-        bases(ks);
-        unatt(ks);
+        unatt(fork_u ? aux : st);
         decode(kOutNoKey);
-        if (two) {
+        if (fork_u) {
           CK(cudaEventRecord(join, aux));
           CK(cudaStreamWaitEvent(st, join, 0));
         }

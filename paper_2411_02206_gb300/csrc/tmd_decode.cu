@@ -480,11 +480,11 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
       if (cnt) {  // this round's placement data, needed during the next round
         const uint32_t ja = j0 + k0;
         prefetch_l2(F.rank + ja);
-        prefetch_l2(F.rank + ja + cnt - 1);
+        prefetch_l2(F.rank + (ja + cnt - 1));
         prefetch_l2(F.qtot_a + ja);
-        prefetch_l2(F.qtot_a + ja + cnt - 1);
+        prefetch_l2(F.qtot_a + (ja + cnt - 1));
         prefetch_l2(F.qmax_a + ja);
-        prefetch_l2(F.qmax_a + ja + cnt - 1);
+        prefetch_l2(F.qmax_a + (ja + cnt - 1));
         prefetch_l2(F.flags_a + ja);
         prefetch_l2(F.sigp_a + ja);
         prefetch_l2(F.sigt_a + ja);

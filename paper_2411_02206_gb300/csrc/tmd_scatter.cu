@@ -229,15 +229,15 @@ __global__ void __cluster_dims__(kScatCta, 1, 1) __launch_bounds__(kScatThreads2
   const uint32_t* __restrict__ tbase = F.tile_base + (size_t)tile * kNBin;
   uint32_t* __restrict__ nat = reinterpret_cast<uint32_t*>(F.native);
   uint32_t st = 0;
-  for (uint32_t l = tid; l < n_own; l += kScatThreads2) {
+  // word by word: consecutive threads write consecutive words of the sorted
+  // records, contiguous in the native list along each (tile, bin) run
+  for (uint32_t w = tid; w < 3 * n_own; w += kScatThreads2) {
+    const uint32_t l = w / 3, c = w - 3 * l;
     const uint4 r = s_buf[l];
     const uint32_t b = r.w & 0xFFFFu;
     const uint32_t d = __ldg(tbase + b) + (lo + l - s_lbase[b]);
     if (d < n_total) {
-      uint32_t* p = nat + (size_t)d * 3;
-      p[0] = r.x;
-      p[1] = r.y;
-      p[2] = r.z;
+      nat[(size_t)d * 3 + c] = c == 0 ? r.x : (c == 1 ? r.y : r.z);
     } else {
       st = kStLimit;
     }
