@@ -172,13 +172,23 @@ __global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, Pla
     const uint32_t e = block_excl_scan<1024>(v, tot);
     F.len_cursor[b] = e;
   }
-  carry = 0;
-  for (uint32_t base = 0; base < (uint32_t)kNBin; base += 1024) {
-    const uint32_t i = base + tid;
-    const uint32_t v = i < (uint32_t)kNBin ? F.n_unatt_bin[i] : 0u;
-    const uint32_t e = block_excl_scan<1024>(v, tot);
-    if (i < (uint32_t)kNBin) F.unatt_start[i] = (uint32_t)carry + e;
-    carry += tot;
+  {
+    // unattached bin starts: kBinPerThread consecutive bins per thread, one scan
+    constexpr int Q = (kNBin + 1023) / 1024;
+    uint32_t v[Q], sum = 0;
+    const uint32_t b0 = tid * Q;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      v[q] = b0 + q < (uint32_t)kNBin ? F.n_unatt_bin[b0 + q] : 0u;
+      sum += v[q];
+    }
+    uint32_t run = block_excl_scan<1024>(sum, tot);
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (b0 + q < (uint32_t)kNBin) F.unatt_start[b0 + q] = run;
+      run += v[q];
+    }
+    carry = tot;
   }
   if (tid == 0) {
     F.unatt_start[kNBin] = (uint32_t)carry;
