@@ -57,7 +57,7 @@ struct tmd_handle {
                                  // transpose, 2 records placed by the track decoder
   int tune_prekey = 0;           // 1: key walk first, key-only work beside the track decoder
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
-  int tune_unatt_bps = 2;        // unattached-decode blocks per SM (0: as many as fit)
+  int tune_unatt_bps = 1;        // unattached-decode blocks per SM (0: as many as fit)
   uint64_t mem_budget = 0;
   uint32_t max_slots = 0;
   std::string autotune_cache;

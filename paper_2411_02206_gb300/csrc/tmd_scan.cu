@@ -303,10 +303,12 @@ __global__ void __launch_bounds__(kBinBlk) k_group_sum(const FrameDev* frames, P
   const uint32_t g = lb / kBinBlocks;
   const uint32_t b = (lb % kBinBlocks) * kBinBlk + threadIdx.x;
   if (b >= (uint32_t)kNBin) return;
-  const uint32_t te = min((g + 1) * kGroup, F.n_tiles);
+  const uint32_t t0 = g * kGroup, nt = min((uint32_t)kGroup, F.n_tiles - t0);
+  const uint16_t* __restrict__ hist = F.tile_hist + (size_t)t0 * kNBin + b;
   uint32_t s = 0;
-#pragma unroll 8
-  for (uint32_t tile = g * kGroup; tile < te; tile++) s += F.tile_hist[(size_t)tile * kNBin + b];
+#pragma unroll
+  for (uint32_t k = 0; k < (uint32_t)kGroup; k++)  // all loads in flight at once
+    s += k < nt ? (uint32_t)hist[(size_t)k * kNBin] : 0u;
   F.group_sum[(size_t)g * kNBin + b] = s;
   if (s) atomicAdd(&F.att_count[b], s);
 }
@@ -351,15 +353,20 @@ __global__ void __launch_bounds__(kBinBlk) k_tile_base(const FrameDev* frames, P
   const uint32_t b = (lb % kBinBlocks) * kBinBlk + threadIdx.x;
   if (b >= (uint32_t)kNBin) return;
   const uint32_t* __restrict__ gsum = F.group_sum;
-  const uint16_t* __restrict__ hist = F.tile_hist;
   uint32_t* __restrict__ tbase = F.tile_base;
-  const uint32_t te = min((g + 1) * kGroup, F.n_tiles);
+  const uint32_t t0 = g * kGroup, nt = min((uint32_t)kGroup, F.n_tiles - t0);
+  const uint16_t* __restrict__ hist = F.tile_hist + (size_t)t0 * kNBin + b;
+  // the group's tile counts first (all loads in flight), then the bases
+  uint32_t c[kGroup];
+#pragma unroll
+  for (uint32_t k = 0; k < (uint32_t)kGroup; k++) c[k] = k < nt ? (uint32_t)hist[(size_t)k * kNBin] : 0u;
   uint32_t run = F.row_start[b];
 #pragma unroll 8
   for (uint32_t gg = 0; gg < g; gg++) run += gsum[(size_t)gg * kNBin + b];
-  for (uint32_t tile = g * kGroup; tile < te; tile++) {
-    tbase[(size_t)tile * kNBin + b] = run;
-    run += hist[(size_t)tile * kNBin + b];
+#pragma unroll
+  for (uint32_t k = 0; k < (uint32_t)kGroup; k++) {
+    if (k < nt) tbase[(size_t)(t0 + k) * kNBin + b] = run;
+    run += c[k];
   }
 }
 

@@ -128,7 +128,7 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
       {&tmd_handle::tune_scatter_variant, {0, 1, 2}},  // 3 differs from 1 within noise
       {&tmd_handle::tune_overlap, {0, 1}},
       {&tmd_handle::tune_unatt_variant, {0, 1}},
-      {&tmd_handle::tune_unatt_bps, {0, 2, 3, 4}},
+      {&tmd_handle::tune_unatt_bps, {0, 1, 2, 3, 4}},
   };
   h->tune_decode_bps = 0;
   float best = 1e30f;
