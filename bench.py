@@ -367,6 +367,20 @@ def run(args):
     dk_bytes = kernel_bytes(dk_name, nt, na, nu)
     achieved = dk_bytes / (dk_ms / dk_n * 1e-3) / 1e9 if (dk_n and dk_bytes) else None
     traffic = dram_traffic(dk_name, tuned, nt, na, nu)
+    # the global-position transform of the decoded list (a row beyond the
+    # decode chain, timed on its own: 12 B read and 12 B written per cluster)
+    xyz = [torch.empty(na + nu, dtype=torch.float32, device=native.device) for _ in range(3)]
+    for _ in range(3):
+        dec.tmd_global_xyz(native, row_start, na + nu, *xyz, stream=stream)
+    reps = max(5, min(args.steps, 50))
+    barrier()
+    start.record(stream)
+    for _ in range(reps):
+        dec.tmd_global_xyz(native, row_start, na + nu, *xyz, stream=stream)
+    stop.record(stream)
+    barrier()
+    xyz_ms = start.elapsed_time(stop) / reps
+    xyz_gbs = 24.0 * (na + nu) / (xyz_ms * 1e-3) / 1e9
     # end to end through the host-buffer entry point
     host = frames.to_torch({k: truth[k] for k in truth if k not in ("sector", "leg")}, None,
                            pin=True)
@@ -386,7 +400,7 @@ def run(args):
     # end to end: the pipelined host entry point over e2e_steps frames (every
     # step copies its inputs up and its native list back; the copies of one
     # step overlap the decode of its neighbours, Sec. 3 / Fig. 3)
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(3, min(args.steps, 64))
     dec.tmd_decode_host_stream([hin] * 2, [hout] * 2, stream)
     barrier()
     t0 = time.perf_counter()
@@ -416,6 +430,10 @@ def run(args):
                               "peak": peak, "unit": "GB/s",
                               "frac": path_bytes(nt, na, nu) / (ms_step * 1e-3) / 1e9 / peak},
             "kernels": {k: _kernel_entry(k, v, prof, nt, na, nu, peak) for k, v in prof.items()},
+            "global_xyz": {"kernel": "k_global_xyz", "ms_per_launch": xyz_ms,
+                           "clusters_per_s": (na + nu) / (xyz_ms * 1e-3),
+                           "algorithmic_bytes": 24 * (na + nu), "gbs": xyz_gbs,
+                           "frac_hbm": xyz_gbs / peak, "in_step": False},
             "top_kernel": top[0],
             "tuning": tuned,
             "cpu_baseline": base,

@@ -302,6 +302,27 @@ int tmd_tune_get(tmd_handle* h, const char* key, int* value);
 int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in, const tmd_frame_out* out,
                  void* stream);
 
+/* Global (x, y, z) positions of the clusters of a native list, for the
+ * reconstruction downstream of the decoder (arXiv:2411.02206, Sec. 1-2: the
+ * decoded TPC clusters feed the tracking of the asynchronous chain).  The
+ * transform uses the nominal geometry of the synthetic TPC, not calibration
+ * maps: a record of bin (s, r) with pad code P and time code T lies at
+ *   x = 85 + r cm, y = (P / 64 - nPads(r) / 2) * w(r), w(r) = 2 x tan(10 deg) / nPads(r),
+ *   psi = (s mod 18) * 20 deg + 10 deg,
+ *   X = x cos(psi) - y sin(psi), Y = x sin(psi) + y cos(psi),
+ *   |Z| = 250 - 0.5 * T / 32 cm, Z > 0 for sectors 0-17 and < 0 for 18-35,
+ * in binary32 (the pad term as one fused multiply-add, everything else
+ * rounded in the order written).
+ *   native:    device, n records of TMD_REC_BYTES bytes (tmd_frame_out.native)
+ *   row_start: device, TMD_NBIN + 1 entries; record i belongs to the last bin b
+ *              with row_start[b] <= i
+ *   x, y, z:   device, n floats each (caller-allocated outputs)
+ * All arrays 4-byte aligned (16-byte alignment takes the vector path).
+ * Asynchronous on `stream`.  Errors: TMD_ERR_ARG (null or misaligned array),
+ * TMD_ERR_CUDA (launch failure). */
+int tmd_global_xyz(tmd_handle* h, const uint8_t* native, const uint32_t* row_start, uint32_t n,
+                   float* x, float* y, float* z, void* stream);
+
 /* Instrumentation.  While enabled, every kernel the handle launches is
  * bracketed by CUDA events on its stream.  tmd_profile_read waits for the
  * recorded launches, returns per kernel its name (32-byte slots in

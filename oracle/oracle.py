@@ -208,6 +208,26 @@ def geometry() -> dict:
     return {"x": x, "w": w, "invw": iw, "npads": npd, "cos": cs, "sin": sn}
 
 
+def sector_centres():
+    """(cos, sin) of the sector-centre azimuths (20 k + 10) deg, binary32."""
+    cs = np.zeros(18, np.float32)
+    sn = np.zeros(18, np.float32)
+    lib().tmd_oracle_sector_centres(_P(_ptr(cs)), _P(_ptr(sn)))
+    return cs, sn
+
+
+def global_xyz(native: np.ndarray, row_start: np.ndarray):
+    """Global (x, y, z) float32 arrays of a native list (records grouped by
+    bin, row_start of 5473 entries), with the nominal synthetic geometry."""
+    native = np.ascontiguousarray(native, dtype=np.uint8).reshape(-1, REC_BYTES)
+    rs = np.ascontiguousarray(row_start, dtype=np.uint32)
+    n = len(native)
+    out = [np.zeros(n, np.float32) for _ in range(3)]
+    lib().tmd_oracle_global_xyz(_P(_ptr(native)), _P(_ptr(rs)), ctypes.c_uint32(n),
+                                *[_P(_ptr(a)) for a in out])
+    return tuple(out)
+
+
 def default_model() -> np.ndarray:
     m = np.zeros(9, np.float32)
     lib().tmd_oracle_default_model(_P(_ptr(m)))

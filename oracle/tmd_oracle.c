@@ -55,18 +55,19 @@ static float g_invw[O_NROW];   /* 1 / pad width */
 static float g_halfnp[O_NROW]; /* nPads / 2 */
 static int g_np[O_NROW];
 static float g_cos[18], g_sin[18]; /* cos, sin of k * 20 deg */
+static float g_ccen[18], g_scen[18]; /* cos, sin of the sector centres (20 k + 10) deg */
 static int g_geo_ready = 0;
 
-/* exact sin/cos of an integer number of degrees (multiple of 20) by reduction
- * to a reference angle in [0, 90), so that 0 and 180 deg give exact zeros */
+/* exact sin/cos of an integer number of degrees by reduction to a reference
+ * angle in [0, 90], so that multiples of 90 deg give exact zeros and ones */
 static void o_sincos_deg(int a, double* s, double* c) {
   int q = ((a % 360) + 360) % 360;
   double ss = 1.0, sc = 1.0;
   if (q > 180) { q = 360 - q; ss = -1.0; }
   if (q > 90) { q = 180 - q; sc = -1.0; }
   double r = (double)q * (3.14159265358979323846 / 180.0);
-  *s = ss * (q == 0 ? 0.0 : sin(r));
-  *c = sc * (q == 0 ? 1.0 : cos(r));
+  *s = ss * (q == 0 ? 0.0 : (q == 90 ? 1.0 : sin(r)));
+  *c = sc * (q == 0 ? 1.0 : (q == 90 ? 0.0 : cos(r)));
 }
 
 static void o_geo_init(void) {
@@ -87,6 +88,9 @@ static void o_geo_init(void) {
     o_sincos_deg(20 * k, &s, &c);
     g_cos[k] = (float)c;
     g_sin[k] = (float)s;
+    o_sincos_deg(20 * k + 10, &s, &c);
+    g_ccen[k] = (float)c;
+    g_scen[k] = (float)s;
   }
   g_geo_ready = 1;
 }
@@ -638,6 +642,44 @@ void tmd_oracle_geometry(float* x, float* w, float* invw, int32_t* np, float* cs
   o_geo_init();
   for (int r = 0; r < O_NROW; r++) { x[r] = g_x[r]; w[r] = g_w[r]; invw[r] = g_invw[r]; np[r] = g_np[r]; }
   for (int k = 0; k < 18; k++) { cs[k] = g_cos[k]; sn[k] = g_sin[k]; }
+}
+
+/* Sector-centre tables: cos, sin of (20 k + 10) deg, k = 0..17. */
+void tmd_oracle_sector_centres(float* cs, float* sn) {
+  o_geo_init();
+  for (int k = 0; k < 18; k++) { cs[k] = g_ccen[k]; sn[k] = g_scen[k]; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Global positions of the clusters of a native list, with the nominal     */
+/* geometry of the synthetic TPC (the decoded clusters feed the tracking of */
+/* the asynchronous chain, Sec. 1-2; real calibration maps are not          */
+/* available).  Record i of bin (s, r) (row_start[b] <= i < row_start[b+1]) */
+/* with pad code P and time code T:                                         */
+/*   local  x = 85 + r, y = (P/64 - nPads(r)/2) * w(r)  (the model's pad_to_y) */
+/*   global X = x cos(psi) - y sin(psi), Y = x sin(psi) + y cos(psi),       */
+/*          psi = (s mod 18) * 20 + 10 deg (the sector centre)              */
+/*   drift  |Z| = 250 - 0.5 * (T / 32), positive for sectors 0-17.          */
+/* binary32, in the order written (the pad term is one fmaf).               */
+/* ------------------------------------------------------------------------ */
+void tmd_oracle_global_xyz(const uint8_t* native, const uint32_t* row_start, uint32_t n,
+                           float* gx, float* gy, float* gz) {
+  o_geo_init();
+  for (int b = 0; b < O_NBIN; b++) {
+    const int s = b / O_NROW, r = b % O_NROW;
+    const float ca = g_ccen[s % 18], sa = g_scen[s % 18];
+    for (uint32_t i = row_start[b]; i < row_start[b + 1] && i < n; i++) {
+      const uint8_t* rec = native + (size_t)i * 12;
+      const uint32_t tcode = (uint32_t)rec[0] | ((uint32_t)rec[1] << 8) | ((uint32_t)rec[2] << 16);
+      const uint32_t pcode = (uint32_t)rec[4] | ((uint32_t)rec[5] << 8);
+      const float yl = o_pad_to_y(pcode, r);
+      const float t = (float)tcode * 0.03125f;
+      const float zabs = 250.0f - t * 0.5f;
+      gx[i] = g_x[r] * ca - yl * sa;
+      gy[i] = g_x[r] * sa + yl * ca;
+      gz[i] = s < 18 ? zabs : -zabs;
+    }
+  }
 }
 
 /* Default model parameters (9 floats, OModel order). */

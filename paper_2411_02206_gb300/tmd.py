@@ -132,6 +132,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_uint32),
                                            ctypes.POINTER(ctypes.c_uint32)]
             L.tmd_profile_read.restype = ctypes.c_int
+            L.tmd_global_xyz.argtypes = [H, _P, _P, ctypes.c_uint32, _P, _P, _P, _P]
+            L.tmd_global_xyz.restype = ctypes.c_int
             L.tmd_last_error_string.argtypes = [H]
             L.tmd_last_error_string.restype = ctypes.c_char_p
             _lib = L
@@ -224,6 +226,20 @@ class Decoder:
         ins = (tmd_frame_in * n)(*fins)
         outs = (tmd_frame_out * n)(*fouts)
         return self._check(self._L.tmd_decode_batch(self.h, n, ins, outs, _P(_stream_ptr(stream))))
+
+    def tmd_global_xyz(self, native, row_start, n: int, x, y, z, stream=None) -> int:
+        """Global positions of a native list (device tensors; x, y, z float32[n])."""
+        return self._check(self._L.tmd_global_xyz(
+            self.h, _P(native.data_ptr()), _P(row_start.data_ptr()), n, _P(x.data_ptr()),
+            _P(y.data_ptr()), _P(z.data_ptr()), _P(_stream_ptr(stream))))
+
+    def global_xyz(self, native, row_start, stream=None):
+        """Allocate and fill float32 x, y, z tensors for a decoded native list."""
+        import torch
+        n = int(native.shape[0])
+        out = [torch.empty(n, dtype=torch.float32, device=native.device) for _ in range(3)]
+        self.tmd_global_xyz(native, row_start, n, *out, stream=stream)
+        return tuple(out)
 
     def tmd_decode_frame_host(self, fin: tmd_frame_in, fout: tmd_frame_out, stream=None) -> int:
         return self._check(self._L.tmd_decode_frame_host(

@@ -35,6 +35,11 @@ MUTANTS = {
     "time_residual_sign": ("o->time_res[d] = T->time[j] - ptime;", "o->time_res[d] = ptime - T->time[j];"),
     "row_key_mod": ("sec = (sec + f->slice_leg_diff[d] % O_NSEC) % O_NSEC;",
                     "sec = (sec + f->slice_leg_diff[d] / O_NSEC) % O_NSEC;"),
+    "xyz_rotation_sign": ("gx[i] = g_x[r] * ca - yl * sa;", "gx[i] = g_x[r] * ca + yl * sa;"),
+    "xyz_sector_edge_not_centre": ("const float ca = g_ccen[s % 18], sa = g_scen[s % 18];",
+                                   "const float ca = g_cos[s % 18], sa = g_sin[s % 18];"),
+    "xyz_drift_speed": ("const float zabs = 250.0f - t * 0.5f;", "const float zabs = 250.0f - t;"),
+    "xyz_side_sign": ("gz[i] = s < 18 ? zabs : -zabs;", "gz[i] = zabs;"),
 }
 
 
@@ -51,6 +56,7 @@ def test_pins_catch_mutant(name, tmp_path):
                            "-shared", "-fPIC", "-o", str(so), str(mut), "-lm"])
     env = dict(os.environ, TMD_ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_xyz.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
