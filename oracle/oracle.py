@@ -235,3 +235,69 @@ def default_model() -> np.ndarray:
 
 
 MODEL_KEYS = ("sy2", "st2", "qty", "qtt", "cty0", "cc0", "ctt0", "syr", "kc")
+
+
+# --- entropy coding (rANS) of a compressed frame -----------------------------
+RANS_M = 4096          # probability scale 2^12
+RANS_LANE_VALUES = 256  # values per lane per chunk
+RANS_CHUNK = 32 * RANS_LANE_VALUES
+RANS_HEAD = 32 + 32 * len(FRAME_FIELDS)
+RANS_CORRUPT = -4
+
+
+def rans_field_encode(values: np.ndarray) -> np.ndarray:
+    """Code one stream (uint8/16/32 values) as a field section (uint8 array)."""
+    v = np.ascontiguousarray(values)
+    if v.dtype not in (np.uint8, np.uint16, np.uint32):
+        raise TypeError(f"dtype {v.dtype}")
+    n, w = v.size, v.dtype.itemsize
+    L = lib()
+    L.tmd_oracle_rans_field_bound.restype = ctypes.c_uint64
+    cap = int(L.tmd_oracle_rans_field_bound(ctypes.c_uint32(n), ctypes.c_uint32(w)))
+    out = np.zeros(cap, np.uint8)
+    size = ctypes.c_uint64(0)
+    rc = L.tmd_oracle_rans_field_encode(_P(_ptr(v)), ctypes.c_uint32(n), ctypes.c_uint32(w),
+                                        _P(_ptr(out)), ctypes.c_uint64(cap), ctypes.byref(size))
+    if rc != 0:
+        raise RuntimeError(f"oracle rans_field_encode: {rc}")
+    return out[:size.value].copy()
+
+
+def rans_field_decode(section: np.ndarray, n: int, dtype):
+    """Decode a field section into n values of dtype; returns (values, ok)."""
+    sec = np.ascontiguousarray(section, np.uint8)
+    out = np.zeros(n, dtype)
+    rc = lib().tmd_oracle_rans_field_decode(_P(_ptr(sec)), ctypes.c_uint64(sec.size),
+                                            ctypes.c_uint32(n),
+                                            ctypes.c_uint32(np.dtype(dtype).itemsize),
+                                            _P(_ptr(out)))
+    return out, rc == 0
+
+
+def rans_encode(frame: dict) -> np.ndarray:
+    """Entropy-code a compressed frame (its 23 streams) into one coded frame."""
+    nt, na, nu = frame_counts(frame)
+    arrs = _check_fields(frame, FRAME_FIELDS, _lengths(nt, na, nu))
+    f = _Frame(nt, na, nu, *[_ptr(arrs[n]) for n, _, _ in FRAME_FIELDS])
+    L = lib()
+    L.tmd_oracle_rans_frame_bound.restype = ctypes.c_uint64
+    cap = int(L.tmd_oracle_rans_frame_bound(ctypes.byref(f)))
+    out = np.zeros(cap, np.uint8)
+    size = ctypes.c_uint64(0)
+    rc = L.tmd_oracle_rans_frame_encode(ctypes.byref(f), _P(_ptr(out)), ctypes.c_uint64(cap),
+                                        ctypes.byref(size))
+    if rc != 0:
+        raise RuntimeError(f"oracle rans_encode: {rc}")
+    return out[:size.value].copy()
+
+
+def rans_decode(blob: np.ndarray, n_tracks: int, n_attached: int, n_unattached: int):
+    """Decode a coded frame with the given counts; returns (frame dict, ok)."""
+    b = np.ascontiguousarray(blob, np.uint8)
+    lens = _lengths(n_tracks, n_attached, n_unattached)
+    out = {n: np.zeros(max(lens[k], 0), dt) for n, dt, k in FRAME_FIELDS}
+    f = _Frame(n_tracks, n_attached, n_unattached, *([0] * len(FRAME_FIELDS)))
+    o = _FrameOut(*[_ptr(out[n]) for n, _, _ in FRAME_FIELDS])
+    rc = lib().tmd_oracle_rans_frame_decode(_P(_ptr(b)), ctypes.c_uint64(b.size),
+                                            ctypes.byref(f), ctypes.byref(o))
+    return out, rc == 0

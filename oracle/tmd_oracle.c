@@ -684,3 +684,354 @@ void tmd_oracle_global_xyz(const uint8_t* native, const uint32_t* row_start, uin
 
 /* Default model parameters (9 floats, OModel order). */
 void tmd_oracle_default_model(float* out9) { memcpy(out9, &O_DEFAULT_MODEL, sizeof(OModel)); }
+
+/* ------------------------------------------------------------------------ */
+/* Entropy coding of a compressed frame: the step before track-model        */
+/* decoding (Sec. 2-3: the CTF's streams are entropy coded with rANS, and   */
+/* the entropy decoding feeds the track-model decoding).  The ALICE rANS    */
+/* format is not available; this is the project's own format, written from  */
+/* the definition of range asymmetric numeral systems (rANS, J. Duda,       */
+/* arXiv:1311.2540):                                                        */
+/*   scale M = 2^12.  Symbol s has frequency f_s (sum of all f = M) and     */
+/*   cumulative frequency c_s = sum of f_t over t < s; it owns the slots    */
+/*   [c_s, c_s + f_s) of [0, M).                                            */
+/*   encode s:  x -> (x div f_s) * M + c_s + (x mod f_s)                    */
+/*   decode:    slot = x mod M, s = the symbol owning slot,                 */
+/*              x -> f_s * (x div M) + slot - c_s                           */
+/*   The state stays in [2^16, 2^32): before s is encoded, while            */
+/*   x >= f_s * 2^20 the low 16 bits are emitted as a word and x >>= 16;    */
+/*   after a symbol is decoded, while x < 2^16, x = (x << 16) | next word.  */
+/*   A stream starts (encoder) and ends (decoder) at x = 2^16.              */
+/*                                                                          */
+/* Symbols are the bytes of the values: a field of width w (1, 2, 4 bytes)  */
+/* has w byte planes, each with its own 256-entry frequency table; value i  */
+/* is coded as its bytes, least significant first.  A field of n values is   */
+/* cut into chunks of 32 * 256 values; lane l (0..31) of a chunk codes the  */
+/* values 32 k + l (k = 0..255) of the chunk, each lane its own rANS stream. */
+/*                                                                          */
+/* Frequency normalisation (count n_s of symbol s among the n bytes of a     */
+/* plane): f_s = 0 if n_s = 0, else max(1, floor(n_s * M / n)); then a      */
+/* deficit M - sum f is added to the symbol with the largest count (lowest  */
+/* symbol on ties), and while the sum exceeds M, 1 is taken from the symbol  */
+/* with the largest f (lowest symbol on ties).  n = 0: f_0 = M.             */
+/*                                                                          */
+/* Byte layout (little-endian; every offset a multiple of 16):              */
+/*   frame header, 32 bytes: u32 magic 0x52444D54 ("TMDR"), version 1,      */
+/*     number of fields 23, values per lane per chunk 256, n_tracks,        */
+/*     n_attached, n_unattached, 0;                                         */
+/*   23 directory entries of 32 bytes, fields in the order of the frame     */
+/*     streams (qpt .. sigma_time_u): u64 section offset from the start,    */
+/*     u64 section bytes, u32 n, u32 width, u32 chunks, u32 0;              */
+/*   field section: u16 freq[w][256]; u32 state[chunks][32] (each lane's    */
+/*     decoder start state); u32 woff[chunks + 1] (chunk c's words occupy   */
+/*     u32 slots [woff[c], woff[c+1]) of the word area, a multiple of 32);  */
+/*     zero padding to 16 bytes; the word area: slot woff[c] + 32 j + l     */
+/*     holds lane l's words 2j (low half) and 2j + 1 (high half) in         */
+/*     decoding order, zero past the lane's last word.                      */
+/* ------------------------------------------------------------------------ */
+#define O_R_M 4096u
+#define O_R_LOWER 65536u
+#define O_R_K 256u
+#define O_R_CHUNK (32u * O_R_K)
+#define O_R_MAGIC 0x52444D54u
+#define O_R_NFIELD 23
+#define O_R_HEAD (32u + 32u * O_R_NFIELD)
+#define O_R_CORRUPT (-4)
+
+static void o_put16(uint8_t* p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
+static void o_put32(uint8_t* p, uint32_t v) {
+  for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+static void o_put64(uint8_t* p, uint64_t v) {
+  for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+static uint32_t o_get16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+static uint32_t o_get32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+static uint64_t o_get64(const uint8_t* p) {
+  return (uint64_t)o_get32(p) | ((uint64_t)o_get32(p + 4) << 32);
+}
+static uint64_t o_align16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
+
+/* value i of a field of width w, and its byte p */
+static uint32_t o_value(const void* a, uint32_t w, uint32_t i) {
+  if (w == 1) return ((const uint8_t*)a)[i];
+  if (w == 2) return ((const uint16_t*)a)[i];
+  return ((const uint32_t*)a)[i];
+}
+static void o_set_value(void* a, uint32_t w, uint32_t i, uint32_t v) {
+  if (w == 1) ((uint8_t*)a)[i] = (uint8_t)v;
+  else if (w == 2) ((uint16_t*)a)[i] = (uint16_t)v;
+  else ((uint32_t*)a)[i] = v;
+}
+
+static void o_rans_normalise(const uint64_t* count, uint64_t n, uint32_t* f) {
+  if (n == 0) {
+    for (int s = 0; s < 256; s++) f[s] = 0;
+    f[0] = O_R_M;
+    return;
+  }
+  uint64_t sum = 0;
+  int smax = 0;
+  for (int s = 0; s < 256; s++) {
+    if (count[s] == 0) f[s] = 0;
+    else {
+      uint64_t v = count[s] * O_R_M / n;
+      f[s] = v < 1 ? 1u : (uint32_t)v;
+    }
+    sum += f[s];
+    if (count[s] > count[smax]) smax = s;
+  }
+  if (sum < O_R_M) f[smax] += (uint32_t)(O_R_M - sum);
+  while (sum > O_R_M) {
+    int b = -1;
+    for (int s = 0; s < 256; s++)
+      if (f[s] > 1 && (b < 0 || f[s] > f[b])) b = s;
+    f[b] -= 1;
+    sum -= 1;
+  }
+}
+
+/* Fixed part of a field section: freq tables, states, chunk offsets. */
+static uint64_t o_rans_fixed(uint32_t n, uint32_t w) {
+  uint64_t nch = ((uint64_t)n + O_R_CHUNK - 1) / O_R_CHUNK;
+  return o_align16(512u * (uint64_t)w + 128u * nch + 4u * (nch + 1));
+}
+
+/* Largest possible section: every symbol emits a word. */
+uint64_t tmd_oracle_rans_field_bound(uint32_t n, uint32_t w) {
+  uint64_t nch = ((uint64_t)n + O_R_CHUNK - 1) / O_R_CHUNK;
+  return o_align16(o_rans_fixed(n, w) + nch * 32u * 4u * ((O_R_K * w + 1) / 2));
+}
+
+/* Encode one field (n values of width w) into a section.  Returns 0, -1 on
+ * allocation failure, -3 if cap is too small. */
+int tmd_oracle_rans_field_encode(const void* vals, uint32_t n, uint32_t w, uint8_t* out,
+                                 uint64_t cap, uint64_t* size) {
+  const uint32_t nch = (uint32_t)(((uint64_t)n + O_R_CHUNK - 1) / O_R_CHUNK);
+  uint32_t f[4][256], c[4][256];
+  for (uint32_t p = 0; p < w; p++) {
+    uint64_t count[256] = {0};
+    for (uint32_t i = 0; i < n; i++) count[(o_value(vals, w, i) >> (8 * p)) & 0xFFu]++;
+    o_rans_normalise(count, n, f[p]);
+    uint32_t acc = 0;
+    for (int s = 0; s < 256; s++) { c[p][s] = acc; acc += f[p][s]; }
+  }
+  const uint64_t a_state = 512u * (uint64_t)w, a_woff = a_state + 128u * (uint64_t)nch;
+  const uint64_t a_words = o_rans_fixed(n, w);
+  if (cap < a_words) return -3;
+  memset(out, 0, a_words);
+  for (uint32_t p = 0; p < w; p++)
+    for (int s = 0; s < 256; s++) o_put16(out + 2 * (256 * p + s), f[p][s]);
+
+  uint16_t* stack = (uint16_t*)malloc(sizeof(uint16_t) * O_R_K * 4);
+  uint16_t* words = (uint16_t*)malloc(sizeof(uint16_t) * 32 * (O_R_K * 4 + 1));
+  uint32_t nw[32];
+  if (!stack || !words) { free(stack); free(words); return -1; }
+  uint64_t woff = 0; /* u32 slots used so far */
+  for (uint32_t ch = 0; ch < nch; ch++) {
+    uint32_t maxpairs = 0;
+    for (uint32_t l = 0; l < 32; l++) {
+      /* this lane's values, in decoding order: i = base + 32 k + l */
+      const uint64_t base = (uint64_t)ch * O_R_CHUNK + l;
+      uint32_t nk = 0;
+      while (nk < O_R_K && base + 32u * nk < n) nk++;
+      uint32_t x = O_R_LOWER, ns = 0;
+      /* encode in reverse decoding order: values last to first, bytes high to low */
+      for (uint32_t k = nk; k-- > 0;) {
+        const uint32_t v = o_value(vals, w, (uint32_t)(base + 32u * k));
+        for (uint32_t p = w; p-- > 0;) {
+          const uint32_t s = (v >> (8 * p)) & 0xFFu, fs = f[p][s];
+          if ((uint64_t)x >= ((uint64_t)fs << 20)) {
+            stack[ns++] = (uint16_t)(x & 0xFFFFu);
+            x >>= 16;
+          }
+          x = (x / fs) * O_R_M + c[p][s] + (x % fs);
+        }
+      }
+      o_put32(out + a_state + 4u * (32u * (uint64_t)ch + l), x);
+      /* the decoder reads the words in the reverse order of emission */
+      for (uint32_t q = 0; q < ns; q++) words[l * (O_R_K * 4 + 1) + q] = stack[ns - 1 - q];
+      nw[l] = ns;
+      if ((ns + 1) / 2 > maxpairs) maxpairs = (ns + 1) / 2;
+    }
+    o_put32(out + a_woff + 4u * (uint64_t)ch, (uint32_t)woff);
+    const uint64_t need = a_words + 4u * (woff + 32u * (uint64_t)maxpairs);
+    if (need > cap) { free(stack); free(words); return -3; }
+    for (uint32_t j = 0; j < maxpairs; j++)
+      for (uint32_t l = 0; l < 32; l++) {
+        const uint32_t q = 2 * j;
+        const uint32_t lo = q < nw[l] ? words[l * (O_R_K * 4 + 1) + q] : 0u;
+        const uint32_t hi = q + 1 < nw[l] ? words[l * (O_R_K * 4 + 1) + q + 1] : 0u;
+        o_put32(out + a_words + 4u * (woff + 32u * j + l), lo | (hi << 16));
+      }
+    woff += 32u * (uint64_t)maxpairs;
+  }
+  o_put32(out + a_woff + 4u * (uint64_t)nch, (uint32_t)woff);
+  free(stack);
+  free(words);
+  uint64_t total = o_align16(a_words + 4u * woff);
+  if (total > cap) return -3;
+  memset(out + a_words + 4u * woff, 0, total - (a_words + 4u * woff));
+  *size = total;
+  return 0;
+}
+
+/* Decode one field section of `bytes` bytes into n values of width w.
+ * Returns 0, or -4 if the section is malformed or a stream fails its checks
+ * (a lane runs out of words, or does not end at the start state 2^16). */
+int tmd_oracle_rans_field_decode(const uint8_t* sec, uint64_t bytes, uint32_t n, uint32_t w,
+                                 void* vals) {
+  const uint32_t nch = (uint32_t)(((uint64_t)n + O_R_CHUNK - 1) / O_R_CHUNK);
+  const uint64_t a_state = 512u * (uint64_t)w, a_woff = a_state + 128u * (uint64_t)nch;
+  const uint64_t a_words = o_rans_fixed(n, w);
+  if (w != 1 && w != 2 && w != 4) return O_R_CORRUPT;
+  if (bytes < a_words) return O_R_CORRUPT;
+  /* the symbol owning each slot, per plane */
+  uint32_t f[4][256], c[4][256];
+  uint8_t slot_sym[4][O_R_M];
+  for (uint32_t p = 0; p < w; p++) {
+    uint32_t acc = 0;
+    for (int s = 0; s < 256; s++) {
+      f[p][s] = o_get16(sec + 2 * (256 * p + s));
+      c[p][s] = acc;
+      for (uint32_t t = 0; t < f[p][s] && acc + t < O_R_M; t++) slot_sym[p][acc + t] = (uint8_t)s;
+      acc += f[p][s];
+    }
+    if (acc != O_R_M) return O_R_CORRUPT;
+  }
+  const uint64_t area = (bytes - a_words) / 4u; /* u32 slots available */
+  if (o_get32(sec + a_woff) != 0) return O_R_CORRUPT;
+  int bad = 0;
+  for (uint32_t ch = 0; ch < nch; ch++) {
+    const uint64_t w0 = o_get32(sec + a_woff + 4u * (uint64_t)ch);
+    const uint64_t w1 = o_get32(sec + a_woff + 4u * ((uint64_t)ch + 1));
+    if (w1 < w0 || (w1 - w0) % 32u != 0 || w1 > area) return O_R_CORRUPT;
+    const uint32_t maxpairs = (uint32_t)((w1 - w0) / 32u);
+    for (uint32_t l = 0; l < 32; l++) {
+      const uint64_t base = (uint64_t)ch * O_R_CHUNK + l;
+      uint32_t x = o_get32(sec + a_state + 4u * (32u * (uint64_t)ch + l));
+      uint32_t q = 0; /* next word of this lane */
+      for (uint32_t k = 0; k < O_R_K && base + 32u * k < n; k++) {
+        uint32_t v = 0;
+        for (uint32_t p = 0; p < w; p++) {
+          const uint32_t slot = x % O_R_M, s = slot_sym[p][slot];
+          x = f[p][s] * (x / O_R_M) + slot - c[p][s];
+          v |= s << (8 * p);
+          while (x < O_R_LOWER) {
+            uint32_t word = 0;
+            if (q / 2 < maxpairs) {
+              const uint32_t pair = o_get32(sec + a_words + 4u * (w0 + 32u * (q / 2) + l));
+              word = (q % 2) ? pair >> 16 : pair & 0xFFFFu;
+            } else {
+              bad = 1; /* out of words: the value is garbage, keep going */
+            }
+            q++;
+            x = (x << 16) | word;
+            if (x < O_R_LOWER) { bad = 1; break; }
+          }
+        }
+        o_set_value(vals, w, (uint32_t)(base + 32u * k), v);
+      }
+      if (x != O_R_LOWER) bad = 1;
+    }
+  }
+  return bad ? O_R_CORRUPT : 0;
+}
+
+/* Field f (0..22) of a frame: array, width and length. */
+static void o_frame_field(const OFrame* F, int i, const void** a, uint32_t* w, uint32_t* n) {
+  const uint32_t nt = F->n_tracks, na = F->n_attached, nu = F->n_unattached, nd = na - nt;
+  const void* arr[O_R_NFIELD] = {F->qpt, F->row, F->slice, F->pad, F->time, F->ncl,
+                                 F->qtot_a, F->qmax_a, F->flags_a, F->sigma_pad_a,
+                                 F->sigma_time_a, F->row_diff, F->slice_leg_diff, F->pad_res,
+                                 F->time_res, F->n_unatt, F->pad_diff_u, F->time_diff_u,
+                                 F->qtot_u, F->qmax_u, F->flags_u, F->sigma_pad_u,
+                                 F->sigma_time_u};
+  static const uint32_t width[O_R_NFIELD] = {1, 1, 1, 2, 4, 2, 2, 2, 1, 1, 1, 1,
+                                             1, 2, 4, 4, 2, 4, 2, 2, 1, 1, 1};
+  const uint32_t len[O_R_NFIELD] = {nt, nt, nt, nt, nt, nt, na, na, na, na, na, nd,
+                                    nd, nd, nd, O_NBIN, nu, nu, nu, nu, nu, nu, nu};
+  *a = arr[i];
+  *w = width[i];
+  *n = len[i];
+}
+
+uint64_t tmd_oracle_rans_frame_bound(const OFrame* F) {
+  if (F->n_attached < F->n_tracks) return 0;
+  uint64_t total = O_R_HEAD;
+  for (int i = 0; i < O_R_NFIELD; i++) {
+    const void* a;
+    uint32_t w, n;
+    o_frame_field(F, i, &a, &w, &n);
+    total += tmd_oracle_rans_field_bound(n, w);
+  }
+  return total;
+}
+
+/* Encode a compressed frame (its 23 streams) into one coded frame.  Returns
+ * 0, -1 on allocation failure, -2 if n_attached < n_tracks, -3 if cap is too
+ * small. */
+int tmd_oracle_rans_frame_encode(const OFrame* F, uint8_t* out, uint64_t cap, uint64_t* size) {
+  if (F->n_attached < F->n_tracks) return -2;
+  if (cap < O_R_HEAD) return -3;
+  memset(out, 0, O_R_HEAD);
+  o_put32(out, O_R_MAGIC);
+  o_put32(out + 4, 1);
+  o_put32(out + 8, O_R_NFIELD);
+  o_put32(out + 12, O_R_K);
+  o_put32(out + 16, F->n_tracks);
+  o_put32(out + 20, F->n_attached);
+  o_put32(out + 24, F->n_unattached);
+  uint64_t off = O_R_HEAD;
+  for (int i = 0; i < O_R_NFIELD; i++) {
+    const void* a;
+    uint32_t w, n;
+    o_frame_field(F, i, &a, &w, &n);
+    uint64_t used = 0;
+    const int rc = tmd_oracle_rans_field_encode(a, n, w, out + off, cap - off, &used);
+    if (rc != 0) return rc;
+    uint8_t* d = out + 32 + 32 * i;
+    o_put64(d, off);
+    o_put64(d + 8, used);
+    o_put32(d + 16, n);
+    o_put32(d + 20, w);
+    o_put32(d + 24, (uint32_t)(((uint64_t)n + O_R_CHUNK - 1) / O_R_CHUNK));
+    off += used;
+  }
+  *size = off;
+  return 0;
+}
+
+/* Decode a coded frame of `bytes` bytes whose counts must be those of F (the
+ * arrays of F are not read); the streams are written to o.  Returns 0 or -4
+ * (malformed or failing its stream checks). */
+int tmd_oracle_rans_frame_decode(const uint8_t* blob, uint64_t bytes, const OFrame* F,
+                                 OFrameOut* o) {
+  if (bytes < O_R_HEAD) return O_R_CORRUPT;
+  if (o_get32(blob) != O_R_MAGIC || o_get32(blob + 4) != 1 || o_get32(blob + 8) != O_R_NFIELD ||
+      o_get32(blob + 12) != O_R_K || o_get32(blob + 16) != F->n_tracks ||
+      o_get32(blob + 20) != F->n_attached || o_get32(blob + 24) != F->n_unattached ||
+      F->n_attached < F->n_tracks)
+    return O_R_CORRUPT;
+  void* dst[O_R_NFIELD] = {o->qpt, o->row, o->slice, o->pad, o->time, o->ncl, o->qtot_a,
+                           o->qmax_a, o->flags_a, o->sigma_pad_a, o->sigma_time_a,
+                           o->row_diff, o->slice_leg_diff, o->pad_res, o->time_res,
+                           o->n_unatt, o->pad_diff_u, o->time_diff_u, o->qtot_u, o->qmax_u,
+                           o->flags_u, o->sigma_pad_u, o->sigma_time_u};
+  int rc = 0;
+  for (int i = 0; i < O_R_NFIELD; i++) {
+    const void* a;
+    uint32_t w, n;
+    o_frame_field(F, i, &a, &w, &n);
+    const uint8_t* d = blob + 32 + 32 * i;
+    const uint64_t off = o_get64(d), len = o_get64(d + 8);
+    if (o_get32(d + 16) != n || o_get32(d + 20) != w ||
+        o_get32(d + 24) != (uint32_t)(((uint64_t)n + O_R_CHUNK - 1) / O_R_CHUNK) ||
+        off % 16 != 0 || off < O_R_HEAD || off > bytes || len > bytes - off)
+      return O_R_CORRUPT;
+    if (tmd_oracle_rans_field_decode(blob + off, len, n, w, dst[i]) != 0) rc = O_R_CORRUPT;
+  }
+  return rc;
+}

@@ -40,6 +40,18 @@ MUTANTS = {
                                    "const float ca = g_cos[s % 18], sa = g_sin[s % 18];"),
     "xyz_drift_speed": ("const float zabs = 250.0f - t * 0.5f;", "const float zabs = 250.0f - t;"),
     "xyz_side_sign": ("gz[i] = s < 18 ? zabs : -zabs;", "gz[i] = zabs;"),
+    "rans_drop_cumulative": ("x = (x / fs) * O_R_M + c[p][s] + (x % fs);",
+                             "x = (x / fs) * O_R_M + (x % fs);"),
+    "rans_renorm_threshold": ("if ((uint64_t)x >= ((uint64_t)fs << 20)) {",
+                              "if ((uint64_t)x >= ((uint64_t)fs << 19)) {"),
+    "rans_words_not_reversed": ("words[l * (O_R_K * 4 + 1) + q] = stack[ns - 1 - q];",
+                                "words[l * (O_R_K * 4 + 1) + q] = stack[q];"),
+    "rans_deficit_to_symbol_zero": ("if (sum < O_R_M) f[smax] += (uint32_t)(O_R_M - sum);",
+                                    "if (sum < O_R_M) f[0] += (uint32_t)(O_R_M - sum);"),
+    "rans_lane_major_words": ("o_put32(out + a_words + 4u * (woff + 32u * j + l), lo | (hi << 16));",
+                              "o_put32(out + a_words + 4u * (woff + maxpairs * l + j), lo | (hi << 16));"),
+    "rans_high_byte_first": ("v |= s << (8 * p);\n          while (x < O_R_LOWER) {",
+                             "v |= s << (8 * (w - 1 - p));\n          while (x < O_R_LOWER) {"),
 }
 
 
@@ -57,6 +69,7 @@ def test_pins_catch_mutant(name, tmp_path):
     env = dict(os.environ, TMD_ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_xyz.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_xyz.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_rans.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
