@@ -407,6 +407,47 @@ def run(args):
     dec.tmd_decode_host_stream([hin] * e2e_steps, [hout] * e2e_steps, stream)
     barrier()
     e2e_dt = time.perf_counter() - t0
+    # entropy-coded frame (the step in front of the decoder): the streams are
+    # coded once on the host (setup, not timed), then the GPU entropy decode
+    # alone and the chained entropy + track-model decode are timed with events
+    t0 = time.perf_counter()
+    blob = tmd.rans_encode(hframe)
+    enc_host_s = time.perf_counter() - t0
+    coded = torch.from_numpy(blob).to(native.device)
+    lens = {"track": nt, "att": na, "diff": na - nt, "bin": 5472, "unatt": nu}
+    tdt = {1: torch.uint8, 2: torch.int16, 4: torch.int32}
+    rdec = {n: torch.empty(lens[k], dtype=tdt[w], device=native.device)
+            for n, w, k in tmd.FRAME_FIELDS}
+    rstatus = torch.zeros(1, dtype=torch.int32, device=native.device)
+    rarr = tmd.tmd_frame_arrays(nt, na, nu, *[tmd._ptr(rdec[n]) for n, _, _ in tmd.FRAME_FIELDS])
+    c_out = (torch.empty_like(native), torch.empty_like(row_start), torch.empty(
+        5472, dtype=torch.int32, device=native.device), torch.empty(1, dtype=torch.int32,
+                                                                    device=native.device))
+    c_fout = tmd.frame_out(*c_out)
+    for _ in range(3):
+        dec.tmd_rans_decode(coded, blob.size, rarr, rstatus, stream)
+        dec.tmd_decode_coded_frame(coded, blob.size, nt, na, nu, c_fout, stream)
+    torch.cuda.synchronize()
+    coded_ok = (int(rstatus.item()) == 0 and int(c_out[3].item()) == 0 and
+                all(torch.equal(rdec[n], frame[n]) for n, _, _ in tmd.FRAME_FIELDS) and
+                torch.equal(c_out[0], native))
+    reps_c = max(5, min(args.steps, 30))
+    barrier()
+    start.record(stream)
+    for _ in range(reps_c):
+        dec.tmd_rans_decode(coded, blob.size, rarr, rstatus, stream)
+    stop.record(stream)
+    barrier()
+    rans_ms = start.elapsed_time(stop) / reps_c
+    start.record(stream)
+    for _ in range(reps_c):
+        dec.tmd_decode_coded_frame(coded, blob.size, nt, na, nu, c_fout, stream)
+    stop.record(stream)
+    barrier()
+    chain_ms = start.elapsed_time(stop) / reps_c
+    rans_bytes = int(blob.size) + h2d
+    rans_gbs = rans_bytes / (rans_ms * 1e-3) / 1e9
+    del coded, rdec, c_out
     assert torch.equal(h_native, native.cpu()), "host entry point disagrees with device path"
     e2e_value = whole_job_rate(e2e_steps * (na + nu), e2e_dt, native.device)
     line = None
@@ -434,6 +475,14 @@ def run(args):
                            "clusters_per_s": (na + nu) / (xyz_ms * 1e-3),
                            "algorithmic_bytes": 24 * (na + nu), "gbs": xyz_gbs,
                            "frac_hbm": xyz_gbs / peak, "in_step": False},
+            "entropy": {"kernel": "k_rans_decode", "coded_bytes": int(blob.size),
+                        "stream_bytes": h2d, "ratio": int(blob.size) / h2d,
+                        "ms_per_frame": rans_ms, "clusters_per_s": (na + nu) / (rans_ms * 1e-3),
+                        "algorithmic_bytes": rans_bytes, "gbs": rans_gbs,
+                        "frac_hbm": rans_gbs / peak,
+                        "chain_ms_per_frame": chain_ms,
+                        "chain_clusters_per_s": (na + nu) / (chain_ms * 1e-3),
+                        "host_encode_s": enc_host_s, "bit_exact": coded_ok, "in_step": False},
             "top_kernel": top[0],
             "tuning": tuned,
             "cpu_baseline": base,

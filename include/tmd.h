@@ -56,6 +56,8 @@ extern "C" {
 #define TMD_STATUS_TIME 4u    /* a decoded time code >= 2^24 (truncated in the record) */
 #define TMD_STATUS_TIMEOUT 8u /* a bounded wait inside a kernel ran out */
 #define TMD_STATUS_LIMIT 16u  /* the frame breaks a decoder limit (record not written) */
+#define TMD_STATUS_CODED 32u  /* an entropy-coded frame is malformed or one of its
+                                 streams failed its checks (tmd_rans_decode) */
 
 typedef struct tmd_handle tmd_handle;
 
@@ -322,6 +324,122 @@ int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in, const tmd_fr
  * TMD_ERR_CUDA (launch failure). */
 int tmd_global_xyz(tmd_handle* h, const uint8_t* native, const uint32_t* row_start, uint32_t n,
                    float* x, float* y, float* z, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Entropy-coded frames: the step before track-model decoding
+ * (arXiv:2411.02206, Sec. 2-3: the streams of a compressed time frame are
+ * entropy coded with rANS, and the entropy decoding feeds the track-model
+ * decoding).  The ALICE rANS format is not public; this is the library's own
+ * format, range asymmetric numeral systems (J. Duda, arXiv:1311.2540):
+ *
+ *   Scale M = 2^12.  Symbol s has frequency f_s (the f of a table sum to M)
+ *   and cumulative frequency c_s = sum of f_t for t < s; it owns the slots
+ *   [c_s, c_s + f_s) of [0, M).  Encoding s maps a state x to
+ *   (x div f_s) * M + c_s + (x mod f_s); decoding takes slot = x mod M, the
+ *   symbol s owning it, and x -> f_s * (x div M) + slot - c_s.  States stay
+ *   in [2^16, 2^32): before s is encoded, while x >= f_s * 2^20 the low 16
+ *   bits are emitted as a word and x >>= 16; after a symbol is decoded, while
+ *   x < 2^16, x = (x << 16) | next word.  Every stream starts (encoding) and
+ *   ends (decoding) at x = 2^16.
+ *
+ *   Symbols are bytes: a stream of width w (1, 2 or 4 bytes per value) has w
+ *   byte planes, each with its own 256-entry frequency table, and value i is
+ *   coded as its bytes, least significant first.  A stream of n values is
+ *   cut into chunks of 32 * TMD_RANS_LANE_VALUES values; lane l (0..31) of a
+ *   chunk codes the chunk's values 32 k + l, k = 0, 1, ..., as its own rANS
+ *   stream (the 32 lanes of a chunk decode independently).
+ *
+ *   Frequencies of a plane whose n bytes hold symbol s n_s times: f_s = 0 if
+ *   n_s = 0, else max(1, floor(n_s * M / n)); a deficit M - sum(f) is added to
+ *   the symbol with the largest n_s (the lowest such symbol), and while the
+ *   sum exceeds M, 1 is taken from the symbol with the largest f_s (the lowest
+ *   such symbol).  A plane with n = 0 has f_0 = M.
+ *
+ * Byte layout of a coded frame (little-endian, 16-byte aligned sections):
+ *   header, 32 bytes: u32 magic TMD_RANS_MAGIC ("TMDR"), u32 version 1,
+ *     u32 fields 23, u32 TMD_RANS_LANE_VALUES, u32 n_tracks, u32 n_attached,
+ *     u32 n_unattached, u32 0;
+ *   23 directory entries of 32 bytes, one per stream of tmd_frame_in in
+ *     member order (qpt ... sigma_time_u): u64 section offset from the start
+ *     of the coded frame, u64 section bytes, u32 values n, u32 width w,
+ *     u32 chunks ceil(n / (32 * TMD_RANS_LANE_VALUES)), u32 0;
+ *   per stream a section: u16 freq[w][256]; u32 state[chunks][32], the start
+ *     state of each lane's decoder; u32 woff[chunks + 1], chunk c's words in
+ *     the u32 slots [woff[c], woff[c+1]) of the word area, a multiple of 32
+ *     slots (woff[0] = 0); zero bytes to a multiple of 16; the word area,
+ *     where slot woff[c] + 32 j + l holds lane l's words 2 j (low 16 bits)
+ *     and 2 j + 1 (high 16 bits) in decoding order, zero past its last word.
+ * ------------------------------------------------------------------------ */
+#define TMD_RANS_MAGIC 0x52444D54u
+#define TMD_RANS_LANE_VALUES 256u
+#define TMD_RANS_HEADER_BYTES 768u
+
+/* Writable SoA arrays of a compressed frame: the members and lengths of
+ * tmd_frame_in, with pointers the decoder writes through. */
+typedef struct tmd_frame_arrays {
+  uint32_t n_tracks, n_attached, n_unattached;
+  uint8_t* qpt;
+  uint8_t* row;
+  uint8_t* slice;
+  uint16_t* pad;
+  uint32_t* time;
+  uint16_t* ncl;
+  uint16_t* qtot_a;
+  uint16_t* qmax_a;
+  uint8_t* flags_a;
+  uint8_t* sigma_pad_a;
+  uint8_t* sigma_time_a;
+  uint8_t* row_diff;
+  uint8_t* slice_leg_diff;
+  uint16_t* pad_res;
+  uint32_t* time_res;
+  uint32_t* n_unatt;
+  uint16_t* pad_diff_u;
+  uint32_t* time_diff_u;
+  uint16_t* qtot_u;
+  uint16_t* qmax_u;
+  uint8_t* flags_u;
+  uint8_t* sigma_pad_u;
+  uint8_t* sigma_time_u;
+} tmd_frame_arrays;
+
+/* Largest coded frame for these counts (every symbol emitting a word), in
+ * bytes; 0 if n_attached < n_tracks. */
+uint64_t tmd_rans_bound(uint32_t n_tracks, uint32_t n_attached, uint32_t n_unattached);
+
+/* Entropy-code the 23 streams of a frame held in HOST memory (`in`, lengths
+ * as in tmd_frame_in) into `out` (host, `capacity` bytes, 16-byte aligned;
+ * tmd_rans_bound bytes always suffice); *size receives the coded bytes.
+ * n_threads host threads share the work (0: one per core).  No handle or GPU
+ * is needed.  Errors: TMD_ERR_ARG (null or misaligned pointer, n_attached <
+ * n_tracks, capacity too small), TMD_ERR_NOMEM. */
+int tmd_rans_encode_host(const tmd_frame_in* in, void* out, uint64_t capacity, uint64_t* size,
+                         uint32_t n_threads);
+
+/* Entropy-decode a coded frame on the GPU, asynchronously on `stream`.
+ *   coded:  device, coded_bytes bytes, 16-byte aligned (borrowed until the
+ *           stream passes the decode)
+ *   dst:    device arrays to fill, counts and natural alignment as in
+ *           tmd_frame_in; the counts must equal those in the coded header
+ *   status: device, one u32; TMD_STATUS_CODED is OR-ed in when the header,
+ *           the directory, a frequency table or a chunk's word offsets are
+ *           malformed, or a lane runs out of words or does not end at its
+ *           start state (the affected values are then unspecified but every
+ *           access stays inside the coded frame and dst).  The caller clears
+ *           *status beforehand.
+ * Errors (host side): TMD_ERR_ARG (null or misaligned pointer, coded_bytes <
+ * TMD_RANS_HEADER_BYTES, n_attached < n_tracks), TMD_ERR_CUDA. */
+int tmd_rans_decode(tmd_handle* h, const void* coded, uint64_t coded_bytes,
+                    const tmd_frame_arrays* dst, uint32_t* status, void* stream);
+
+/* Entropy decoding followed by track-model decoding of one coded frame: the
+ * streams are decoded into handle-owned device memory (grown on demand) and
+ * the frame is then decoded as by tmd_decode_frame into `out`, all on
+ * `stream`.  out->status receives TMD_STATUS_CODED as well as the decoder's
+ * bits.  Errors as tmd_rans_decode and tmd_decode_frame, plus TMD_ERR_NOMEM. */
+int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t coded_bytes,
+                           uint32_t n_tracks, uint32_t n_attached, uint32_t n_unattached,
+                           const tmd_frame_out* out, void* stream);
 
 /* Instrumentation.  While enabled, every kernel the handle launches is
  * bracketed by CUDA events on its stream.  tmd_profile_read waits for the

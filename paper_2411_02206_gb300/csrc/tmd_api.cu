@@ -194,6 +194,7 @@ tmd_handle::~tmd_handle() {
   }
   if (scratch) cudaFree(scratch);
   if (stage) cudaFree(stage);
+  if (coded) cudaFree(coded);
   if (trace_status) cudaFree(trace_status);
   if (aux) cudaStreamDestroy(aux);
   if (fork) cudaEventDestroy(fork);

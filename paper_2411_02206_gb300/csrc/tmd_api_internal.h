@@ -68,6 +68,8 @@ struct tmd_handle {
   int next_slot = 0;
   void* stage = nullptr;  // device staging of tmd_decode_frame_host
   size_t stage_bytes = 0;
+  void* coded = nullptr;  // entropy-decoded streams of tmd_decode_coded_frame
+  size_t coded_bytes = 0;
   TmdServer* server = nullptr;
   TmdProfile prof;
   uint32_t* trace_status = nullptr;        // status word of tmd_track_trace calls

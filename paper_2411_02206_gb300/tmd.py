@@ -25,6 +25,8 @@ TMD_OK, TMD_PENDING = 0, 1
 TMD_ERR_ARG, TMD_ERR_CORRUPT, TMD_ERR_BUDGET, TMD_ERR_TIMEOUT = -1, -2, -3, -4
 TMD_ERR_CUDA, TMD_ERR_NOMEM, TMD_ERR_STATE = -5, -6, -7
 STATUS_COUNT, STATUS_ROW, STATUS_TIME, STATUS_TIMEOUT, STATUS_LIMIT = 1, 2, 4, 8, 16
+STATUS_CODED = 32
+RANS_HEADER_BYTES = 768
 
 # (field, element bytes, length kind) in tmd_frame_in order
 FRAME_FIELDS = [
@@ -55,6 +57,10 @@ class tmd_config(ctypes.Structure):
 class tmd_frame_in(ctypes.Structure):
     _fields_ = [("n_tracks", ctypes.c_uint32), ("n_attached", ctypes.c_uint32),
                 ("n_unattached", ctypes.c_uint32)] + [(n, _P) for n, _, _ in FRAME_FIELDS]
+
+
+class tmd_frame_arrays(ctypes.Structure):
+    _fields_ = tmd_frame_in._fields_
 
 
 class tmd_frame_out(ctypes.Structure):
@@ -134,6 +140,18 @@ def lib():
             L.tmd_profile_read.restype = ctypes.c_int
             L.tmd_global_xyz.argtypes = [H, _P, _P, ctypes.c_uint32, _P, _P, _P, _P]
             L.tmd_global_xyz.restype = ctypes.c_int
+            L.tmd_rans_bound.argtypes = [ctypes.c_uint32] * 3
+            L.tmd_rans_bound.restype = ctypes.c_uint64
+            L.tmd_rans_encode_host.argtypes = [ctypes.POINTER(tmd_frame_in), _P, ctypes.c_uint64,
+                                               ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint32]
+            L.tmd_rans_encode_host.restype = ctypes.c_int
+            L.tmd_rans_decode.argtypes = [H, _P, ctypes.c_uint64, ctypes.POINTER(tmd_frame_arrays),
+                                          _P, _P]
+            L.tmd_rans_decode.restype = ctypes.c_int
+            L.tmd_decode_coded_frame.argtypes = [H, _P, ctypes.c_uint64, ctypes.c_uint32,
+                                                 ctypes.c_uint32, ctypes.c_uint32,
+                                                 ctypes.POINTER(tmd_frame_out), _P]
+            L.tmd_decode_coded_frame.restype = ctypes.c_int
             L.tmd_last_error_string.argtypes = [H]
             L.tmd_last_error_string.restype = ctypes.c_char_p
             _lib = L
@@ -147,6 +165,33 @@ def tmd_decode_frame_noalloc(fin: tmd_frame_in, fout: tmd_frame_out, stream=None
     rc = lib().tmd_decode_frame_noalloc(ctypes.byref(fin), ctypes.byref(fout),
                                         _P(_stream_ptr(stream)), err, len(err))
     return rc, err.value.decode()
+
+
+def tmd_rans_bound(n_tracks: int, n_attached: int, n_unattached: int) -> int:
+    return int(lib().tmd_rans_bound(n_tracks, n_attached, n_unattached))
+
+
+def tmd_rans_encode_host(fin: tmd_frame_in, out, capacity: int, n_threads: int = 0):
+    """Entropy-code a frame held in host memory; returns (rc, coded bytes)."""
+    size = ctypes.c_uint64(0)
+    rc = lib().tmd_rans_encode_host(ctypes.byref(fin), _P(_ptr(out)), capacity,
+                                    ctypes.byref(size), n_threads)
+    return rc, int(size.value)
+
+
+def rans_encode(frame: dict, n_threads: int = 0):
+    """Entropy-code a host frame dict (numpy arrays or CPU tensors); returns
+    a uint8 numpy array (a view of a 16-byte aligned buffer)."""
+    import numpy as np
+    nt, na, nu = counts(frame)
+    cap = tmd_rans_bound(nt, na, nu)
+    buf = np.empty(cap + 16, np.uint8)
+    pad = (-buf.ctypes.data) % 16
+    out = buf[pad:pad + cap]
+    rc, size = tmd_rans_encode_host(frame_in(frame), out, cap, n_threads)
+    if rc != TMD_OK:
+        raise TmdError(rc, "tmd_rans_encode_host failed")
+    return out[:size]
 
 
 class TmdError(RuntimeError):
@@ -240,6 +285,18 @@ class Decoder:
         out = [torch.empty(n, dtype=torch.float32, device=native.device) for _ in range(3)]
         self.tmd_global_xyz(native, row_start, n, *out, stream=stream)
         return tuple(out)
+
+    def tmd_rans_decode(self, coded, coded_bytes: int, arrays: tmd_frame_arrays, status,
+                        stream=None) -> int:
+        return self._check(self._L.tmd_rans_decode(self.h, _P(_ptr(coded)), coded_bytes,
+                                                   ctypes.byref(arrays), _P(_ptr(status)),
+                                                   _P(_stream_ptr(stream))))
+
+    def tmd_decode_coded_frame(self, coded, coded_bytes: int, n_tracks: int, n_attached: int,
+                               n_unattached: int, fout: tmd_frame_out, stream=None) -> int:
+        return self._check(self._L.tmd_decode_coded_frame(
+            self.h, _P(_ptr(coded)), coded_bytes, n_tracks, n_attached, n_unattached,
+            ctypes.byref(fout), _P(_stream_ptr(stream))))
 
     def tmd_decode_frame_host(self, fin: tmd_frame_in, fout: tmd_frame_out, stream=None) -> int:
         return self._check(self._L.tmd_decode_frame_host(
@@ -338,6 +395,38 @@ class Decoder:
         att = torch.empty(NBIN, dtype=torch.int32, device=dev)
         status = torch.empty(1, dtype=torch.int32, device=dev)
         self.tmd_decode_frame(frame_in(frame), frame_out(native, row_start, att, status), stream)
+        return native, row_start, att, status
+
+    def rans_decode(self, coded, n_tracks: int, n_attached: int, n_unattached: int,
+                    stream=None):
+        """Entropy-decode a device-resident coded frame (uint8 tensor); returns
+        (frame dict of device tensors, status int32[1])."""
+        import torch
+        dev = coded.device
+        tdt = {1: torch.uint8, 2: torch.int16, 4: torch.int32}
+        lens = {"track": n_tracks, "att": n_attached, "diff": n_attached - n_tracks,
+                "bin": NBIN, "unatt": n_unattached}
+        frame = {n: torch.empty(lens[k], dtype=tdt[w], device=dev) for n, w, k in FRAME_FIELDS}
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        arrays = tmd_frame_arrays(n_tracks, n_attached, n_unattached,
+                                  *[_ptr(frame[n]) for n, _, _ in FRAME_FIELDS])
+        self.tmd_rans_decode(coded, int(coded.numel()), arrays, status, stream)
+        return frame, status
+
+    def decode_coded(self, coded, n_tracks: int, n_attached: int, n_unattached: int,
+                     stream=None):
+        """Entropy decoding then track-model decoding of a device-resident
+        coded frame; returns (native, row_start, att_count, status) as decode()."""
+        import torch
+        dev = coded.device
+        native = torch.empty((n_attached + n_unattached, REC_BYTES), dtype=torch.uint8,
+                             device=dev)
+        row_start = torch.empty(NBIN + 1, dtype=torch.int32, device=dev)
+        att = torch.empty(NBIN, dtype=torch.int32, device=dev)
+        status = torch.empty(1, dtype=torch.int32, device=dev)
+        self.tmd_decode_coded_frame(coded, int(coded.numel()), n_tracks, n_attached,
+                                    n_unattached, frame_out(native, row_start, att, status),
+                                    stream)
         return native, row_start, att, status
 
     def encode(self, truth: dict, stream=None) -> dict:
