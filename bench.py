@@ -330,7 +330,8 @@ def run(args):
     tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
                                               "scatter_variant", "overlap", "unatt_variant",
                                               "place", "prekey", "decode_blocks_per_sm",
-                                              "unatt_blocks_per_sm")}
+                                              "unatt_blocks_per_sm", "rans_variant",
+                                              "rans_overlap")}
     for _ in range(args.warmup):
         dec.tmd_decode_frame(fin, fout, stream)
     torch.cuda.synchronize()
