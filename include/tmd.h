@@ -22,6 +22,10 @@
  *     never throws; tmd_last_error_string() describes the last failure.
  *   - A handle is used by one host thread at a time, except tmd_submit /
  *     tmd_poll / tmd_release, which lock internally.
+ *   - Calls that decode or encode through a handle share its scratch memory:
+ *     each such call, on whatever stream, first waits (on the device) for the
+ *     previous one to finish with it.  Inside a stream capture nothing is
+ *     waited for: the captured graph orders the work.
  */
 #ifndef TMD_H
 #define TMD_H

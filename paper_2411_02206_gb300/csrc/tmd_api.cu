@@ -143,6 +143,23 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
 // ---------------------------------------------------------------------------
 // handle
 // ---------------------------------------------------------------------------
+int tmd_handle::order_after_previous(cudaStream_t st, bool* order) {
+  tmd_handle* h = this;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  *order = cap == cudaStreamCaptureStatusNone;  // in a capture the caller's graph orders the work
+  if (*order && scratch_busy) CK(cudaStreamWaitEvent(st, scratch_done, 0));
+  return TMD_OK;
+}
+
+int tmd_handle::mark_scratch_done(cudaStream_t st, bool order) {
+  if (!order) return TMD_OK;
+  tmd_handle* h = this;
+  CK(cudaEventRecord(scratch_done, st));
+  scratch_busy = true;
+  return TMD_OK;
+}
+
 int tmd_handle::ensure_scratch(size_t bytes) {
   if (bytes <= scratch_bytes) return TMD_OK;
   tmd_handle* h = this;
@@ -198,6 +215,7 @@ tmd_handle::~tmd_handle() {
   if (trace_status) cudaFree(trace_status);
   if (aux) cudaStreamDestroy(aux);
   if (fork) cudaEventDestroy(fork);
+  if (scratch_done) cudaEventDestroy(scratch_done);
   if (join) cudaEventDestroy(join);
   if (h2d) cudaStreamSynchronize(h2d), cudaStreamDestroy(h2d);
   if (d2h) cudaStreamSynchronize(d2h), cudaStreamDestroy(d2h);
@@ -232,6 +250,8 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming),
+                           "event")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->scratch_done, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, prepare_count_rank(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, prepare_att_scatter(), "smem attribute")) != TMD_OK ||
@@ -398,13 +418,15 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   int slot = 0;
   if ((rc = h->acquire_slot(record_bytes, slot)) != TMD_OK) return rc;
   tmd_handle::Slot& S = h->slots[slot];
+  bool order = false;
+  if ((rc = h->order_after_previous(st, &order)) != TMD_OK) return rc;
   const bool two = (h->tune_overlap || h->tune_prekey) && !tin;
   rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on,
                    two ? h->aux : nullptr, h->fork, h->join, trace);
   if (rc != TMD_OK) return rc;
   CK(cudaEventRecord(S.done, st));
   S.used = true;
-  return TMD_OK;
+  return h->mark_scratch_done(st, order);
 }
 
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,

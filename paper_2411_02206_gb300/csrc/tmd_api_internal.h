@@ -86,6 +86,14 @@ struct tmd_handle {
   size_t pipe_bytes[kPipeSlots] = {};
   cudaEvent_t pipe_in[kPipeSlots] = {}, pipe_dec[kPipeSlots] = {}, pipe_out[kPipeSlots] = {};
 
+  // Calls share the scratch (and the coded-frame streams): a call on any
+  // stream first waits for the previous call's work on them, recorded in
+  // scratch_done.  Inside a stream capture the caller's graph orders the
+  // work and nothing is waited for or recorded (*order is false).
+  cudaEvent_t scratch_done = nullptr;
+  bool scratch_busy = false;
+  int order_after_previous(cudaStream_t st, bool* order);
+  int mark_scratch_done(cudaStream_t st, bool order);
   int ensure_scratch(size_t bytes);
   int acquire_slot(size_t bytes, int& slot);
   ~tmd_handle();

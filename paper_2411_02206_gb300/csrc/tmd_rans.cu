@@ -661,6 +661,8 @@ extern "C" int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t
   for (int f = 0; f < kFields; f++) *slots[f] = b + off[f];
   uint32_t* cstatus = reinterpret_cast<uint32_t*>(b + off[kFields]);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool order = false;  // after the previous call's use of the streams and the scratch
+  if ((rc = h->order_after_previous(st, &order)) != TMD_OK) return rc;
   rc = tmd_cuda_check(h, cudaMemsetAsync(cstatus, 0, 4, st), "cudaMemsetAsync");
   if (rc != TMD_OK) return rc;
   rc = tmd_rans_decode(h, coded, coded_bytes, &a, cstatus, stream);
@@ -679,5 +681,7 @@ extern "C" int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t
   rc = tmd_decode_frame(h, &in, out, stream);
   if (rc != TMD_OK) return rc;
   k_status_or<<<1, 1, 0, st>>>(out->status, cstatus);
-  return tmd_cuda_check(h, cudaGetLastError(), "k_status_or launch");
+  rc = tmd_cuda_check(h, cudaGetLastError(), "k_status_or launch");
+  if (rc != TMD_OK) return rc;
+  return h->mark_scratch_done(st, order);
 }

@@ -124,6 +124,27 @@ def test_corrupt_frames_set_status(dec):
         assert gpu[3] == ora[3], f"{name}: status gpu={gpu[3]} oracle={ora[3]}"
 
 
+def test_calls_on_two_streams_share_the_scratch_in_order(dec):
+    """Back-to-back decodes of two frames on two streams with no host
+    synchronisation between them: the second call waits on the device for
+    the first to finish with the handle's scratch, so both are exact."""
+    import torch
+    from paper_2411_02206_gb300 import frames
+    fa = G.oracle_frame(synth.make_truth(n_tracks=1200, n_unatt=40_000, seed=31))
+    fb = G.oracle_frame(synth.make_truth(n_tracks=1100, n_unatt=45_000, seed=32))
+    da, db = frames.to_torch(fa, "cuda:0"), frames.to_torch(fb, "cuda:0")
+    dec.decode(db)  # size the scratch for both beforehand (no reallocation below)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ra = dec.decode(da, stream=s1)
+    rb = dec.decode(db, stream=s2)
+    torch.cuda.synchronize()
+    for r, f, what in ((ra, fa, "first stream"), (rb, fb, "second stream")):
+        got = (r[0].cpu().numpy(), frames.to_numpy(r[1], np.uint32),
+               frames.to_numpy(r[2], np.uint32), int(r[3].item()))
+        G.assert_same_decode(got, O.decode(f), what)
+
+
 def test_batch_equals_single(dec):
     import torch
     from paper_2411_02206_gb300 import frames, tmd
