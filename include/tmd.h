@@ -299,8 +299,9 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *                               the attached-cluster chain (1)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
- *   "rans_variant"   0..2  word refill of the entropy decoder: a branch (0), predicated
- *                          selects (1), a 64-bit word queue topped up per two symbols (2)
+ *   "rans_variant"   0..3  word refill of the entropy decoder: a branch (0), predicated
+ *                          selects (1), a 64-bit word queue topped up per two symbols (2),
+ *                          a branch with a counted word supply (3)
  *   "rans_overlap"   0..1  4-byte streams entropy-decoded on a second stream (1)
  * tmd_autotune times the decode chain on the given frames (device buffers,
  * decoded several times) for each candidate setting, keeps the fastest, and

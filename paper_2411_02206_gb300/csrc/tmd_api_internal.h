@@ -59,7 +59,7 @@ struct tmd_handle {
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 1;        // unattached-decode blocks per SM (0: as many as fit)
   int tune_rans_variant = 0;     // word refill of the entropy decoder (0 branch, 1 predicated,
-                                 // 2 word queue)
+                                 // 2 word queue, 3 branch with a counted word supply)
   int tune_rans_overlap = 1;     // 4-byte streams entropy-decoded on the second stream
   uint64_t mem_budget = 0;
   uint32_t max_slots = 0;

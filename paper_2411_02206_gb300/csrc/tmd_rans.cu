@@ -274,7 +274,10 @@ __device__ uint64_t check_entry(const Job& J, const JobField& F, uint32_t w) {
 // selects and checks the lane's word count once at the end of the stream;
 // V = 2 keeps up to 3 pending words in a 64-bit queue, takes a word with
 // predicated shifts, and tops the queue up from a prefetched pair once per
-// two symbols (a symbol takes at most one word, so the queue never runs dry).
+// two symbols (a symbol takes at most one word, so the queue never runs dry);
+// V = 3 branches like V = 0 but keeps the next word in the low half of cur,
+// moves to the prefetched pair with selects and counts the words taken,
+// checked against the lane's words once at the end of the stream.
 template <int W, int THREADS, int MINB, int V>
 __global__ void __launch_bounds__(THREADS, MINB) k_rans_decode(const __grid_constant__ Job J) {
   using T = typename ValueType<W>::T;
@@ -403,6 +406,36 @@ __global__ void __launch_bounds__(THREADS, MINB) k_rans_decode(const __grid_cons
           out[32ull * k] = (T)v;
         }
         if (2 * j + (half ? 1u : 0u) > 2 * maxp) bad = true;  // read past its words
+      } else if constexpr (V == 3) {
+        bool two = true;    // cur still holds two words
+        uint32_t used = 0;  // words taken
+        uint32_t jn = 2;    // next pair to prefetch
+        const uint32_t* np = P + 64;
+        for (uint32_t k = 0; k < nk; k++) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int p = 0; p < W; p++) {
+            const uint32_t e = s_tab[p * kM + (x & (kM - 1))];
+            x = ((e >> 20) + 1) * (x >> 12) + (e & (kM - 1));
+            v |= ((e >> 12) & 0xFFu) << (8 * p);
+            if (x < kLower) {
+              x = (x << 16) | (cur & 0xFFFFu);
+              used++;
+              if (two) {
+                cur >>= 16;
+              } else {
+                cur = nxt;
+                nxt = jn < maxp ? __ldg(np) : 0u;
+                np += 32;
+                jn++;
+              }
+              two = !two;
+              if (x < kLower) bad = true;
+            }
+          }
+          out[32ull * k] = (T)v;
+        }
+        if (used > 2 * maxp) bad = true;  // read past its words
       } else {
         uint64_t q = 0;     // pending words, the next in bits 0-15
         uint32_t c = 0;     // words in q
@@ -492,8 +525,10 @@ cudaError_t launch_width(const uint8_t* coded, uint64_t bytes, const tmd_frame_a
     blocks += std::max<uint32_t>(1, (F.nch + kT / 32 - 1) / (kT / 32));
   }
   const int smem = W * (int)kM * 4;
-  auto kern = variant == 2 ? k_rans_decode<W, kT, kB, 2>
-                           : (variant ? k_rans_decode<W, kT, kB, 1> : k_rans_decode<W, kT, kB, 0>);
+  auto kern = variant == 3   ? k_rans_decode<W, kT, kB, 3>
+              : variant == 2 ? k_rans_decode<W, kT, kB, 2>
+              : variant == 1 ? k_rans_decode<W, kT, kB, 1>
+                             : k_rans_decode<W, kT, kB, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<blocks, kT, smem, st>>>(J);

@@ -31,7 +31,7 @@ const Param kParams[] = {
     {"unatt_variant", &tmd_handle::tune_unatt_variant, 0, 1},
     {"decode_blocks_per_sm", &tmd_handle::tune_decode_bps, 0, 64},
     {"unatt_blocks_per_sm", &tmd_handle::tune_unatt_bps, 0, 64},
-    {"rans_variant", &tmd_handle::tune_rans_variant, 0, 2},
+    {"rans_variant", &tmd_handle::tune_rans_variant, 0, 3},
     {"rans_overlap", &tmd_handle::tune_rans_overlap, 0, 1},
 };
 

@@ -171,7 +171,7 @@ def test_full_size_pbpb_frame(dec):
         assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("overlap", [0, 1])
 def test_every_decoder_setting(dec, variant, overlap):
     """Every word-refill variant, with and without the second stream, gives
