@@ -449,8 +449,21 @@ def run(args):
     rans_bytes = int(blob.size) + h2d
     rans_gbs = rans_bytes / (rans_ms * 1e-3) / 1e9
     del coded, rdec, c_out
+    # end to end from coded frames in pinned host memory (the form in which
+    # compressed frames cross the host link): one upload of the coded bytes,
+    # entropy + track-model decoding, the native list back, pipelined
+    h_blob = torch.from_numpy(blob.copy()).pin_memory()
+    cframe = tmd.tmd_coded_frame(h_blob.data_ptr(), int(blob.size), nt, na, nu)
+    dec.tmd_decode_coded_host_stream([cframe] * 2, [hout] * 2, stream)
+    barrier()
+    t0 = time.perf_counter()
+    dec.tmd_decode_coded_host_stream([cframe] * e2e_steps, [hout] * e2e_steps, stream)
+    barrier()
+    e2e_coded_dt = time.perf_counter() - t0
+    coded_e2e_ok = int(h_st[0].item()) == 0
     assert torch.equal(h_native, native.cpu()), "host entry point disagrees with device path"
     e2e_value = whole_job_rate(e2e_steps * (na + nu), e2e_dt, native.device)
+    e2e_coded_value = whole_job_rate(e2e_steps * (na + nu), e2e_coded_dt, native.device)
     line = None
     if rank == 0:
         base = cpu_baseline(truth) if not args.no_cpu_baseline else None
@@ -483,7 +496,11 @@ def run(args):
                         "frac_hbm": rans_gbs / peak,
                         "chain_ms_per_frame": chain_ms,
                         "chain_clusters_per_s": (na + nu) / (chain_ms * 1e-3),
-                        "host_encode_s": enc_host_s, "bit_exact": coded_ok, "in_step": False},
+                        "host_encode_s": enc_host_s, "bit_exact": coded_ok, "in_step": False,
+                        "e2e": {"value": e2e_coded_value, "unit": UNIT,
+                                "h2d_bytes_per_step": int(blob.size), "d2h_bytes_per_step": d2h,
+                                "api": "tmd_decode_coded_host_stream", "frames": e2e_steps,
+                                "status_ok": coded_e2e_ok}},
             "top_kernel": top[0],
             "tuning": tuned,
             "cpu_baseline": base,

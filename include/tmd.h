@@ -449,6 +449,25 @@ int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t coded_byte
                            uint32_t n_tracks, uint32_t n_attached, uint32_t n_unattached,
                            const tmd_frame_out* out, void* stream);
 
+/* A coded frame held in HOST memory, for tmd_decode_coded_host_stream. */
+typedef struct tmd_coded_frame {
+  const void* data; /* the coded frame (pinned host memory for overlapped copies) */
+  uint64_t bytes;
+  uint32_t n_tracks, n_attached, n_unattached;
+} tmd_coded_frame;
+
+/* The host streaming pipeline of tmd_decode_host_stream for coded frames, the
+ * form in which the paper's compressed time frames cross the host link
+ * (Sec. 3, Fig. 3): frame i's coded bytes go up in one copy on a copy stream
+ * while earlier frames are entropy-decoded and track-model decoded (as by
+ * tmd_decode_coded_frame) on `stream` and their results come back to out[]
+ * on a second copy stream, through three handle-owned device slots.
+ * Synchronous on return; results equal those of tmd_decode_coded_frame.
+ * Errors: TMD_ERR_ARG (null pointer, n_attached < n_tracks, bytes <
+ * TMD_RANS_HEADER_BYTES), TMD_ERR_NOMEM, TMD_ERR_CUDA. */
+int tmd_decode_coded_host_stream(tmd_handle* h, uint32_t n, const tmd_coded_frame* in,
+                                 const tmd_frame_out* out, void* stream);
+
 /* Instrumentation.  While enabled, every kernel the handle launches is
  * bracketed by CUDA events on its stream.  tmd_profile_read waits for the
  * recorded launches, returns per kernel its name (32-byte slots in

@@ -12,6 +12,10 @@
 // stream.  A slot is refilled only after the results of the frame that last
 // used it have left; with three slots the upload of frame i waits for the
 // download of frame i - 3, so both copy directions stay busy.
+//
+// tmd_decode_coded_host_stream runs the same pipeline for coded frames: one
+// upload of the coded bytes per frame, then entropy decoding and track-model
+// decoding on the compute stream.
 #include <algorithm>
 #include <cstring>
 
@@ -145,6 +149,90 @@ extern "C" int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in,
   return tmd_cuda_check(h, cudaStreamSynchronize(st), "stream synchronize");
 }
 
+namespace {
+
+// Copy streams and slot events of the host pipelines, made on first use.
+int pipe_streams(tmd_handle* h) {
+  if (h->h2d) return TMD_OK;
+  int rc = TMD_OK;
+  if ((rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking),
+                           "stream")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking),
+                           "stream")) != TMD_OK)
+    return rc;
+  for (int s = 0; s < tmd_handle::kPipeSlots; s++)
+    for (cudaEvent_t* e : {&h->pipe_in[s], &h->pipe_dec[s], &h->pipe_out[s]})
+      if ((rc = tmd_cuda_check(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming),
+                               "event")) != TMD_OK)
+        return rc;
+  return TMD_OK;
+}
+
+// Device bytes of one coded frame's slot: the coded bytes, then the outputs.
+size_t coded_slot_bytes(const tmd_coded_frame& c) {
+  const size_t n = (size_t)c.n_attached + c.n_unattached;
+  return up(c.bytes) + up(n * TMD_REC_BYTES) + up(4 * (TMD_NBIN + 1)) + up(4 * TMD_NBIN) + 256;
+}
+
+}  // namespace
+
+extern "C" int tmd_decode_coded_host_stream(tmd_handle* h, uint32_t n, const tmd_coded_frame* in,
+                                            const tmd_frame_out* out, void* stream) {
+  if (!h) return TMD_ERR_ARG;
+  if (n == 0) return TMD_OK;
+  if (!in || !out) return tmd_set_error(h, TMD_ERR_ARG, "null frame arrays");
+  for (uint32_t i = 0; i < n; i++) {
+    if (in[i].n_attached < in[i].n_tracks)
+      return tmd_set_error(h, TMD_ERR_ARG, "frame %u: n_attached < n_tracks", i);
+    if (!in[i].data || in[i].bytes < TMD_RANS_HEADER_BYTES)
+      return tmd_set_error(h, TMD_ERR_ARG, "frame %u: no coded frame", i);
+  }
+  if (cudaSetDevice(h->device) != cudaSuccess) return tmd_set_error(h, TMD_ERR_CUDA, "cudaSetDevice");
+  cudaStream_t comp = static_cast<cudaStream_t>(stream);
+  int rc = pipe_streams(h);
+  if (rc != TMD_OK) return rc;
+  size_t need = 0;
+  for (uint32_t i = 0; i < n; i++) need = std::max(need, coded_slot_bytes(in[i]));
+  const int slots = (int)std::min<uint32_t>(n, tmd_handle::kPipeSlots);
+  for (int s = 0; s < slots; s++)
+    if ((rc = grow(h, &h->pipe_buf[s], &h->pipe_bytes[s], need)) != TMD_OK) return rc;
+  if ((rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_dec[0], comp), "event")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->h2d, h->pipe_dec[0], 0), "wait")) != TMD_OK)
+    return rc;
+  for (uint32_t i = 0; i < n && rc == TMD_OK; i++) {
+    const int s = (int)(i % slots);
+    const tmd_coded_frame& c = in[i];
+    const size_t nrec = (size_t)c.n_attached + c.n_unattached;
+    char* p = static_cast<char*>(h->pipe_buf[s]);
+    tmd_frame_out o;
+    o.native = reinterpret_cast<uint8_t*>(p + up(c.bytes));
+    o.row_start = reinterpret_cast<uint32_t*>(p + up(c.bytes) + up(nrec * TMD_REC_BYTES));
+    o.att_count = o.row_start + up(4 * (TMD_NBIN + 1)) / 4;
+    o.status = o.att_count + up(4 * TMD_NBIN) / 4;
+    tmd_frame_in counts{};
+    counts.n_tracks = c.n_tracks;
+    counts.n_attached = c.n_attached;
+    counts.n_unattached = c.n_unattached;
+    if (i >= (uint32_t)slots)
+      rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->h2d, h->pipe_out[s], 0), "wait");
+    if (rc == TMD_OK)
+      rc = tmd_cuda_check(h, cudaMemcpyAsync(p, c.data, c.bytes, cudaMemcpyHostToDevice, h->h2d),
+                          "H2D copy");
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_in[s], h->h2d), "event");
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(comp, h->pipe_in[s], 0), "wait");
+    if (rc == TMD_OK)
+      rc = tmd_decode_coded_frame(h, p, c.bytes, c.n_tracks, c.n_attached, c.n_unattached, &o,
+                                  comp);
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_dec[s], comp), "event");
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->d2h, h->pipe_dec[s], 0), "wait");
+    if (rc == TMD_OK) rc = fetch_frame(h, &counts, &o, &out[i], h->d2h);
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaEventRecord(h->pipe_out[s], h->d2h), "event");
+  }
+  const int rc2 = tmd_cuda_check(h, cudaStreamSynchronize(h->d2h), "stream synchronize");
+  const int rc3 = tmd_cuda_check(h, cudaStreamSynchronize(comp), "stream synchronize");
+  return rc != TMD_OK ? rc : (rc2 != TMD_OK ? rc2 : rc3);
+}
+
 extern "C" int tmd_decode_host_stream(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
                                       const tmd_frame_out* out, void* stream) {
   if (!h) return TMD_ERR_ARG;
@@ -155,19 +243,8 @@ extern "C" int tmd_decode_host_stream(tmd_handle* h, uint32_t n, const tmd_frame
       return tmd_set_error(h, TMD_ERR_ARG, "frame %u: n_attached < n_tracks", i);
   if (cudaSetDevice(h->device) != cudaSuccess) return tmd_set_error(h, TMD_ERR_CUDA, "cudaSetDevice");
   cudaStream_t comp = static_cast<cudaStream_t>(stream);
-  int rc = TMD_OK;
-  if (!h->h2d) {
-    if ((rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking),
-                             "stream")) != TMD_OK ||
-        (rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking),
-                             "stream")) != TMD_OK)
-      return rc;
-    for (int s = 0; s < tmd_handle::kPipeSlots; s++)
-      for (cudaEvent_t* e : {&h->pipe_in[s], &h->pipe_dec[s], &h->pipe_out[s]})
-        if ((rc = tmd_cuda_check(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming),
-                                 "event")) != TMD_OK)
-          return rc;
-  }
+  int rc = pipe_streams(h);
+  if (rc != TMD_OK) return rc;
   size_t need = 0;
   for (uint32_t i = 0; i < n; i++) need = std::max(need, frame_bytes(&in[i]));
   const int slots = (int)std::min<uint32_t>(n, tmd_handle::kPipeSlots);

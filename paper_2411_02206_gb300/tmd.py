@@ -63,6 +63,11 @@ class tmd_frame_arrays(ctypes.Structure):
     _fields_ = tmd_frame_in._fields_
 
 
+class tmd_coded_frame(ctypes.Structure):
+    _fields_ = [("data", _P), ("bytes", ctypes.c_uint64), ("n_tracks", ctypes.c_uint32),
+                ("n_attached", ctypes.c_uint32), ("n_unattached", ctypes.c_uint32)]
+
+
 class tmd_frame_out(ctypes.Structure):
     _fields_ = [("native", _P), ("row_start", _P), ("att_count", _P), ("status", _P)]
 
@@ -152,6 +157,10 @@ def lib():
                                                  ctypes.c_uint32, ctypes.c_uint32,
                                                  ctypes.POINTER(tmd_frame_out), _P]
             L.tmd_decode_coded_frame.restype = ctypes.c_int
+            L.tmd_decode_coded_host_stream.argtypes = [H, ctypes.c_uint32,
+                                                       ctypes.POINTER(tmd_coded_frame),
+                                                       ctypes.POINTER(tmd_frame_out), _P]
+            L.tmd_decode_coded_host_stream.restype = ctypes.c_int
             L.tmd_last_error_string.argtypes = [H]
             L.tmd_last_error_string.restype = ctypes.c_char_p
             _lib = L
@@ -297,6 +306,13 @@ class Decoder:
         return self._check(self._L.tmd_decode_coded_frame(
             self.h, _P(_ptr(coded)), coded_bytes, n_tracks, n_attached, n_unattached,
             ctypes.byref(fout), _P(_stream_ptr(stream))))
+
+    def tmd_decode_coded_host_stream(self, coded, fouts, stream=None) -> int:
+        n = len(coded)
+        ca = (tmd_coded_frame * n)(*coded)
+        oa = (tmd_frame_out * n)(*fouts)
+        return self._check(self._L.tmd_decode_coded_host_stream(self.h, n, ca, oa,
+                                                                _P(_stream_ptr(stream))))
 
     def tmd_decode_frame_host(self, fin: tmd_frame_in, fout: tmd_frame_out, stream=None) -> int:
         return self._check(self._L.tmd_decode_frame_host(

@@ -193,3 +193,29 @@ def test_every_decoder_setting(dec, variant, overlap):
     finally:
         dec.tmd_tune_set("rans_variant", 0)
         dec.tmd_tune_set("rans_overlap", 1)
+
+
+def test_coded_host_stream_pipeline(dec):
+    """tmd_decode_coded_host_stream over coded frames of different sizes (more
+    frames than device slots, pinned and pageable host memory) gives every
+    frame the oracle's decode."""
+    import torch
+    from paper_2411_02206_gb300 import tmd
+    ofs, coded, outs, keep = [], [], [], []
+    for i, (nt, nu) in enumerate(((900, 20_000), (2500, 5_000), (0, 7_000), (1700, 30_000),
+                                  (300, 0))):
+        of = G.oracle_frame(synth.make_truth(n_tracks=nt, n_unatt=nu, seed=50 + i))
+        blob = tmd.rans_encode(of)
+        host = torch.from_numpy(blob.copy())
+        if i % 2 == 0:
+            host = host.pin_memory()
+        keep.append(host)
+        _, na, nu2 = O.frame_counts(of)
+        coded.append(tmd.tmd_coded_frame(host.data_ptr(), blob.size, *O.frame_counts(of)))
+        o = (np.zeros((na + nu2, 12), np.uint8), np.zeros(5473, np.uint32),
+             np.zeros(5472, np.uint32), np.zeros(1, np.uint32))
+        outs.append(o)
+        ofs.append(of)
+    dec.tmd_decode_coded_host_stream(coded, [tmd.frame_out(*o) for o in outs])
+    for i, (of, o) in enumerate(zip(ofs, outs)):
+        G.assert_same_decode((o[0], o[1], o[2], int(o[3][0])), O.decode(of), f"coded frame {i}")
