@@ -150,11 +150,11 @@ def oracle_frame(truth):
     return f
 
 
-def cpu_baseline(truth, min_seconds=10.0, max_reps=8):
+def cpu_baseline(truth, min_seconds=10.0, max_reps=8, frame=None):
     """The oracle decoder, single-threaded, on this host: the full frame
     decoded repeatedly until min_seconds of CPU work (bounded sample)."""
     from oracle import oracle as O
-    f = oracle_frame(truth)
+    f = oracle_frame(truth) if frame is None else frame
     nt, na, nu = O.frame_counts(f)
     reps, t = 0, 0.0
     while (t < min_seconds and reps < max_reps) or reps == 0:
@@ -165,6 +165,33 @@ def cpu_baseline(truth, min_seconds=10.0, max_reps=8):
     return {"value": reps * (na + nu) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"the full {WORKLOAD} frame ({na + nu} clusters) decoded {reps}x by the "
                       f"serial C oracle, {t:.1f} s"}
+
+
+def cpu_baseline_all_cores(frame, threads=None):
+    """The same serial oracle decoder on every host core at once: one host
+    thread per core, each decoding the whole frame into its own buffers (the
+    C decoder runs outside the interpreter lock), aggregate clusters/s over
+    the wall time of the slowest."""
+    import concurrent.futures as cf
+    from oracle import oracle as O
+    nt, na, nu = O.frame_counts(frame)
+    n = threads or max(1, min(os.cpu_count() or 1, 32))
+    # each thread holds its native list and the decoder's work arrays (about
+    # 20 B per cluster): keep all of them within half of the available memory
+    try:
+        avail = next(int(l.split()[1]) * 1024 for l in open("/proc/meminfo")
+                     if l.startswith("MemAvailable:"))
+        n = max(1, min(n, avail // (2 * 20 * (na + nu) + 1)))
+    except (OSError, StopIteration, ValueError):
+        n = 1
+    O.decode({k: v[:0] if k != "n_unatt" else np.zeros_like(v) for k, v in frame.items()})
+    with cf.ThreadPoolExecutor(max_workers=n) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda _: O.decode(frame)[3], range(n)))
+        dt = time.perf_counter() - t0
+    return {"value": n * (na + nu) / dt, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"the full {WORKLOAD} frame ({na + nu} clusters) decoded once on each "
+                      f"of {n} host threads at the same time, {dt:.1f} s"}
 
 
 def kernel_bytes(name, nt, na, nu):
@@ -466,7 +493,12 @@ def run(args):
     e2e_coded_value = whole_job_rate(e2e_steps * (na + nu), e2e_coded_dt, native.device)
     line = None
     if rank == 0:
-        base = cpu_baseline(truth) if not args.no_cpu_baseline else None
+        base = host_all = None
+        if not args.no_cpu_baseline:
+            oframe = oracle_frame(truth)
+            base = cpu_baseline(truth, frame=oframe)
+            host_all = cpu_baseline_all_cores(oframe)
+            del oframe
         clocks = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -504,6 +536,7 @@ def run(args):
             "top_kernel": top[0],
             "tuning": tuned,
             "cpu_baseline": base,
+            "cpu_baseline_all_cores": host_all,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "api": "tmd_decode_host_stream",
                     "frames": e2e_steps},
