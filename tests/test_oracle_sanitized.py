@@ -1,8 +1,9 @@
 """The oracle under AddressSanitizer and UndefinedBehaviorSanitizer (host
 side, no GPU): a sanitized build decodes, encodes and traces frames of several
 shapes -- empty, tracks only, unattached only, loopers with many legs, corrupt
-counts -- in a child process, and any invalid access or undefined operation
-aborts it."""
+counts -- and entropy-codes and decodes streams and frames, intact, cut short
+and with flipped bytes, in a child process; any invalid access or undefined
+operation aborts it."""
 import os
 import shutil
 import subprocess
@@ -40,6 +41,28 @@ g = dict(f); g["row_diff"] = f["row_diff"].copy(); g["row_diff"][5] = 200
 O.decode(g)  # the row may or may not leave the detector; it must not misbehave
 g = dict(f); g["slice"] = f["slice"].copy(); g["slice"][3] = 77
 assert O.decode(g)[3] & O.ST_ROW
+# entropy coder: round trips, then malformed sections and frames must be
+# rejected without touching memory outside their buffers
+rng = np.random.default_rng(7)
+for dt, n in ((np.uint8, 0), (np.uint8, 8193), (np.uint16, 33), (np.uint32, 2 * 8192 + 5)):
+    v = (rng.geometric(0.02, n) - 1).astype(dt)
+    sec = O.rans_field_encode(v)
+    d, ok = O.rans_field_decode(sec, n, dt)
+    assert ok and np.array_equal(d, v)
+    if n:
+        for cut in (sec.size // 2, 16, 0):
+            O.rans_field_decode(sec[:cut].copy(), n, dt)
+        bad = sec.copy(); bad[512 * dt().itemsize + 3] ^= 0xFF
+        O.rans_field_decode(bad, n, dt)
+blob = O.rans_encode(f)
+nt, na, nu = O.frame_counts(f)
+dec, ok = O.rans_decode(blob, nt, na, nu)
+assert ok and all(np.array_equal(dec[k], f[k]) for k, _, _ in O.FRAME_FIELDS)
+for i in range(0, blob.size, max(1, blob.size // 97)):
+    b = blob.copy(); b[i] ^= 0x5A
+    O.rans_decode(b, nt, na, nu)
+for cut in (O.RANS_HEAD - 1, O.RANS_HEAD + 5, blob.size - 1):
+    O.rans_decode(blob[:cut].copy(), nt, na, nu)
 print("sanitized oracle ok")
 '''
 
