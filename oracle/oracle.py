@@ -7,8 +7,9 @@ imports this module; the CUDA library and the oracle share no code.
 The oracle implements track-model encoding and decoding as described in
 Sec. 3 of arXiv:2411.02206 (attached clusters as residuals to the track model,
 unattached clusters as differences to the preceding cluster of their
-(sector,row) after sorting by position).  Frames are dicts of numpy arrays
-whose keys are the field names of ``FRAME_FIELDS``.
+(sector,row) after sorting by position), the rANS entropy coding of a
+frame's streams, and the global positions of a native list.  Frames are
+dicts of numpy arrays whose keys are the field names of ``FRAME_FIELDS``.
 """
 from __future__ import annotations
 

@@ -15,7 +15,11 @@
  *     position (time, then pad) and stored as differences to the preceding one;
  *   - track-model decoding: the exact inverse of both, producing the native
  *     cluster list grouped by (sector,row), attached clusters first in
- *     (track, cluster) order, then the unattached clusters in stored order.
+ *     (track, cluster) order, then the unattached clusters in stored order;
+ *   - entropy coding of the compressed frame's streams (rANS, Sec. 2-3; the
+ *     format is this project's own, defined with the code below);
+ *   - the global (x, y, z) positions of a native list with the nominal
+ *     geometry (the decoded clusters feed the downstream tracking).
  *
  * The paper does not give the track model (it is in the cited CTD2019
  * proceedings, not available here).  The model below is this project's
