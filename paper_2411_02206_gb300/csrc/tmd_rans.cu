@@ -18,6 +18,7 @@
 // consecutive values per step.  Three launches, one per value width, size
 // blocks and shared memory for their tables (16, 32, 64 KB).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -161,6 +162,35 @@ void encode_chunks(const void* vals, uint32_t n, const Plane* pl, uint32_t c0, u
   }
 }
 
+// Runs fn(t) for t = 0 .. threads-1, fn(0) on the calling thread.  Parts
+// whose thread cannot be started run on the calling thread; every started
+// thread is joined; a part that throws makes run_parts throw std::bad_alloc
+// after all parts have finished (no exception leaves a worker thread).
+template <class Fn>
+void run_parts(unsigned threads, Fn fn) {
+  std::atomic<bool> failed{false};
+  auto part = [&](unsigned t) noexcept {
+    try {
+      fn(t);
+    } catch (...) {
+      failed = true;
+    }
+  };
+  std::vector<std::thread> pool;
+  unsigned started = 1;
+  for (; started < threads; started++) {
+    try {
+      pool.emplace_back(part, started);
+    } catch (...) {
+      break;
+    }
+  }
+  for (unsigned u = started; u < threads; u++) part(u);
+  part(0);
+  for (auto& th : pool) th.join();
+  if (failed) throw std::bad_alloc();
+}
+
 template <int W>
 void encode_stream(const void* vals, uint32_t n, unsigned threads, std::vector<uint8_t>& sec) {
   const uint32_t nch = chunks_of(n);
@@ -175,11 +205,7 @@ void encode_stream(const void* vals, uint32_t n, unsigned threads, std::vector<u
       for (int p = 0; p < W; p++) c[p * 256 + ((v >> (8 * p)) & 0xFFu)]++;
     }
   };
-  std::vector<std::thread> pool;
-  for (unsigned t = 1; t < threads; t++) pool.emplace_back(count, t);
-  count(0);
-  for (auto& th : pool) th.join();
-  pool.clear();
+  run_parts(threads, count);
   Plane pl[W];
   for (int p = 0; p < W; p++) {
     uint64_t sum[256] = {};
@@ -196,9 +222,7 @@ void encode_stream(const void* vals, uint32_t n, unsigned threads, std::vector<u
     encode_chunks<W>(vals, n, pl, (uint32_t)((uint64_t)nch * t / threads),
                      (uint32_t)((uint64_t)nch * (t + 1) / threads), states.data(), pairs);
   };
-  for (unsigned t = 1; t < threads; t++) pool.emplace_back(enc, t);
-  enc(0);
-  for (auto& th : pool) th.join();
+  run_parts(threads, enc);
   // section: freq, states, woff, pad, words
   std::vector<uint32_t> woff(nch + 1, 0);
   for (uint32_t c = 0; c < nch; c++) woff[c + 1] = woff[c] + (uint32_t)pairs[c].size();
@@ -600,7 +624,7 @@ extern "C" int tmd_rans_encode_host(const tmd_frame_in* in, void* out, uint64_t 
       std::memcpy(head + 48 + 32 * f, d32, 16);
       off += sec.size();
     }
-  } catch (const std::bad_alloc&) {
+  } catch (...) {  // allocation failure; nothing may cross the C boundary
     return TMD_ERR_NOMEM;
   }
   std::memcpy(o, head, kHead);

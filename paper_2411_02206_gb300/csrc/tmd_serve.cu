@@ -253,22 +253,42 @@ void TmdServer::run() {
   }
 }
 
+// The handle's server, started on first use; nullptr (with the handle's
+// error set) if its allocation, streams or driver thread cannot be made.
 static TmdServer* server_of(tmd_handle* h) {
   if (h->server) return h->server;
-  TmdServer* s = new TmdServer();
+  TmdServer* s = new (std::nothrow) TmdServer();
+  if (!s) {
+    tmd_set_error(h, TMD_ERR_NOMEM, "server allocation failed");
+    return nullptr;
+  }
   s->h = h;
   cudaSetDevice(h->device);
-  cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
-  cudaStreamCreateWithFlags(&s->compute[0], cudaStreamNonBlocking);
-  cudaStreamCreateWithFlags(&s->compute[1], cudaStreamNonBlocking);
+  if (cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->compute[0], cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->compute[1], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    for (cudaStream_t st : {s->copy, s->compute[0], s->compute[1]})
+      if (st) cudaStreamDestroy(st);
+    delete s;
+    tmd_set_error(h, TMD_ERR_CUDA, "server streams could not be created");
+    return nullptr;
+  }
   // keep freed pool memory resident instead of returning it to the driver
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  try {
+    s->driver = std::thread([s] { s->run(); });
+  } catch (...) {
+    for (cudaStream_t st : {s->copy, s->compute[0], s->compute[1]}) cudaStreamDestroy(st);
+    delete s;
+    tmd_set_error(h, TMD_ERR_NOMEM, "server thread could not be started");
+    return nullptr;
+  }
   h->server = s;
-  s->driver = std::thread([s] { s->run(); });
   return s;
 }
 
@@ -324,6 +344,7 @@ extern "C" int tmd_submit(tmd_handle* h, const tmd_frame_in* in, uint64_t* req_i
     return tmd_set_error(h, TMD_ERR_BUDGET, "frame needs %llu bytes, the budget is %llu",
                          (unsigned long long)bytes, (unsigned long long)h->mem_budget);
   TmdServer* s = server_of(h);
+  if (!s) return TMD_ERR_NOMEM;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     Request r;
