@@ -289,3 +289,36 @@ def test_frame_streams_compress():
         if name in ("time_res", "slice_leg_diff", "flags_a"):
             assert ln < 0.5 * fr[name].nbytes + 2048, (name, ln, fr[name].nbytes)
     assert math.isfinite(blob.size)
+
+
+def test_frame_sections_equal_the_streams_coded_alone():
+    # the frame coder adds only the header and directory: each section is the
+    # stream coded on its own, byte for byte
+    fr = _small_frame()
+    blob = O.rans_encode(fr)
+    for i, (name, dt, _) in enumerate(O.FRAME_FIELDS):
+        o, ln = np.frombuffer(blob[32 + 32 * i: 48 + 32 * i].tobytes(), "<u8")
+        assert np.array_equal(blob[o:o + ln], O.rans_field_encode(fr[name])), name
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_random_mixtures_round_trip(seed):
+    # mixtures of a few distributions, random widths and lengths (chunk
+    # boundaries, partial lanes), decoded by the oracle and by the
+    # independent textbook decoder
+    rng = np.random.default_rng(1000 + seed)
+    dt = [np.uint8, np.uint16, np.uint32][seed % 3]
+    n = int(rng.choice([int(rng.integers(0, 64)), int(rng.integers(8100, 8300)),
+                        int(rng.integers(20_000, 40_000))]))
+    top = np.iinfo(dt).max
+    parts = [rng.geometric(float(rng.uniform(0.001, 0.9)), n) - 1,
+             rng.integers(0, top, n, dtype=np.uint64, endpoint=True),
+             np.full(n, int(rng.integers(0, top)), np.uint64)]
+    pick = rng.integers(0, 3, n)
+    v = np.choose(pick, [np.asarray(p, np.uint64) for p in parts]) & np.uint64(top)
+    v = v.astype(dt)
+    sec = O.rans_field_encode(v)
+    d, ok = O.rans_field_decode(sec, n, dt)
+    assert ok and np.array_equal(d, v)
+    if n <= 9000:
+        assert np.array_equal(_textbook_decode(sec, n, np.dtype(dt).itemsize), v.astype(np.int64))
