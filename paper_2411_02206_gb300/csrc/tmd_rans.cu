@@ -16,7 +16,10 @@
 // interleaved by lane, so a warp's loads of pair j are one 128-byte line).
 // Values are written by the lane at positions 32 k + l: a warp stores 32
 // consecutive values per step.  Three launches, one per value width, size
-// blocks and shared memory for their tables (16, 32, 64 KB).
+// blocks and shared memory for their tables (16, 32, 64 KB); the 4-byte
+// streams run on the handle's second stream beside the others.  The word
+// refill has four forms with identical results (tuning key rans_variant);
+// the branch form is the default, the fastest measured.
 #include <algorithm>
 #include <atomic>
 #include <cstring>
