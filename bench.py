@@ -427,7 +427,7 @@ def run(args):
     d2h = (na + nu) * 12 + 5473 * 4 + 5472 * 4 + 4
     # end to end: the pipelined host entry point over e2e_steps frames (every
     # step copies its inputs up and its native list back; the copies of one
-    # step overlap the decode of its neighbours, Sec. 3 / Fig. 3)
+    # step overlap the decode of its neighbours, Sec. 4 / Fig. 2)
     e2e_steps = max(3, min(args.steps, 64))
     dec.tmd_decode_host_stream([hin] * 2, [hout] * 2, stream)
     barrier()

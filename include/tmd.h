@@ -1,7 +1,7 @@
 /*
  * tmd.h -- C-ABI of the GB300 TPC track-model decoder (libtmd.so).
  *
- * What it computes (arXiv:2411.02206, Sec. 3, "TPC track-model decoding on
+ * What it computes (arXiv:2411.02206, Sec. 4, "TPC track-model decoding on
  * GPU"): after entropy decoding, a compressed time frame stores the clusters
  * attached to tracks as residuals to the track model and the unattached
  * clusters, sorted by position within each (sector,row), as differences to
@@ -157,17 +157,23 @@ typedef struct tmd_track_out {
   uint32_t* status; /* one u32 */
 } tmd_track_out;
 
-/* Create a decoder on cfg->device.  *out receives the handle. */
+/* Create a decoder on cfg->device.  *out receives the handle.  The paper has
+ * no counterpart (its decoder is part of a larger framework); the handle owns
+ * the scratch memory, streams, launch records, tuning and serving state that
+ * the other calls use.  Errors: TMD_ERR_ARG (null pointer, no such device),
+ * TMD_ERR_CUDA, TMD_ERR_NOMEM; *out is NULL on failure. */
 int tmd_create(const tmd_config* cfg, tmd_handle** out);
 
-/* Drain or cancel in-flight served requests and free every buffer the handle
- * owns.  The handle is invalid afterwards. */
+/* Stop serving (requests still queued are dropped, work already on the GPU
+ * is waited for), then free every buffer the handle owns.  The handle is
+ * invalid afterwards; device pointers handed out by tmd_poll become invalid
+ * too.  The paper has no counterpart (handle management). */
 int tmd_destroy(tmd_handle* h);
 
 /* Text of the last error on this handle ("" if none); valid until the next call. */
 const char* tmd_last_error_string(const tmd_handle* h);
 
-/* Decode one frame (Sec. 3), asynchronously on `stream` (a cudaStream_t, or
+/* Decode one frame (Sec. 4), asynchronously on `stream` (a cudaStream_t, or
  * NULL for the legacy default stream).  Inputs and outputs are device
  * buffers borrowed until the stream reaches the end of the decode.  The
  * handle keeps scratch memory sized for the largest frame seen. */
@@ -200,8 +206,8 @@ int tmd_batch_destroy(tmd_batch* b);
 int tmd_decode_frame_host(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_out* out,
                           void* stream);
 
-/* Decode n frames given HOST buffers, pipelined (arXiv:2411.02206, Sec. 3 and
- * Fig. 3: several instances on streams hide the transfers): frame i's inputs
+/* Decode n frames given HOST buffers, pipelined (arXiv:2411.02206, Sec. 4 and
+ * Fig. 2: several instances on streams hide the transfers): frame i's inputs
  * are copied to one of three handle-owned device slots on a copy stream while
  * earlier frames are decoded on `stream` and their native lists, row offsets,
  * attached counts and status are copied back to out[] on a second copy
@@ -254,12 +260,16 @@ int tmd_track_trace(tmd_handle* h, const tmd_frame_in* in, uint32_t n, const uin
                     float* state, void* stream);
 
 /* Track-model encoding of the attached clusters (the synchronous side of
- * Sec. 3), device buffers, asynchronous on `stream`. */
+ * Sec. 4), device buffers, asynchronous on `stream`. */
 int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,
                       void* stream);
 
-/* Serving.  tmd_submit queues a frame and returns at once.  A driver thread
- * admits queued frames in arrival order while the device-memory budget
+/* Serving (continuous batching of frames as they arrive).  The paper has no
+ * counterpart: its decoder runs several instances on streams to overlap the
+ * transfers (Sec. 4, Fig. 2); admission by a memory budget and batching of
+ * the requests in flight is this library's form of that concurrency for a
+ * stream of requests.  tmd_submit queues a frame and returns at once.  A
+ * driver thread admits queued frames in arrival order while the device-memory budget
  * (tmd_config.mem_budget_bytes) and the slot table (tmd_config.max_slots)
  * allow, gives each admitted frame output buffers the handle owns -- and,
  * when the frame is in host memory, copies its streams into device buffers
@@ -271,10 +281,14 @@ int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out
 int tmd_submit(tmd_handle* h, const tmd_frame_in* in, uint64_t* req_id);
 
 /* Wait up to timeout_us for request req_id.  TMD_OK: *out receives device
- * pointers owned by the handle until tmd_release; TMD_PENDING: not done yet. */
+ * pointers owned by the handle until tmd_release; TMD_PENDING: not done yet;
+ * TMD_ERR_STATE: unknown or released id; the request's own error code if it
+ * failed (TMD_ERR_NOMEM, TMD_ERR_CUDA).  No paper counterpart (serving). */
 int tmd_poll(tmd_handle* h, uint64_t req_id, uint32_t timeout_us, tmd_frame_out* out);
 
-/* Free the buffers of a finished request. */
+/* Free the buffers of a finished request (or drop a queued one).
+ * TMD_ERR_STATE while the request is still being copied or decoded, or for an
+ * unknown id.  No paper counterpart (serving). */
 int tmd_release(tmd_handle* h, uint64_t req_id);
 
 /* Tuning.  Parameters change how work is laid out, never results:
@@ -313,7 +327,7 @@ int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in, const tmd_fr
                  void* stream);
 
 /* Global (x, y, z) positions of the clusters of a native list, for the
- * reconstruction downstream of the decoder (arXiv:2411.02206, Sec. 1-2: the
+ * reconstruction downstream of the decoder (arXiv:2411.02206, Sec. 1 and 3: the
  * decoded TPC clusters feed the tracking of the asynchronous chain).  The
  * transform uses the nominal geometry of the synthetic TPC, not calibration
  * maps: a record of bin (s, r) with pad code P and time code T lies at
@@ -335,7 +349,7 @@ int tmd_global_xyz(tmd_handle* h, const uint8_t* native, const uint32_t* row_sta
 
 /* ------------------------------------------------------------------------
  * Entropy-coded frames: the step before track-model decoding
- * (arXiv:2411.02206, Sec. 2-3: the streams of a compressed time frame are
+ * (arXiv:2411.02206, Sec. 1, 3 and 4: the streams of a compressed time frame are
  * entropy coded with rANS, and the entropy decoding feeds the track-model
  * decoding).  The ALICE rANS format is not public; this is the library's own
  * format, range asymmetric numeral systems (J. Duda, arXiv:1311.2540):
@@ -458,7 +472,7 @@ typedef struct tmd_coded_frame {
 
 /* The host streaming pipeline of tmd_decode_host_stream for coded frames, the
  * form in which the paper's compressed time frames cross the host link
- * (Sec. 3, Fig. 3): frame i's coded bytes go up in one copy on a copy stream
+ * (Sec. 4, Fig. 2): frame i's coded bytes go up in one copy on a copy stream
  * while earlier frames are entropy-decoded and track-model decoded (as by
  * tmd_decode_coded_frame) on `stream` and their results come back to out[]
  * on a second copy stream, through three handle-owned device slots.

@@ -5,7 +5,7 @@ CPU-baseline leg of ``bench.py`` are the only callers.  The product path never
 imports this module; the CUDA library and the oracle share no code.
 
 The oracle implements track-model encoding and decoding as described in
-Sec. 3 of arXiv:2411.02206 (attached clusters as residuals to the track model,
+Sec. 4 of arXiv:2411.02206 (attached clusters as residuals to the track model,
 unattached clusters as differences to the preceding cluster of their
 (sector,row) after sorting by position), the rANS entropy coding of a
 frame's streams, and the global positions of a native list.  Frames are

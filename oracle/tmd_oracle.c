@@ -1,13 +1,13 @@
 /*
  * tmd_oracle.c -- plain, serial CPU oracle for TPC track-model encoding and
- * decoding (arXiv:2411.02206, Sec. 3).
+ * decoding (arXiv:2411.02206, Sec. 4).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
  * only the test suite, the smoke check and the CPU-baseline leg of the bench
  * load it.  It shares no source, header, table or helper with the CUDA
  * library; both are written independently from the same format definition.
  *
- * What it computes (Sec. 3):
+ * What it computes (Sec. 4):
  *   - track-model encoding: each attached cluster after the first of its track
  *     is stored as the residual of its quantised pad/time to the prediction of
  *     the track model, which is updated with the cluster after each step;
@@ -16,7 +16,7 @@
  *   - track-model decoding: the exact inverse of both, producing the native
  *     cluster list grouped by (sector,row), attached clusters first in
  *     (track, cluster) order, then the unattached clusters in stored order;
- *   - entropy coding of the compressed frame's streams (rANS, Sec. 2-3; the
+ *   - entropy coding of the compressed frame's streams (rANS, Sec. 1, 3 and 4; the
  *     format is this project's own, defined with the code below);
  *   - the global (x, y, z) positions of a native list with the nominal
  *     geometry (the decoded clusters feed the downstream tracking).
@@ -447,7 +447,7 @@ int tmd_oracle_decode(const OFrame* f, uint8_t* native, uint32_t* row_start,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Encoder (the synchronous side of Sec. 3), used to build test frames     */
+/* Encoder (the synchronous side of Sec. 4), used to build test frames     */
 /* whose decoded result is known: the quantised truth itself.              */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -657,7 +657,7 @@ void tmd_oracle_sector_centres(float* cs, float* sn) {
 /* ------------------------------------------------------------------------ */
 /* Global positions of the clusters of a native list, with the nominal     */
 /* geometry of the synthetic TPC (the decoded clusters feed the tracking of */
-/* the asynchronous chain, Sec. 1-2; real calibration maps are not          */
+/* the asynchronous chain, Sec. 1 and 3; real calibration maps are not          */
 /* available).  Record i of bin (s, r) (row_start[b] <= i < row_start[b+1]) */
 /* with pad code P and time code T:                                         */
 /*   local  x = 85 + r, y = (P/64 - nPads(r)/2) * w(r)  (the model's pad_to_y) */
@@ -691,7 +691,7 @@ void tmd_oracle_default_model(float* out9) { memcpy(out9, &O_DEFAULT_MODEL, size
 
 /* ------------------------------------------------------------------------ */
 /* Entropy coding of a compressed frame: the step before track-model        */
-/* decoding (Sec. 2-3: the CTF's streams are entropy coded with rANS, and   */
+/* decoding (Sec. 1, 3 and 4: the CTF's streams are entropy coded with rANS, and   */
 /* the entropy decoding feeds the track-model decoding).  The ALICE rANS    */
 /* format is not available; this is the project's own format, written from  */
 /* the definition of range asymmetric numeral systems (rANS, J. Duda,       */

@@ -1,5 +1,5 @@
 // tmd_decode.cu -- attached-cluster decoding and encoding (arXiv:2411.02206,
-// Sec. 3: one GPU thread per track; the thread propagates the track through
+// Sec. 4: one GPU thread per track; the thread propagates the track through
 // the TPC and restores each cluster's absolute coordinates from the stored
 // residual and the track prediction).
 //

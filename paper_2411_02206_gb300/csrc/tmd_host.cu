@@ -5,8 +5,8 @@
 // list, row offsets and status back to the host buffers; synchronous.
 //
 // tmd_decode_host_stream: the same for a sequence of frames, pipelined the
-// way Sec. 3 of arXiv:2411.02206 runs several decoding instances on streams
-// to hide the transfers (Fig. 3): kPipeSlots device slots; frame i's inputs
+// way Sec. 4 of arXiv:2411.02206 runs several decoding instances on streams
+// to hide the transfers (Fig. 2): kPipeSlots device slots; frame i's inputs
 // go up on a host-to-device copy stream while earlier frames are decoded on
 // the compute stream and their results come back on a device-to-host copy
 // stream.  A slot is refilled only after the results of the frame that last

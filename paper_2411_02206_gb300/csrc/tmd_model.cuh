@@ -1,7 +1,7 @@
 // tmd_model.cuh -- device track model for TPC track-model encoding/decoding
-// (arXiv:2411.02206, Sec. 3: "every GPU-thread receives one track, it
-// propagates it through the TPC and computes the absolute values of the
-// coordinates using the residuals given in input and the reconstructed track").
+// (arXiv:2411.02206, Sec. 4: the attached-cluster kernel gives each thread one
+// track, carries the track model along it through the TPC and restores each
+// cluster's absolute coordinates from the stored residual and the model).
 //
 // The paper leaves the track model to its reference [rohr-global-track]; this
 // library defines it as a linear Kalman filter in the sector-local frame:

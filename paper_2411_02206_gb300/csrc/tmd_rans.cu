@@ -1,5 +1,5 @@
 // tmd_rans.cu -- entropy coding of compressed frames, the step in front of
-// track-model decoding (arXiv:2411.02206, Sec. 2-3: the CTF's streams are
+// track-model decoding (arXiv:2411.02206, Sec. 1, 3 and 4: the CTF's streams are
 // entropy coded with rANS; the entropy decoding feeds the track-model
 // decoding).  The format is the library's own, defined with its byte layout
 // in include/tmd.h: rANS (J. Duda, arXiv:1311.2540) with a 2^12 probability

@@ -1,6 +1,6 @@
 // tmd_scan.cu -- track preparation and row offsets of the decoder.
 //
-// Track preparation (replaces the CPU-precomputed SoA indices of Sec. 3 of
+// Track preparation (replaces the CPU-precomputed SoA indices of Sec. 4 of
 // arXiv:2411.02206 with device scans): trackStart = exclusive scan of the
 // track lengths, and a decode order with the longest tracks first (bucketed by
 // length), so that warps of the persistent decoder take similar tracks and

@@ -1,5 +1,5 @@
 // tmd_scatter.cu -- native records of the attached clusters (arXiv:2411.02206,
-// Sec. 3: the decoded clusters end up in the native per-(sector,row) list).
+// Sec. 4: the decoded clusters end up in the native per-(sector,row) list).
 //
 // Cluster j of ranking tile t with key b and rank r goes to native index
 //   tileBase[t][b] + r

@@ -1,4 +1,4 @@
-// tmd_unatt.cu -- unattached-cluster decoding (arXiv:2411.02206, Sec. 3: each
+// tmd_unatt.cu -- unattached-cluster decoding (arXiv:2411.02206, Sec. 4: each
 // coordinate is the stored difference plus the coordinate of the previously
 // decoded cluster of the same TPC region).
 //

@@ -1,5 +1,5 @@
 // tmd_xpose.cu -- placement of the attached clusters by a per-sector transpose
-// (arXiv:2411.02206, Sec. 3: the decoded clusters end up in the native
+// (arXiv:2411.02206, Sec. 4: the decoded clusters end up in the native
 // per-(sector,row) list, attached clusters of a row in track order).
 //
 // The native list is the attached clusters sorted stably by (sector, row),

@@ -1,6 +1,6 @@
 // tmd_xyz.cu -- global (x, y, z) positions of the decoded clusters, the
 // transform the downstream reconstruction applies to the native cluster list
-// (arXiv:2411.02206, Sec. 1-2: the decoded TPC clusters feed the tracking of
+// (arXiv:2411.02206, Sec. 1 and 3: the decoded TPC clusters feed the tracking of
 // the asynchronous chain).  The real transform applies calibration maps that
 // are not available; this one uses the nominal geometry of the synthetic TPC:
 //

@@ -1,5 +1,5 @@
 """Seeded synthetic inputs shaped like ALICE TPC time frames, for track-model
-encoding and decoding (arXiv:2411.02206, Sec. 3).
+encoding and decoding (arXiv:2411.02206, Sec. 4).
 
 This module is the one input source shared by the CUDA path, the tests and the
 CPU oracle.  It holds none of the method's arithmetic (no track model, no
