@@ -10,6 +10,10 @@ both sides, max over ranks), the roofline of the dominant kernel measured live
 with per-kernel CUDA events, the end-to-end rate through the host-buffer entry
 point (pinned host copies inside the timed region), the CPU oracle timed on
 this host as a baseline, and the SM clocks sampled during the timed region.
+Beside the step, each with its own clock record: the multi-frame schedule on
+64 frames of 0.5-40 M clusters (64 plain launches vs one batched chain vs one
+graph launch) and serving of a Poisson stream of requests at 80 % of the
+measured batched capacity (p50/p99 latency, sustained clusters/s).
 
 --impl reference times the CPU oracle alone (the reference arm of this
 benchmark) on the same workload and metric.
@@ -19,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -43,12 +48,32 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _config(n_tracks, n_att, n_unatt, seed, note):
-    att = f"{n_att} attached" if n_att is not None else "about 37 M attached"
-    return {"workload": f"{WORKLOAD}: full Pb-Pb-shaped time frame, {n_tracks} tracks of 20-152 "
-                        f"clusters, {att} + {n_unatt} unattached clusters, seed {seed}",
-            "frame_clusters": (n_att + n_unatt) if n_att is not None else None,
-            "n_tracks": n_tracks, "l2": note}
+def _config(scale: float = 1.0):
+    """The workload, named the same way by both arms of the benchmark (the
+    exact cluster counts of the generated frame are in the line's `frame`)."""
+    from paper_2411_02206_gb300 import synth
+    kw = synth.SHAPES[WORKLOAD]
+    nt, nu = int(round(kw["n_tracks"] * scale)), int(round(kw["n_unatt"] * scale))
+    c = {"workload": f"{WORKLOAD}: full Pb-Pb-shaped time frame, {nt} tracks of 20-152 "
+                     f"clusters (about {37.8 * scale:.1f} M attached) + {nu} unattached "
+                     f"clusters, seed {kw['seed']}",
+         "n_tracks": nt, "n_unattached": nu, "seed": kw["seed"],
+         "l2": "inputs (0.9 GB) + outputs (0.7 GB) larger than L2 (129 MB)"}
+    if scale != 1.0:
+        c["scale"] = scale
+    return c
+
+
+def host_cpu() -> str:
+    """Model name of this host's CPU (lscpu), for the CPU baselines."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 def _dist():
@@ -163,6 +188,7 @@ def cpu_baseline(truth, min_seconds=10.0, max_reps=8, frame=None):
         t += time.perf_counter() - t0
         reps += 1
     return {"value": reps * (na + nu) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu": host_cpu(),
             "sample": f"the full {WORKLOAD} frame ({na + nu} clusters) decoded {reps}x by the "
                       f"serial C oracle, {t:.1f} s"}
 
@@ -190,13 +216,33 @@ def cpu_baseline_all_cores(frame, threads=None):
         list(ex.map(lambda _: O.decode(frame)[3], range(n)))
         dt = time.perf_counter() - t0
     return {"value": n * (na + nu) / dt, "unit": UNIT, "cores": n, "kind": "oracle",
-            "sample": f"the full {WORKLOAD} frame ({na + nu} clusters) decoded once on each "
+            "cpu": host_cpu(), "sample": f"the full {WORKLOAD} frame ({na + nu} clusters) decoded once on each "
                       f"of {n} host threads at the same time, {dt:.1f} s"}
 
 
+# Roofline bytes per unit of the path (compressed bytes read + native bytes
+# written): 27 B per attached cluster (15 B of streams + 12 B record), 25 B
+# per unattached cluster (13 + 12), 11 B per track header.
+UNIT_BYTES = {"attached": 27, "unattached": 25, "track": 11}
+# the units each decoder kernel processes
+KERNEL_UNITS = {"k_att_scatter": "attached", "k_track_decode": "attached",
+                "k_count_rank": "attached", "k_key_rank": "attached",
+                "k_unatt_decode": "unattached"}
+
+
 def kernel_bytes(name, nt, na, nu):
-    """Algorithmic bytes of one launch of a decoder kernel (each input byte
-    read once, each output byte written once):
+    """Roofline bytes of one launch of a decoder kernel: the path's bytes per
+    unit (UNIT_BYTES) times the units the launch processes (every attached or
+    every unattached cluster of the frame); None for the small kernels."""
+    kind = KERNEL_UNITS.get(name)
+    if kind is None:
+        return None
+    return UNIT_BYTES[kind] * (na if kind == "attached" else nu)
+
+
+def moved_bytes(name, nt, na, nu):
+    """Bytes a decoder kernel actually reads and writes once (intermediates
+    included, informational):
       k_track_decode  per track a 19 B header (qpt, row, slice, pad, time,
                       ncl, track start, decode order), per cluster after the
                       first of its track 8 B of residual streams; per cluster
@@ -207,27 +253,13 @@ def kernel_bytes(name, nt, na, nu):
       k_count_rank    per attached cluster the 2 B key read and the 2 B rank
                       written, per ranking tile a 2 B count per bin written;
       k_unatt_decode  per unattached cluster 13 B read and 12 B written, the
-                      per-bin counts read;
-      k_xscatter      per attached cluster 15 B read (key, pad code, time
-                      code, 7 B of charges, sigmas and flags) and the 12 B
-                      native record written;
-      k_xcount, k_seg_count, k_seg_runs
-                      per attached cluster the 2 B key read;
-      k_track_keys    per cluster after the first of its track the 2 B of row
-                      and sector/leg differences read, per cluster the 2 B key
-                      written, per track 10 B (row, slice, length, start,
-                      order)."""
+                      per-bin counts read."""
     n_tiles = -(-na // 32768)
     table = {
         "k_track_decode": 8 * (na - nt) + 19 * nt + 8 * na,
         "k_att_scatter": 29 * na,
         "k_count_rank": 4 * na + 2 * 5472 * n_tiles,
         "k_unatt_decode": 25 * nu + 4 * 5472,
-        "k_xscatter": 27 * na,
-        "k_xcount": 2 * na,
-        "k_seg_count": 2 * na,
-        "k_seg_runs": 2 * na,
-        "k_track_keys": 2 * (na - nt) + 2 * na + 10 * nt,
     }
     return table.get(name)
 
@@ -241,25 +273,41 @@ def path_bytes(nt, na, nu):
     return 19 * na + 8 * (na - nt) + 11 * nt + 25 * nu + 4 * 5472 + 4 * 5473
 
 
+KERNEL_SOURCES = {"k_track_decode": ("tmd_decode.cu", "tmd_model.cuh"),
+                  "k_att_scatter": ("tmd_scatter.cu",), "k_count_rank": ("tmd_rank.cu",),
+                  "k_key_rank": ("tmd_rank.cu",), "k_unatt_decode": ("tmd_unatt.cu",)}
+
+
+def source_sha(kernel):
+    """First 12 hex digits of the SHA-1 of the source files of `kernel`: a
+    DRAM-traffic figure measured on other sources does not apply."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES.get(kernel, ()):
+        with open(os.path.join(ROOT, "paper_2411_02206_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def dram_traffic(kernel, tuned, nt, na, nu):
     """DRAM bytes (read + write) of one launch of `kernel` on this workload,
     from the ncu figures committed in profiles/dram_traffic.txt: bytes per
-    unit (attached or unattached cluster) measured on a 0.2-scale frame of
-    the same shape, times this launch's units.  None when the file has no
-    line for the kernel under the current tuning (the kernel changed, or was
-    not captured)."""
+    unit (attached or unattached cluster) measured on a smaller frame of the
+    same shape, times this launch's units.  None when the file has no line
+    for the kernel under the current tuning and the current kernel sources
+    (the kernel changed since the capture, or was not captured)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         f = line.split()
-        if len(f) != 4 or f[0].startswith("#") or f[0] != kernel:
+        if len(f) != 5 or f[0].startswith("#") or f[0] != kernel:
             continue
         key, val = f[1].split("=")
-        if str(tuned.get(key)) != val:
+        if str(tuned.get(key)) != val or f[2] != source_sha(kernel):
             continue
-        units = na if f[2] == "attached" else nu
-        return float(f[3]) * units
+        units = na if f[3] == "attached" else nu
+        return float(f[4]) * units
     return None
 
 
@@ -279,6 +327,9 @@ def _kernel_entry(name, v, prof, nt, na, nu, peak):
     if b:
         e["gbs"] = b / (ms * 1e-3) / 1e9
         e["frac_hbm"] = e["gbs"] / peak
+    m = moved_bytes(name, nt, na, nu)
+    if m:
+        e["moved_gbs"] = m / (ms * 1e-3) / 1e9
     return e
 
 
@@ -317,10 +368,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": _config(full["n_tracks"], None, full["n_unatt"], full["seed"],
-                              "CPU only; per-step sample described in cpu_baseline"),
+            "config": _config(),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "cpu": host_cpu(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -336,6 +386,13 @@ def run(args):
     torch.cuda.set_device(local)
     from paper_2411_02206_gb300 import build, frames, tmd
     build.build()
+    # the frames of the multi-frame and serving legs are generated on the host
+    # cores while the single-frame leg runs (rank 0 only; both legs use one GPU)
+    legs = rank == 0 and args.scale == 1.0
+    bpool = FramePool(batch_specs_c2(args.frames), workers=7) \
+        if legs and not args.no_batch else None
+    spool = FramePool(serve_specs_c3(args.serve_frames), workers=7) \
+        if legs and not args.no_serve else None
     dec = tmd.Decoder(local)
     truth, seed = make_inputs(seed_offset=rank, scale=args.scale)
     dev_truth = frames.to_torch(truth, f"cuda:{local}")
@@ -354,11 +411,7 @@ def run(args):
     if not args.no_autotune:
         dec.tmd_autotune([fin], [fout], stream)
     _apply_tune(dec, args.tune)
-    tuned = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
-                                              "scatter_variant", "overlap", "unatt_variant",
-                                              "place", "prekey", "decode_blocks_per_sm",
-                                              "unatt_blocks_per_sm", "rans_variant",
-                                              "rans_overlap")}
+    tuned = {k: dec.tmd_tune_get(k) for k in tmd.tune_keys()}
     for _ in range(args.warmup):
         dec.tmd_decode_frame(fin, fout, stream)
     torch.cuda.synchronize()
@@ -428,7 +481,7 @@ def run(args):
     # end to end: the pipelined host entry point over e2e_steps frames (every
     # step copies its inputs up and its native list back; the copies of one
     # step overlap the decode of its neighbours, Sec. 4 / Fig. 2)
-    e2e_steps = max(3, min(args.steps, 64))
+    e2e_steps = 48  # enough frames that the pipeline's fill and drain are amortised
     dec.tmd_decode_host_stream([hin] * 2, [hout] * 2, stream)
     barrier()
     t0 = time.perf_counter()
@@ -491,6 +544,19 @@ def run(args):
     assert torch.equal(h_native, native.cpu()), "host entry point disagrees with device path"
     e2e_value = whole_job_rate(e2e_steps * (na + nu), e2e_dt, native.device)
     e2e_coded_value = whole_job_rate(e2e_steps * (na + nu), e2e_coded_dt, native.device)
+    # the multi-frame schedule and serving legs (rank 0; frames generated on
+    # the host cores since the start)
+    batch = serve = None
+    if bpool is not None or spool is not None:
+        del xyz
+        torch.cuda.empty_cache()
+    if bpool is not None:
+        batch = batch_leg(dec, bpool.frames(dec, f"cuda:{local}"), args.steps, f"cuda:{local}",
+                          local)
+        torch.cuda.empty_cache()
+    if spool is not None:
+        serve = serve_leg(dec, spool.frames(dec, f"cuda:{local}"), args.requests, local, local)
+        torch.cuda.empty_cache()
     line = None
     if rank == 0:
         base = host_all = None
@@ -505,8 +571,8 @@ def run(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": _config(nt, na, nu, seed,
-                              "inputs (0.9 GB) + outputs (0.7 GB) larger than L2 (129 MB)"),
+            "config": _config(args.scale),
+            "frame": {"n_tracks": nt, "n_attached": na, "n_unattached": nu, "seed": seed},
             "roofline": {"bound": "hbm", "kernel": dk_name, "achieved": achieved,
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -542,6 +608,8 @@ def run(args):
                     "frames": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks,
+            "batch": batch,
+            "serve": serve,
         }
         if base:
             line["cores_replaced"] = value / base["value"]
@@ -557,20 +625,29 @@ def _gen(kw):
     return synth.make_truth(**kw)
 
 
-def _make_frames(dec, specs, device):
-    """Generate truths in a spawn-started process pool, encode them on the GPU."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    from paper_2411_02206_gb300 import frames
-    workers = max(1, min(len(specs), (os.cpu_count() or 4) - 1))
-    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
-        truths = list(ex.map(_gen, specs))
-    out = []
-    for tr in truths:
-        dev = frames.to_torch(tr, device)
-        enc = dec.encode(dev)
-        out.append(frames.assemble(dev, enc))
-    return out
+class FramePool:
+    """Truths of many frames generated in a spawn-started process pool (the
+    generator is plain numpy, one frame per task), started before the GPU work
+    so that generation overlaps it; `frames()` encodes them on the GPU as they
+    arrive and keeps only the device frames."""
+
+    def __init__(self, specs, workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.specs = specs
+        n = workers or max(1, min(len(specs), (os.cpu_count() or 4) - 1))
+        self.ex = cf.ProcessPoolExecutor(n, mp_context=mp.get_context("spawn"))
+        self.futs = [self.ex.submit(_gen, kw) for kw in specs]
+
+    def frames(self, dec, device):
+        from paper_2411_02206_gb300 import frames
+        out = []
+        for fut in self.futs:
+            dev = frames.to_torch(fut.result(), device)
+            enc = dec.encode(dev)
+            out.append(frames.assemble(dev, enc))
+        self.ex.shutdown()
+        return out
 
 
 def _alloc_out(tmd, torch, frame, device):
@@ -581,27 +658,22 @@ def _alloc_out(tmd, torch, frame, device):
             torch.empty(1, dtype=torch.int32, device=device))
 
 
-def run_batch(args):
-    """64 frames of log-uniform size (0.5-40 M clusters, pp-like to Pb-Pb-like
-    mixes): 64 plain tmd_decode_frame calls vs one tmd_decode_batch call vs
-    one graph launch of a planned batch, on the same resident frames."""
+def batch_leg(dec, frs, steps, device, clock_index):
+    """The multi-frame schedule (64 frames of log-uniform 0.5-40 M clusters,
+    pp-like to Pb-Pb-like mixes, seeds 1000+i): 64 plain tmd_decode_frame
+    calls vs one tmd_decode_batch call vs one graph launch of a planned batch,
+    on the same resident frames; results must be identical to the plain
+    launches (which the GPU tests pin to the oracle)."""
     import torch
-    from paper_2411_02206_gb300 import build, synth, tmd
-    build.build()
-    dev = "cuda:0"
-    dec = tmd.Decoder(0)
-    specs = synth.batch_specs(n_frames=args.frames)
-    frs = _make_frames(dec, specs, dev)
-    outs = [_alloc_out(tmd, torch, f, dev) for f in frs]
+    from paper_2411_02206_gb300 import tmd
+    outs = [_alloc_out(tmd, torch, f, device) for f in frs]
     fins = [tmd.frame_in(f) for f in frs]
     fouts = [tmd.frame_out(*o) for o in outs]
     total = sum(sum(tmd.counts(f)[1:]) for f in frs)
     stream = torch.cuda.current_stream()
-    if not args.no_autotune:
-        dec.tmd_autotune(fins[:8], fouts[:8], stream)
-    _apply_tune(dec, args.tune)
+    reps = max(3, min(steps, 20))
 
-    def timeit(fn, reps):
+    def timeit(fn):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -614,44 +686,41 @@ def run_batch(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    t_plain = timeit(lambda: [dec.tmd_decode_frame(fi, fo, stream) for fi, fo in zip(fins, fouts)],
-                     args.steps)
-    ref = [o[0].clone() for o in outs]
-    t_batch = timeit(lambda: dec.tmd_decode_batch(fins, fouts, stream), args.steps)
-    same_b = all(torch.equal(r, o[0]) for r, o in zip(ref, outs))
     bh = dec.tmd_batch_create(fins, fouts)
-    t_graph = timeit(lambda: dec.tmd_batch_launch(bh, stream), args.steps)
-    same_g = all(torch.equal(r, o[0]) for r, o in zip(ref, outs))
+    with ClockSampler(clock_index) as clk:
+        t_plain = timeit(lambda: [dec.tmd_decode_frame(fi, fo, stream)
+                                  for fi, fo in zip(fins, fouts)])
+        ref = [o[0].clone() for o in outs]
+        t_batch = timeit(lambda: dec.tmd_decode_batch(fins, fouts, stream))
+        same_b = all(torch.equal(r, o[0]) for r, o in zip(ref, outs))
+        t_graph = timeit(lambda: dec.tmd_batch_launch(bh, stream))
+        same_g = all(torch.equal(r, o[0]) for r, o in zip(ref, outs))
     dec.tmd_batch_destroy(bh)
     ok = all(int(o[3].item()) == 0 for o in outs)
-    line = {"workload": f"batch of {len(frs)} frames, {total} clusters "
-                        "(log-uniform 0.5-40 M per frame, seeds 1000+i)",
-            "metric": METRIC, "unit": UNIT, "steps": args.steps,
+    del outs, ref
+    return {"workload": f"batch of {len(frs)} frames, {total} clusters (log-uniform "
+                        "0.5-40 M per frame, pp-like to Pb-Pb-like mixes, seeds 1000+i)",
+            "frames": len(frs), "clusters": total, "reps": reps,
             "plain_launches": {"value": total / (t_plain * 1e-3), "ms": t_plain},
             "batched_chain": {"value": total / (t_batch * 1e-3), "ms": t_batch},
             "graph_launch": {"value": total / (t_graph * 1e-3), "ms": t_graph},
-            "identical_to_plain": bool(same_b and same_g), "status_ok": ok}
-    print(json.dumps(line), flush=True)
-    dec.close()
-    return 0
+            "speedup_vs_plain": t_plain / min(t_batch, t_graph),
+            "identical_to_plain": bool(same_b and same_g), "status_ok": ok,
+            "clocks": clk.summary()}
 
 
-def run_serve(args):
-    """Poisson stream of requests (frames drawn with replacement from a pool
-    of seeded frames, log-uniform 1e5-5e7 clusters) at a rate of 80 % of the
-    measured batched capacity; p50/p99 latency from submit to observed
-    completion, and sustained clusters/s."""
+def serve_leg(dec, frs, n_req, device, clock_index, load=0.8):
+    """Serving: a Poisson stream of n_req requests (frames drawn with
+    replacement from a pool of seeded frames, log-uniform 1e5-5e7 clusters,
+    seeds 5000+i) at `load` times the measured batched capacity, memory
+    budget 120 GB.  Latency from submission to the poller seeing the result
+    done; p50/p99 and sustained clusters/s over the whole stream."""
     import random
     import threading
     import torch
-    from paper_2411_02206_gb300 import build, synth, tmd
-    build.build()
-    dev = "cuda:0"
-    dec = tmd.Decoder(0)
-    specs = synth.batch_specs(n_frames=args.frames, seed=5000, lo=1e5, hi=5e7)
-    frs = _make_frames(dec, specs, dev)
+    from paper_2411_02206_gb300 import tmd
     sizes = [sum(tmd.counts(f)[1:]) for f in frs]
-    outs = [_alloc_out(tmd, torch, f, dev) for f in frs]
+    outs = [_alloc_out(tmd, torch, f, device) for f in frs]
     fins = [tmd.frame_in(f) for f in frs]
     fouts = [tmd.frame_out(*o) for o in outs]
     stream = torch.cuda.current_stream()
@@ -665,18 +734,18 @@ def run_serve(args):
         dec.tmd_decode_batch(fins, fouts, stream)
     b.record(stream)
     torch.cuda.synchronize()
+    del outs
     capacity = 3 * sum(sizes) / (a.elapsed_time(b) * 1e-3)   # clusters/s
-    srv = tmd.Decoder(0, mem_budget_bytes=120 << 30, max_slots=256)
+    srv = tmd.Decoder(device if isinstance(device, int) else torch.cuda.current_device(),
+                      mem_budget_bytes=120 << 30, max_slots=256)
     rng = random.Random(7)
-    n_req = args.requests
     picks = [rng.randrange(len(frs)) for _ in range(n_req)]
     mean = sum(sizes[i] for i in picks) / n_req
-    rate = 0.8 * capacity / mean                               # requests/s
+    rate = load * capacity / mean                              # requests/s
     submitted = {}
     lat = []
     done_clusters = 0
     lock = threading.Lock()
-    finished = threading.Event()
 
     def poller():
         nonlocal done_clusters
@@ -697,33 +766,65 @@ def run_serve(args):
                 pending.pop(0)
 
     th = threading.Thread(target=poller)
-    th.start()
-    t_start = time.perf_counter()
-    t_next = t_start
-    for i, k in enumerate(picks):
-        t_next += rng.expovariate(rate)
-        while True:
-            gap = t_next - time.perf_counter()
-            if gap <= 0:
-                break
-            time.sleep(gap if gap > 0.0005 else 0)
-        t0 = time.perf_counter()
-        rid = srv.tmd_submit(fins[k])
-        with lock:
-            submitted[i] = (rid, t0, sizes[k])
-    finished.set()
-    th.join()
-    wall = time.perf_counter() - t_start
-    lat.sort()
-    line = {"workload": f"serving: Poisson stream of {n_req} frames drawn from {len(frs)} "
-                        "seeded frames (log-uniform 1e5-5e7 clusters), budget 120 GB",
-            "metric": METRIC, "unit": UNIT, "offered_rate_req_s": rate,
-            "batched_capacity": capacity,
-            "sustained": done_clusters / wall,
-            "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[int(len(lat) * 0.99) - 1],
-            "mean_frame_clusters": mean}
-    print(json.dumps(line), flush=True)
+    with ClockSampler(clock_index) as clk:
+        th.start()
+        t_start = time.perf_counter()
+        t_next = t_start
+        for i, k in enumerate(picks):
+            t_next += rng.expovariate(rate)
+            while True:
+                gap = t_next - time.perf_counter()
+                if gap <= 0:
+                    break
+                time.sleep(gap if gap > 0.0005 else 0)
+            t0 = time.perf_counter()
+            rid = srv.tmd_submit(fins[k])
+            with lock:
+                submitted[i] = (rid, t0, sizes[k])
+        th.join()
+        wall = time.perf_counter() - t_start
     srv.close()
+    lat.sort()
+    return {"workload": f"serving: Poisson stream of {n_req} requests drawn from {len(frs)} "
+                        "seeded frames (log-uniform 1e5-5e7 clusters, seeds 5000+i), "
+                        "budget 120 GB",
+            "requests": n_req, "load": load, "offered_rate_req_s": rate,
+            "batched_capacity": capacity, "sustained": done_clusters / wall,
+            "unit": UNIT, "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[max(0, int(len(lat) * 0.99) - 1)],
+            "mean_frame_clusters": mean, "clocks": clk.summary()}
+
+
+def batch_specs_c2(n):
+    from paper_2411_02206_gb300 import synth
+    return synth.batch_specs(n_frames=n)
+
+
+def serve_specs_c3(n):
+    from paper_2411_02206_gb300 import synth
+    return synth.batch_specs(n_frames=n, seed=5000, lo=1e5, hi=5e7)
+
+
+def run_batch(args):
+    import torch
+    from paper_2411_02206_gb300 import build, tmd
+    build.build()
+    pool = FramePool(batch_specs_c2(args.frames))
+    dec = tmd.Decoder(0)
+    frs = pool.frames(dec, "cuda:0")
+    print(json.dumps(batch_leg(dec, frs, args.steps, "cuda:0", 0)), flush=True)
+    dec.close()
+    return 0
+
+
+def run_serve(args):
+    import torch
+    from paper_2411_02206_gb300 import build, tmd
+    build.build()
+    pool = FramePool(serve_specs_c3(args.serve_frames))
+    dec = tmd.Decoder(0)
+    frs = pool.frames(dec, "cuda:0")
+    print(json.dumps(serve_leg(dec, frs, args.requests, 0, 0)), flush=True)
     dec.close()
     return 0
 
@@ -738,6 +839,10 @@ def main():
                     help="frame: the bench line; batch / serve: extra measurements")
     ap.add_argument("--frames", type=int, default=64)
     ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--serve-frames", type=int, default=24,
+                    help="pool of seeded frames the serving requests are drawn from")
+    ap.add_argument("--no-batch", action="store_true", help="skip the multi-frame leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune", action="append", metavar="KEY=VALUE",

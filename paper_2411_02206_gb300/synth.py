@@ -266,14 +266,17 @@ def shape_truth(name: str, scale: float = 1.0, seed: int | None = None) -> dict:
     return make_truth(**kw)
 
 
-def batch_specs(n_frames: int = 64, seed: int = 1000, lo: float = 0.5e6, hi: float = 40e6):
-    """Keyword sets for make_truth: total clusters log-uniform in [lo, hi] and
-    a mix from pp-like (few tracks, mostly unattached) to central Pb-Pb (many
-    long tracks)."""
+def batch_specs(n_frames: int = 64, seed: int = 1000, lo: float = 0.5e6, hi: float = 40e6,
+                totals=None):
+    """Keyword sets for make_truth: total clusters log-uniform in [lo, hi] (or
+    the given list of totals) and a mix from pp-like (few tracks, mostly
+    unattached) to central Pb-Pb (many long tracks)."""
     rng = np.random.default_rng(seed)
     out = []
-    for i in range(n_frames):
+    for i in range(n_frames if totals is None else len(totals)):
         total = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+        if totals is not None:
+            total = float(totals[i])
         dense = rng.uniform(0.0, 1.0)  # 0: pp-like, 1: central Pb-Pb
         att_share = 0.25 + 0.4 * dense
         n_tracks = max(1, int(total * att_share / (60 + 30 * dense)))

@@ -42,6 +42,15 @@ FRAME_FIELDS = [
     ("sigma_time_u", 1, "unatt"),
 ]
 TRUTH_FIELDS = ["qpt", "ncl", "row", "sector", "leg", "pad", "time"]
+# tuning parameters of tmd_tune_set / tmd_tune_get (include/tmd.h)
+TUNE_KEYS = ("decode_variant", "rank_variant", "scatter_variant", "overlap", "unatt_variant",
+             "place", "prekey", "decode_blocks_per_sm", "unatt_blocks_per_sm", "rans_variant",
+             "rans_overlap")
+
+
+def tune_keys() -> tuple:
+    """Names of the library's tuning parameters."""
+    return TUNE_KEYS
 TRACK_OUT_FIELDS = ["qpt", "row", "slice", "pad", "time", "ncl", "row_diff", "slice_leg_diff",
                     "pad_res", "time_res", "status"]
 
