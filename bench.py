@@ -226,8 +226,7 @@ def cpu_baseline_all_cores(frame, threads=None):
 UNIT_BYTES = {"attached": 27, "unattached": 25, "track": 11}
 # the units each decoder kernel processes
 KERNEL_UNITS = {"k_att_scatter": "attached", "k_track_decode": "attached",
-                "k_count_rank": "attached", "k_key_rank": "attached",
-                "k_unatt_decode": "unattached"}
+                "k_key_rank": "attached", "k_unatt_decode": "unattached"}
 
 
 def kernel_bytes(name, nt, na, nu):
@@ -246,19 +245,22 @@ def moved_bytes(name, nt, na, nu):
       k_track_decode  per track a 19 B header (qpt, row, slice, pad, time,
                       ncl, track start, decode order), per cluster after the
                       first of its track 8 B of residual streams; per cluster
-                      8 B written (key, pad code, time code);
+                      6 B written (pad code, time code);
+      k_key_rank      per cluster after the first of its track 2 B of row and
+                      sector differences read, per cluster the 2 B key written
+                      and read back and the 2 B rank written, the head bitmap
+                      (1 bit per cluster), per ranking tile a 2 B count per
+                      bin written;
       k_att_scatter   per attached cluster 17 B read (key, rank, pad code,
                       time code, 7 B of charges, sigmas and flags) and the
                       12 B native record written;
-      k_count_rank    per attached cluster the 2 B key read and the 2 B rank
-                      written, per ranking tile a 2 B count per bin written;
       k_unatt_decode  per unattached cluster 13 B read and 12 B written, the
                       per-bin counts read."""
     n_tiles = -(-na // 32768)
     table = {
-        "k_track_decode": 8 * (na - nt) + 19 * nt + 8 * na,
+        "k_track_decode": 8 * (na - nt) + 19 * nt + 6 * na,
         "k_att_scatter": 29 * na,
-        "k_count_rank": 4 * na + 2 * 5472 * n_tiles,
+        "k_key_rank": 2 * (na - nt) + 6 * na + na // 8 + 2 * 5472 * n_tiles,
         "k_unatt_decode": 25 * nu + 4 * 5472,
     }
     return table.get(name)
@@ -274,7 +276,7 @@ def path_bytes(nt, na, nu):
 
 
 KERNEL_SOURCES = {"k_track_decode": ("tmd_decode.cu", "tmd_model.cuh"),
-                  "k_att_scatter": ("tmd_scatter.cu",), "k_count_rank": ("tmd_rank.cu",),
+                  "k_att_scatter": ("tmd_scatter.cu",),
                   "k_key_rank": ("tmd_rank.cu",), "k_unatt_decode": ("tmd_unatt.cu",)}
 
 

@@ -292,30 +292,20 @@ int tmd_poll(tmd_handle* h, uint64_t req_id, uint32_t timeout_us, tmd_frame_out*
 int tmd_release(tmd_handle* h, uint64_t req_id);
 
 /* Tuning.  Parameters change how work is laid out, never results:
- *   "decode_variant"      0..3  staging of the track decoder: rounds of 32 or
- *                               16 model steps staged synchronously (0, 1), or
- *                               rounds of 8 or 16 steps double-buffered with
- *                               asynchronous copies (2, 3)
- *   "rank_variant"        0..2  ranking of equal keys: match.any on every
- *                               step (0) or only on steps with repeated keys,
- *                               found with a shared-memory bitmap per step (1)
- *                               or per group of 8 steps (2)
- *   "scatter_variant"     0..3  stores of the record scatter: one record per
- *                               thread (0), three lanes per record in one
- *                               store instruction (1; 3: with 2 instead of 4
- *                               clusters per thread), or a whole ranking tile
- *                               regrouped in (bin, rank) order through
- *                               distributed shared memory first (2)
+ *   "decode_variant"      0..1  staging of the track decoder: rounds of 16 (0)
+ *                               or 8 (1) model steps, each lane's next round
+ *                               copied asynchronously while it runs the current
+ *   "scatter_variant"     0..1  stores of the record scatter: one record per
+ *                               thread (0), or three lanes per record in one
+ *                               store instruction (1)
  *   "unatt_variant"       0..1  record write-out of the unattached decoder:
  *                               word by word (0) or one staged 16-byte
  *                               {record, index} entry per thread (1)
- *   "overlap"             0..1  unattached decoder on a second stream beside
- *                               the attached-cluster chain (1)
+ *   "overlap"             0..2  unattached decoder on a second stream: no (0),
+ *                               beside the track decoder and the scatter (1),
+ *                               beside the scatter (2)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
- *   "rans_variant"   0..3  word refill of the entropy decoder: a branch (0), predicated
- *                          selects (1), a 64-bit word queue topped up per two symbols (2),
- *                          a branch with a counted word supply (3)
  *   "rans_overlap"   0..1  4-byte streams entropy-decoded on a second stream (1)
  * tmd_autotune times the decode chain on the given frames (device buffers,
  * decoded several times) for each candidate setting, keeps the fastest, and

@@ -104,19 +104,16 @@ int tmd_validate_frame(tmd_handle* h, const tmd_frame_in* in, const tmd_frame_ou
 }
 
 void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
-                FrameLayout& L, bool xpose) {
+                FrameLayout& L) {
   L.n_tblocks = ceil_div(nt, kTrackBlk);
   L.n_tiles = ceil_div(na, kTile);
   L.n_groups = ceil_div(L.n_tiles, kGroup);
   L.n_chunks = ceil_div(nu, kChunk);
-  L.n_sblk = xpose ? ceil_div(na, kSegBlk) : 0u;
-  // every sector's last tile may be partial: at most kNSec tiles more than the
-  // attached clusters fill
-  L.n_xtiles = xpose && na ? ceil_div(na, kXT) + kNSec : 0u;
   auto z = [&](size_t bytes) { size_t o = zoff; zoff = align_up(zoff + bytes, 256); return o; };
   auto p = [&](size_t bytes) { size_t o = poff; poff = align_up(poff + bytes, 256); return o; };
   L.z_len = z((size_t)kLenBuckets * 4);
   L.z_lb = z((size_t)L.n_chunks * 8 + 8);
+  L.z_heads = z(((size_t)na + 31) / 32 * 4 + 4);
   L.track_start = p(((size_t)nt + 1) * 4);
   L.order = p((size_t)nt * 4 + 4);
   L.keys = p((size_t)na * 2 + 16);
@@ -129,15 +126,6 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
   L.unatt_start = p(((size_t)kNBin + 1) * 4);
   L.blk_sum = p((size_t)L.n_tblocks * 4 + 4);
   L.att_count = p((size_t)kNBin * 4);
-  L.seg_cnt = L.seg_tot = L.runs = L.xt_whist = L.xt_hist = L.xt_base = 0;
-  if (xpose) {
-    L.seg_cnt = p((size_t)2 * kNSec * L.n_sblk * 4 + 4);
-    L.seg_tot = p((size_t)2 * kNSec * 4);
-    L.runs = p((size_t)na * 8 + 8);  // a run starts at a cluster: at most na runs
-    L.xt_whist = p((size_t)L.n_xtiles * kXWarps * kNRow * 2 + 4);
-    L.xt_hist = p((size_t)L.n_xtiles * kNRow * 2 + 4);
-    L.xt_base = p((size_t)L.n_xtiles * kNRow * 4 + 4);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -253,21 +241,16 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->scratch_done, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, prepare_count_rank(), "smem attribute")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, prepare_att_scatter(), "smem attribute")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, prepare_xscatter(), "smem attribute")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, prepare_key_rank(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(0, &h->occ_decode_v[0]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, occupancy_track_decode(2, &h->occ_decode_v[2]), "occupancy")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, occupancy_track_decode(3, &h->occ_decode_v[3]), "occupancy")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, occupancy_track_decode(4, &h->occ_decode_v[4]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_unatt_decode(&h->occ_unatt), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                   &h->occ_encode, k_track_encode, 256, 0), "occupancy")) != TMD_OK) {
     delete h;
     return rc;
   }
-  for (int v = 0; v < 5; v++)
+  for (int v = 0; v < 2; v++)
     if (h->occ_decode_v[v] < 1) h->occ_decode_v[v] = 1;
   h->occ_decode = h->occ_decode_v[h->tune_decode_variant];
   if (!h->autotune_cache.empty()) tmd_tune_load(h);
@@ -293,10 +276,9 @@ extern "C" const char* tmd_last_error_string(const tmd_handle* h) {
 // instrumentation
 // ---------------------------------------------------------------------------
 static const char* kKernelNames[kKNum] = {
-    "k_put_record", "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2", "k_track_decode",
-    "k_count_rank", "k_group_sum", "k_row_offsets", "k_tile_base", "k_att_scatter",
-    "k_unatt_decode", "k_track_encode", "k_seg_count", "k_seg_scan", "k_seg_runs", "k_xcount",
-    "k_xrow_offsets", "k_xbase", "k_xscatter", "k_track_keys", "k_chunk_order"};
+    "k_put_record", "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2",
+    "k_track_decode", "k_key_rank", "k_group_sum", "k_row_offsets", "k_tile_base",
+    "k_att_scatter", "k_unatt_decode", "k_track_encode"};
 
 cudaEvent_t TmdProfile::get() {
   if (pool.empty()) {
@@ -374,7 +356,7 @@ struct RecordLayout {
 static RecordLayout record_layout(uint32_t n, bool enc) {
   RecordLayout r;
   r.pre = 0;
-  r.frames = align_up(9 * ((size_t)n + 1) * 4, 64);
+  r.frames = align_up(6 * ((size_t)n + 1) * 4, 64);
   r.enc = align_up(r.frames + (size_t)n * sizeof(FrameDev), 64);
   r.bytes = align_up(r.enc + (enc ? (size_t)n * sizeof(EncDev) : 0), 64);
   r.counters_unused = 0;
@@ -420,7 +402,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   tmd_handle::Slot& S = h->slots[slot];
   bool order = false;
   if ((rc = h->order_after_previous(st, &order)) != TMD_OK) return rc;
-  const bool two = (h->tune_overlap || h->tune_prekey) && !tin;
+  const bool two = h->tune_overlap && !tin;
   rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on,
                    two ? h->aux : nullptr, h->fork, h->join, trace);
   if (rc != TMD_OK) return rc;
@@ -449,13 +431,9 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   uint32_t* pre_warp = pre + 3 * (nf + 1);
   uint32_t* pre_chunk = pre + 4 * (nf + 1);
   uint32_t* pre_kt = pre + 5 * (nf + 1);
-  uint32_t* pre_sblk = pre + 6 * (nf + 1);
-  uint32_t* pre_xtile = pre + 7 * (nf + 1);
-  uint32_t* pre_kblk = pre + 8 * (nf + 1);
   FrameDev* fd = reinterpret_cast<FrameDev*>(host + R.frames);
   EncDev* ed = reinterpret_cast<EncDev*>(host + R.enc);
   pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = pre_kt[0] = 0;
-  pre_sblk[0] = pre_xtile[0] = pre_kblk[0] = 0;
   uint32_t* zero_bins = reinterpret_cast<uint32_t*>(zb + 256);
   for (uint32_t f = 0; f < nf; f++) {
     FrameDev& F = fd[f];
@@ -493,18 +471,9 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     }
     F.n_tblocks = l.n_tblocks; F.n_tiles = l.n_tiles; F.n_groups = l.n_groups;
     F.n_chunks = l.n_chunks;
-    F.n_sblk = l.n_sblk;
-    F.n_xtiles = l.n_xtiles;
-    if (l.seg_tot) {
-      F.seg_cnt = reinterpret_cast<uint32_t*>(pb + l.seg_cnt);
-      F.seg_tot = reinterpret_cast<uint32_t*>(pb + l.seg_tot);
-      F.runs = reinterpret_cast<uint2*>(pb + l.runs);
-      F.xt_whist = reinterpret_cast<uint16_t*>(pb + l.xt_whist);
-      F.xt_hist = reinterpret_cast<uint16_t*>(pb + l.xt_hist);
-      F.xt_base = reinterpret_cast<uint32_t*>(pb + l.xt_base);
-    }
     F.len_cursor = reinterpret_cast<uint32_t*>(zb + l.z_len);
     F.lookback = reinterpret_cast<unsigned long long*>(zb + l.z_lb);
+    F.heads = encode ? nullptr : reinterpret_cast<uint32_t*>(zb + l.z_heads);
     F.track_start = reinterpret_cast<uint32_t*>(pb + l.track_start);
     F.order = reinterpret_cast<uint32_t*>(pb + l.order);
     F.keys = reinterpret_cast<uint16_t*>(pb + l.keys);
@@ -522,9 +491,6 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     pre_warp[f + 1] = pre_warp[f] + ceil_div(F.n_tracks, 32);  // encoder warp tasks
     pre_chunk[f + 1] = pre_chunk[f] + l.n_chunks;
     pre_kt[f + 1] = pre_kt[f] + ceil_div(F.n_tracks, 32);
-    pre_sblk[f + 1] = pre_sblk[f] + l.n_sblk;
-    pre_xtile[f + 1] = pre_xtile[f] + l.n_xtiles;
-    pre_kblk[f + 1] = pre_kblk[f] + ceil_div(F.n_tracks, kKeyTracks);
   }
   PlanDev P;
   const uint32_t* dpre = reinterpret_cast<const uint32_t*>(dev + R.pre);
@@ -535,9 +501,6 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   P.pre_warp = dpre + 3 * (nf + 1);
   P.pre_chunk = dpre + 4 * (nf + 1);
   P.pre_kt = dpre + 5 * (nf + 1);
-  P.pre_sblk = dpre + 6 * (nf + 1);
-  P.pre_xtile = dpre + 7 * (nf + 1);
-  P.pre_kblk = dpre + 8 * (nf + 1);
   P.counters = reinterpret_cast<uint32_t*>(zb);
   const FrameDev* dframes = reinterpret_cast<const FrameDev*>(dev + R.frames);
   const EncDev* denc = reinterpret_cast<const EncDev*>(dev + R.enc);
@@ -580,49 +543,16 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       timed(kKTrackEncode, [&] { k_track_encode<<<grid, 256, 0, st>>>(denc, dframes, P, n_warp); });
     }
   } else {
+    // keys and ranks, row offsets, tile bases; the track decode and the
+    // record scatter; the unattached decode (it needs only rowStart and the
+    // attached counts) on the second stream beside the decode and the
+    // scatter (overlap 1) or beside the scatter alone (overlap 2)
     const uint32_t n_kt = pre_kt[nf];
-    const bool xpose = h->tune_place == 1;
-    const bool in_decoder = h->tune_place == 2;  // records placed by the decoder
-    const bool prekey = h->tune_prekey == 1 || in_decoder;
-    const uint32_t n_sblk = pre_sblk[nf], n_xt = pre_xtile[nf];
-    const bool two = aux && fork && join;
-    // the phases of the chain, each on a given stream
-    auto decode = [&](int out) {  // warp tasks of 32 tracks, taken from counters[0]
-      if (!n_kt) return;
-      const int var = h->tune_decode_variant;
-      int bps = out == kOutPlace ? h->occ_decode_v[4] : h->occ_decode_v[var];
-      if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
-      const uint32_t per_block = kDecodeThreads / 32;
-      const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
-          (uint32_t)(h->sms * bps), (n_kt + per_block - 1) / per_block));
-      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt, out); });
-    };
-    auto counts = [&](cudaStream_t s_) {  // per-row counts, row offsets (keys only)
-      if (xpose) {
-        if (n_sblk) {
-          timed_on(s_, kKSegCount, [&] { k_seg_count<<<n_sblk, kSegThreads, 0, s_>>>(dframes, P); });
-          timed_on(s_, kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, s_>>>(dframes, P); });
-          timed_on(s_, kKSegRuns, [&] { k_seg_runs<<<n_sblk, kSegThreads, 0, s_>>>(dframes, P); });
-        } else {
-          timed_on(s_, kKSegScan, [&] { k_seg_scan<<<nf * kNSec, 1024, 0, s_>>>(dframes, P); });
-        }
-        if (n_xt) timed_on(s_, kKXCount, [&] { k_xcount<<<n_xt, kXThreads, 0, s_>>>(dframes, P); });
-        timed_on(s_, kKXRowOffsets, [&] { k_xrow_offsets<<<nf, 1024, 0, s_>>>(dframes, P); });
-      } else {
-        if (n_tile)
-          timed_on(s_, kKCountRank, [&] { launch_count_rank(h->tune_rank_variant, n_tile, s_, dframes, P); });
-        if (n_grp) timed_on(s_, kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, s_>>>(dframes, P); });
-        timed_on(s_, kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, s_>>>(dframes, P); });
-      }
-    };
-    auto bases = [&](cudaStream_t s_) {  // first native index of every tile and row
-      if (xpose) {
-        if (n_xt) timed_on(s_, kKXBase, [&] { k_xbase<<<nf * kNSec, kNRow * kXBaseQ, 0, s_>>>(dframes, P); });
-      } else if (n_grp) {
-        timed_on(s_, kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, s_>>>(dframes, P); });
-      }
-    };
-    auto unatt = [&](cudaStream_t s_) {  // needs rowStart and the attached counts
+    const bool two = aux && fork && join && n_chunk;
+    if (n_tile) timed(kKKeyRank, [&] { launch_key_rank(n_tile, st, dframes, P); });
+    if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+    timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
+    auto unatt = [&](cudaStream_t s_) {
       if (!n_chunk) return;
       int bps = h->occ_unatt;
       if (h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;
@@ -631,71 +561,37 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
         launch_unatt_decode(h->tune_unatt_variant, grid, s_, dframes, P, n_chunk);
       });
     };
-    auto place = [&]() {  // native records of the attached clusters
-      if (in_decoder) return;
-      if (xpose) {
-        if (n_xt) timed(kKXScatter, [&] { launch_xscatter(n_xt, st, dframes, P); });
-      } else if (n_tile) {
-        timed(kKAttScatter, [&] { launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P); });
-      }
+    auto fork_unatt = [&]() -> int {
+      CK(cudaEventRecord(fork, st));
+      CK(cudaStreamWaitEvent(aux, fork, 0));
+      unatt(aux);
+      return TMD_OK;
     };
-    if (prekey) {
-      // keys first; with a second stream everything that needs only keys runs
-      // beside the track decoder
-      const uint32_t n_kblk = pre_kblk[nf];
-      if (n_kblk) timed(kKTrackKeys, [&] { k_track_keys<<<n_kblk, kKeyTracks, 0, st>>>(dframes, P); });
-      if (in_decoder) {
-        // the decoder places the records: ranks and tile bases first, and a
-        // decode order that goes tile by tile
-        if (n_tile) timed(kKChunkOrder, [&] { k_chunk_order<<<n_tile, 256, 0, st>>>(dframes, P); });
-        counts(st);
-        bases(st);
-        const bool fork_u = two && n_chunk;
-        if (fork_u) {
-          CK(cudaEventRecord(fork, st));
-          CK(cudaStreamWaitEvent(aux, fork, 0));
-        }
-        unatt(fork_u ? aux : st);
-        decode(kOutPlace);
-        if (fork_u) {
-          CK(cudaEventRecord(join, aux));
-          CK(cudaStreamWaitEvent(st, join, 0));
-        }
-      } else {
-        // counts and bases first; the unattached decode runs beside the
-        // track decoder (memory-bound beside latency-bound)
-        counts(st);
-        bases(st);
-        const bool fork_u = two && n_chunk;
-        if (fork_u) {
-          CK(cudaEventRecord(fork, st));
-          CK(cudaStreamWaitEvent(aux, fork, 0));
-        }
-        unatt(fork_u ? aux : st);
-        decode(kOutNoKey);
-        if (fork_u) {
-          CK(cudaEventRecord(join, aux));
-          CK(cudaStreamWaitEvent(st, join, 0));
-        }
-        place();
-      }
+    if (two && h->tune_overlap == 1) {
+      const int rc = fork_unatt();
+      if (rc != TMD_OK) return rc;
+    }
+    if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+    if (n_kt) {
+      const int var = h->tune_decode_variant;
+      int bps = h->occ_decode_v[var];
+      if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
+      const uint32_t per_block = kDecodeThreads / 32;
+      const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
+          (uint32_t)(h->sms * bps), (n_kt + per_block - 1) / per_block));
+      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt); });
+    }
+    if (two && h->tune_overlap != 1) {
+      const int rc = fork_unatt();
+      if (rc != TMD_OK) return rc;
+    }
+    if (n_tile)
+      timed(kKAttScatter, [&] { launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P); });
+    if (two) {
+      CK(cudaEventRecord(join, aux));
+      CK(cudaStreamWaitEvent(st, join, 0));
     } else {
-      decode(kOutAll);
-      counts(st);
-      // the unattached decode needs only rowStart / attCount: with an aux
-      // stream it runs beside the tile bases and the record scatter
-      const bool fork_u = two && n_chunk;
-      if (fork_u) {
-        CK(cudaEventRecord(fork, st));
-        CK(cudaStreamWaitEvent(aux, fork, 0));
-      }
-      unatt(fork_u ? aux : st);
-      bases(st);
-      place();
-      if (fork_u) {
-        CK(cudaEventRecord(join, aux));
-        CK(cudaStreamWaitEvent(st, join, 0));
-      }
+      unatt(st);
     }
   }
   CK(cudaGetLastError());

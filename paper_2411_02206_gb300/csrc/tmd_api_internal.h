@@ -16,10 +16,8 @@ struct TmdServer;  // serving state (tmd_serve.cu)
 
 // Kernel ids of the instrumentation.
 enum TmdKernel {
-  kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode, kKCountRank,
-  kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode,
-  kKSegCount, kKSegScan, kKSegRuns, kKXCount, kKXRowOffsets, kKXBase, kKXScatter, kKTrackKeys,
-  kKChunkOrder, kKNum
+  kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode, kKKeyRank,
+  kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode, kKNum
 };
 
 struct TmdProfile {
@@ -45,21 +43,15 @@ struct tmd_handle {
   int device = 0;
   int sms = 0;
   int occ_decode = 1, occ_unatt = 1, occ_encode = 1;
-  int occ_decode_v[5] = {1, 1, 1, 1, 1};  // resident blocks per SM: decoder variants 0-3, and
-                                          // the decoder that places records (4)
+  int occ_decode_v[2] = {1, 1};  // resident blocks per SM of the decoder variants
   // tuning parameters (launch shapes only; results never depend on them)
-  int tune_decode_variant = 3;   // staging-round variant of the track decoder
-  int tune_rank_variant = 1;     // duplicate-key handling of the ranking kernel
+  int tune_decode_variant = 0;   // staging-round variant of the track decoder
   int tune_scatter_variant = 1;  // store pattern of the record scatter
   int tune_unatt_variant = 1;    // record write-out of the unattached decode
-  int tune_overlap = 1;          // unattached decode on a second stream beside the scatter
-  int tune_place = 0;            // placement: 0 rank + scatter in input order, 1 per-sector
-                                 // transpose, 2 records placed by the track decoder
-  int tune_prekey = 0;           // 1: key walk first, key-only work beside the track decoder
+  int tune_overlap = 2;          // unattached decode on a second stream: 0 no, 1 beside the
+                                 // track decode and the scatter, 2 beside the scatter
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 1;        // unattached-decode blocks per SM (0: as many as fit)
-  int tune_rans_variant = 0;     // word refill of the entropy decoder (0 branch, 1 predicated,
-                                 // 2 word queue, 3 branch with a counted word supply)
   int tune_rans_overlap = 1;     // 4-byte streams entropy-decoded on the second stream
   uint64_t mem_budget = 0;
   uint32_t max_slots = 0;
@@ -116,16 +108,14 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
                const TraceReq* trace = nullptr);
 // Scratch layout of one frame.  The zeroed part of all frames is contiguous.
 struct FrameLayout {
-  uint32_t n_tblocks, n_tiles, n_groups, n_chunks, n_sblk, n_xtiles;
-  size_t z_len, z_lb;                             // offsets in the zeroed part
+  uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
+  size_t z_len, z_lb, z_heads;                    // offsets in the zeroed part
   size_t track_start, order, keys, kf_pad, kf_time, rank, tile_hist, group_sum, tile_base,
       unatt_start, blk_sum, att_count;            // offsets in the plain part
-  size_t seg_cnt, seg_tot, runs, xt_whist, xt_hist, xt_base;  // transpose placement (xpose)
 };
-// Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts;
-// with xpose, also the buffers of the per-sector transpose placement.
+// Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts.
 void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
-                FrameLayout& L, bool xpose = true);
+                FrameLayout& L);
 
 // Bytes of scratch and of launch record that a call needs.
 void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin,

@@ -71,7 +71,7 @@ extern "C" int tmd_batch_create(tmd_handle* h, uint32_t n, const tmd_frame_in* i
   if (rc == TMD_OK) {
     // no timing events inside the graph; the fork/join events become edges
     rc = tmd_enqueue(h, n, in, out, nullptr, nullptr, b->scratch, b->host_record, b->dev_record,
-                     b->cap, false, (h->tune_overlap || h->tune_prekey) ? b->aux : nullptr,
+                     b->cap, false, h->tune_overlap ? b->aux : nullptr,
                      b->fork, b->join);
     const int rc2 = tmd_cuda_check(h, cudaStreamEndCapture(b->cap, &b->graph), "end capture");
     if (rc == TMD_OK) rc = rc2;

@@ -20,27 +20,11 @@ constexpr int kChunk = 2048;             // unattached clusters per scan chunk
 constexpr int kLenBuckets = 1024;        // track-length buckets of the decode order
 constexpr int kDecodeThreads = 128;      // threads per block of the track decoder
 constexpr int kScatThreads = 256;        // threads per block of the record scatter
-constexpr int kScatCta = 8;              // CTAs per thread-block cluster of the regrouping scatter
-constexpr int kScatThreads2 = 512;       // threads per CTA of the regrouping scatter
-constexpr int kScatClusterSmem = (kTile / kScatCta) * 16 + kNBin * 2;
-// Placement by per-sector transpose (tmd_xpose.cu).
-constexpr int kSegBlk = 4096;            // attached clusters per block of the run search
-constexpr int kSegThreads = 256;         // 16 clusters per thread
-constexpr int kXT = 8192;                // sector-stream positions per transpose tile
-constexpr int kXWarps = 8;               // warps per transpose tile
-constexpr int kXSub = kXT / kXWarps;     // positions per warp
-constexpr int kXThreads = kXWarps * 32;
-constexpr int kXSteps = kXSub / 32;      // steps of 32 positions per warp
-constexpr int kXLook = 8;                // steps of loads in flight per warp (record transpose)
-constexpr int kXCountLook = 16;          // steps of key loads in flight per warp (tile counts)
-constexpr int kXBaseQ = 6;               // threads per row of the tile-base scan
-constexpr int kXScatterSmem = kXT * kRecBytes;
 
 // One frame as the kernels see it: caller inputs, caller outputs, scratch.
 struct FrameDev {
   uint32_t n_tracks, n_att, n_unatt;
   uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
-  uint32_t n_sblk, n_xtiles;  // run-search blocks, transpose tiles (upper bound)
   // per track
   const uint8_t* qpt;
   const uint8_t* row;
@@ -88,13 +72,8 @@ struct FrameDev {
   uint32_t* blk_sum;       // n_tblocks
   uint32_t* len_cursor;    // kLenBuckets (zeroed)
   unsigned long long* lookback;  // n_chunks (zeroed)
-  // placement by per-sector transpose
-  uint32_t* seg_cnt;       // [2][kNSec][n_sblk]: runs, clusters per (sector, block); scanned
-  uint32_t* seg_tot;       // [2][kNSec]: runs, clusters per sector
-  uint2* runs;             // n_att (upper bound): {stream position, first j}, sector-major
-  uint16_t* xt_whist;      // n_xtiles x kXWarps x kNRow: per-warp row counts of a tile
-  uint16_t* xt_hist;       // n_xtiles x kNRow: row counts of a tile
-  uint32_t* xt_base;       // n_xtiles x kNRow: first native index of (tile, row)
+  uint32_t* heads;         // (n_att + 31) / 32 words, bit j set when cluster j is the
+                           // first of its track (zeroed; set by the track scan)
 };
 
 // Encoder view of a frame: attached truth in, compressed attached streams out.
@@ -129,9 +108,6 @@ struct PlanDev {
   const uint32_t* pre_warp;   // encoder: warp tasks of 32 tracks
   const uint32_t* pre_chunk;  // unattached chunks
   const uint32_t* pre_kt;     // decoder: warp tasks of 32 tracks
-  const uint32_t* pre_sblk = nullptr;   // run-search blocks
-  const uint32_t* pre_xtile = nullptr;  // transpose tiles (upper bound per frame)
-  const uint32_t* pre_kblk = nullptr;   // key-walk blocks
   uint32_t* counters;         // [0] decode/encode task, [1] unattached ticket (zeroed)
 };
 
@@ -174,57 +150,30 @@ __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames);
 __global__ void k_track_scan1(const FrameDev* frames, PlanDev plan);
 __global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);
 __global__ void k_track_scan2(const FrameDev* frames, PlanDev plan);
-// Ranking variants (identical results): 0 orders equal keys of a step with
-// match.any, 1 detects duplicate keys with a shared-memory bitmap and falls
-// back to match.any only for steps that have some, 2 does the same test for
-// groups of 8 steps.
-void launch_count_rank(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                       PlanDev plan);
-cudaError_t prepare_count_rank();
+// Keys, tile histograms and stable ranks of the attached clusters (grid:
+// ranking tiles of all frames).
+void launch_key_rank(uint32_t grid, cudaStream_t st, const FrameDev* frames, PlanDev plan);
+cudaError_t prepare_key_rank();
 __global__ void k_group_sum(const FrameDev* frames, PlanDev plan);
 __global__ void k_row_offsets(const FrameDev* frames, PlanDev plan);
 __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
-// The track decoder is instantiated in four variants (staging rounds of 32,
-// 16, 8 steps, and 16 steps under a register cap; a tuning parameter, every
-// instance computes identical results); host code launches it through these
-// two functions.  Its warps take tasks of 32 tracks (pre_kt of the plan) from
-// counters[0].
-// Decoder outputs: key + pad + time codes, pad + time codes, or the native
-// records of the attached clusters placed directly (ranks and tile bases
-// computed beforehand from k_track_keys' keys).
-constexpr int kOutAll = 0, kOutNoKey = 1, kOutPlace = 2;
+// The track decoder is instantiated in variants of its staging (a tuning
+// parameter, every instance computes identical results); host code launches
+// it through these two functions.  Its warps take tasks of 32 tracks (pre_kt
+// of the plan) from counters[0] and write the pad and time codes of every
+// attached cluster (the keys come from k_key_rank).
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_tasks, int out = kOutAll);
-// Decode order for placement by the decoder: the tracks that start in each
-// ranking tile, longest first, tile after tile (grid: ranking tiles).
-__global__ void k_chunk_order(const FrameDev* frames, PlanDev plan);
-// Key walk of the attached clusters (keys only, integer): one block per
-// kKeyTracks consecutive tracks (pre_kblk), in windows of kKeyWin clusters.
-constexpr int kKeyTracks = 128;
-constexpr int kKeyWin = 12288;
-__global__ void k_track_keys(const FrameDev* frames, PlanDev plan);
+                         PlanDev plan, uint32_t n_tasks);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
-// Record scatter variants 0..3 (identical results; see tmd_scatter.cu),
+// Record scatter variants 0, 1 (identical results; see tmd_scatter.cu),
 // launched over n_tiles ranking tiles of all frames.
 void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan);
-cudaError_t prepare_att_scatter();
 // Unattached decode variants 0, 1 (record write-out word by word or one
 // record per thread; identical results), launched through these functions.
 void launch_unatt_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                          PlanDev plan, uint32_t n_tickets);
 cudaError_t occupancy_unatt_decode(int* blocks_per_sm);
-// Placement by per-sector transpose (identical results to k_count_rank ...
-// k_att_scatter); grids: run-search blocks (pre_sblk), frames x kNSec,
-// transpose tiles (pre_xtile), frames.
-__global__ void k_seg_count(const FrameDev* frames, PlanDev plan);
-__global__ void k_seg_scan(const FrameDev* frames, PlanDev plan);
-__global__ void k_seg_runs(const FrameDev* frames, PlanDev plan);
-__global__ void k_xcount(const FrameDev* frames, PlanDev plan);
-__global__ void k_xrow_offsets(const FrameDev* frames, PlanDev plan);
-__global__ void k_xbase(const FrameDev* frames, PlanDev plan);
-cudaError_t prepare_xscatter();
-void launch_xscatter(uint32_t grid, cudaStream_t st, const FrameDev* frames, PlanDev plan);
 __global__ void k_selftest_wait(const unsigned long long* never, uint32_t* status);
 __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDev plan,
                                uint32_t n_tasks);

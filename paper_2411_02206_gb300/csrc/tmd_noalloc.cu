@@ -7,14 +7,19 @@
 // the same kernels as tmd_decode_frame but takes its working memory from one
 // fixed array in the library's device image, g_noalloc_scratch, instead of a
 // handle's scratch allocation.  The caller still provides the frame's inputs
-// and outputs.
+// and outputs.  The chain is the default one of tmd_decode_frame (key and rank
+// pass, track decoder variant 0, three-lane record scatter, unattached decode
+// with one staged record per thread), all on the caller's stream (no second
+// stream).
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it until the process exits.  In host code its name is only a
 // stand-in for the device symbol, so the device address is looked up with
-// cudaGetSymbolAddress once per device (with that device current) and passed
-// to the kernels.  All calls share the array and it keeps the previous call's
-// contents; the parts that must start at zero are cleared by every call.
+// cudaGetSymbolAddress on every call (with the caller's device current; the
+// lookup allocates nothing) and passed to the kernels; the occupancy figures
+// and the shared-memory attributes are set up once per device.  All calls
+// share the array and it keeps the previous call's contents; the parts that
+// must start at zero are cleared by every call.
 #include <cstdio>
 #include <mutex>
 
@@ -32,7 +37,6 @@ constexpr int kMaxDevices = 64;
 
 struct DeviceState {
   bool ready = false;
-  unsigned char* base = nullptr;  // device address of g_noalloc_scratch
   int sms = 0, occ_decode = 1, occ_unatt = 1;
 };
 
@@ -72,7 +76,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   FrameLayout L;
   size_t zoff = 256 + ((size_t)kNBin * 4 + 255) / 256 * 256;  // counters + zero bins
   size_t poff = 0;
-  plan_frame(in->n_tracks, in->n_attached, in->n_unattached, zoff, poff, L, false);
+  plan_frame(in->n_tracks, in->n_attached, in->n_unattached, zoff, poff, L);
   const size_t zbytes = (zoff + 255) / 256 * 256;
   const size_t need = zbytes + poff;
   if (need > kScratchMax) {
@@ -90,24 +94,23 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     return TMD_ERR_CUDA;
   }
   DeviceState* S = &g_state[dev];
+  void* scratch_addr = nullptr;
+  if (cudaGetSymbolAddress(&scratch_addr, g_noalloc_scratch) != cudaSuccess || !scratch_addr) {
+    cudaGetLastError();
+    set_err(err, err_len, "cudaGetSymbolAddress of the scratch array failed");
+    return TMD_ERR_CUDA;
+  }
   {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!S->ready) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        set_err(err, err_len, "cudaGetSymbolAddress of the scratch array failed");
-        return TMD_ERR_CUDA;
-      }
       int sms = 0, od = 0, ou = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          prepare_count_rank() != cudaSuccess ||
+          prepare_key_rank() != cudaSuccess ||
           occupancy_track_decode(0, &od) != cudaSuccess ||
           occupancy_unatt_decode(&ou) != cudaSuccess) {
         set_err(err, err_len, "device set-up failed");
         return TMD_ERR_CUDA;
       }
-      S->base = static_cast<unsigned char*>(p);
       S->sms = sms;
       S->occ_decode = od > 0 ? od : 1;
       S->occ_unatt = ou > 0 ? ou : 1;
@@ -115,8 +118,9 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  unsigned char* rec = S->base;
-  char* zb = reinterpret_cast<char*>(S->base + kRecordBytes);
+  unsigned char* base = static_cast<unsigned char*>(scratch_addr);
+  unsigned char* rec = base;
+  char* zb = reinterpret_cast<char*>(base + kRecordBytes);
   char* pb = zb + zbytes;
   FrameDev F;
   memset(&F, 0, sizeof F);
@@ -134,6 +138,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.n_chunks = L.n_chunks;
   F.len_cursor = reinterpret_cast<uint32_t*>(zb + L.z_len);
   F.lookback = reinterpret_cast<unsigned long long*>(zb + L.z_lb);
+  F.heads = reinterpret_cast<uint32_t*>(zb + L.z_heads);
   F.track_start = reinterpret_cast<uint32_t*>(pb + L.track_start);
   F.order = reinterpret_cast<uint32_t*>(pb + L.order);
   F.keys = reinterpret_cast<uint16_t*>(pb + L.keys);
@@ -170,19 +175,19 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   if (n_tblk) k_track_scan1<<<n_tblk, 256, 0, st>>>(dframe, P);
   k_frame_scan<<<1, 1024, 0, st>>>(dframe, P);
   if (n_tblk) k_track_scan2<<<n_tblk, 256, 0, st>>>(dframe, P);
+  if (n_tile) launch_key_rank(n_tile, st, dframe, P);
+  if (n_grp) k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
+  k_row_offsets<<<1, 1024, 0, st>>>(dframe, P);
+  if (n_grp) k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
   if (n_kt) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_decode);
     const uint32_t want = (n_kt + kDecodeThreads / 32 - 1) / (kDecodeThreads / 32);
     launch_track_decode(0, want < cap ? want : cap, st, dframe, P, n_kt);
   }
-  if (n_tile) launch_count_rank(1, n_tile, st, dframe, P);
-  if (n_grp) k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
-  k_row_offsets<<<1, 1024, 0, st>>>(dframe, P);
-  if (n_grp) k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
-  if (n_tile) launch_att_scatter(0, n_tile, st, dframe, P);
+  if (n_tile) launch_att_scatter(1, n_tile, st, dframe, P);
   if (n_chunk) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_unatt);
-    launch_unatt_decode(0, n_chunk < cap ? n_chunk : cap, st, dframe, P, n_chunk);
+    launch_unatt_decode(1, n_chunk < cap ? n_chunk : cap, st, dframe, P, n_chunk);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -1,34 +1,41 @@
-// tmd_rank.cu -- per-row counts and stable ranks of the attached clusters.
+// tmd_rank.cu -- (sector,row) keys, per-row counts and stable ranks of the
+// attached clusters.
 //
 // The native list groups clusters by (sector,row) with the attached clusters
 // of a bin in (track, cluster) order, i.e. in input order j.  A stable
-// counting sort of the bin keys key[j] = sector * 152 + row (written by the
-// track decoder) gives every cluster its place:
+// counting sort of the bin keys key[j] = sector * 152 + row gives every
+// cluster its place: native index = tileBase[tile][key] + rank[j].
 //
-//   k_count_rank  tile = kTile consecutive clusters, one block, warp w =
-//                 kTileSub consecutive clusters of the tile.  Pass 1 counts
-//                 keys per warp (packed 16-bit shared-memory counters), the
-//                 block turns the per-warp counts into per-warp exclusive
-//                 offsets and writes the tile histogram; pass 2 reads the keys
-//                 in stream order (32 consecutive clusters per step) and gives
-//                 every cluster its rank among the tile's clusters of the same
-//                 bin, equal keys of one step ordered by lane (match.any).
-//                 Variant 1 first tests the step for repeated keys with a
-//                 per-warp bitmap (atom.or returns the bit's old value) and
-//                 takes the match.any path only when some key repeats;
-//                 consecutive clusters mostly belong to one track and lie in
-//                 distinct rows, so most steps take the short path.  Variant
-//                 2 tests 8 steps (256 keys) at once: without a repeated key
-//                 the 8 steps' count reads and writes are independent and
-//                 issue together; a group with one runs step by step.
+// The key of a cluster depends only on the track's stored first row and
+// sector and on the row and sector differences before it: the track model
+// never feeds back into the walk (Sec. 4: rows and sectors are stored as
+// differences along the track).  So the keys are a segmented prefix sum over
+// the attached-cluster stream -- rows mod 256, sectors mod 36, restarting at
+// every track's first cluster -- and need not wait for the track decoder.
 //
-// The native index of cluster j is then tileBase[tile][key] + rank[j].
+//   k_key_rank  tile = kTile consecutive clusters, one block, warp w =
+//               kTileSub consecutive clusters of the tile.  Pass 1 walks the
+//               warp's clusters in steps of 32 (one per lane): the track
+//               heads of a step come from the head bitmap (bit j set when
+//               cluster j starts a track, written by the track scan), a lane
+//               loads its header (a head) or its row and sector difference,
+//               and a warp scan with a carry from the previous step gives the
+//               row and sector of every cluster.  The loads of 8 steps are
+//               issued before their scans.  The keys are written and counted
+//               per warp (packed 16-bit shared-memory counters).  The block
+//               then turns the per-warp counts into per-warp exclusive
+//               offsets and writes the tile histogram; pass 2 reads the keys
+//               back in stream order and gives every cluster its rank among
+//               the tile's clusters of the same bin.  A step whose keys are
+//               all distinct (tested with a per-warp bitmap: atom.or returns
+//               the bit's old value) ranks with one shared-memory read and
+//               write per lane; a step with a repeated key orders equal keys
+//               by lane with match.any.
 #include "tmd_internal.cuh"
 
 namespace tmd {
 
-template <int V>
-__global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, PlanDev plan) {
+__global__ void __launch_bounds__(256, 2) k_key_rank(const FrameDev* frames, PlanDev plan) {
   // [kTileWarps][kNBin/2] packed u16 counts, then [kTileWarps][kRankBitmapWords]
   extern __shared__ uint32_t s_mem[];
   const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, blockIdx.x);
@@ -36,7 +43,7 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
   if (*F.status & kStCount) return;
   const uint32_t tile = blockIdx.x - plan.pre_tile[f];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint16_t* __restrict__ keys = F.keys;
+  uint16_t* __restrict__ keys = F.keys;
   uint16_t* __restrict__ rank = F.rank;
   uint16_t* __restrict__ tile_hist = F.tile_hist;
   const uint32_t n_att = F.n_att;
@@ -48,32 +55,110 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
   __syncwarp();
   const uint32_t j_begin = tile * (uint32_t)kTile + wid * (uint32_t)kTileSub;
   const uint32_t j_end = min(j_begin + (uint32_t)kTileSub, n_att);
-  // pass 1: counts per warp; 8 keys per lane per 16-byte load, 8 loads in
-  // flight per lane
-  for (uint32_t jb = j_begin; jb < j_end; jb += 8u * 256u) {
-    uint4 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint32_t j = jb + 256u * u + 8u * lane;
-      v[u] = j + 8 <= j_end ? *reinterpret_cast<const uint4*>(keys + j) : make_uint4(0, 0, 0, 0);
+  const uint32_t le_mask = lanemask_le();
+  // pass 1: keys (segmented scan of the row and sector differences) and
+  // per-warp counts
+  if (j_begin < j_end) {
+    const uint32_t* __restrict__ ts = F.track_start;
+    const uint8_t* __restrict__ rd = F.row_diff;
+    const uint8_t* __restrict__ sld = F.sld;
+    const uint8_t* __restrict__ hrow = F.row;
+    const uint8_t* __restrict__ hsec = F.slice;
+    const uint32_t* __restrict__ heads = F.heads;
+    // the track holding j_begin: the largest t with trackStart[t] <= j_begin
+    // (n_tracks >= 1 here: the attached clusters are the tracks' clusters)
+    uint32_t lo = 0, hi = F.n_tracks - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (ts[mid] <= j_begin) lo = mid; else hi = mid - 1;
     }
+    const uint32_t t0 = lo, s0 = ts[t0];
+    // carry = row and sector of cluster j_begin - 1 when it lies in the same
+    // track (row in bits 0-15, sector in bits 16-31)
+    uint32_t carry = 0;
+    if (s0 < j_begin) {
+      const uint32_t hs = hsec[t0];
+      uint32_t sr = 0, ss = 0;
+      for (uint32_t d = s0 - t0 + lane; d < j_begin - t0 - 1; d += 32) {
+        sr += rd[d];
+        ss += sld[d] % (uint32_t)kNSec;
+      }
+      sr = __reduce_add_sync(0xffffffffu, sr);
+      ss = __reduce_add_sync(0xffffffffu, ss);
+      carry = ((hrow[t0] + sr) & 255u) |
+              (((hs < (uint32_t)kNSec ? hs : kNSec - 1u) + ss) % (uint32_t)kNSec) << 16;
+    }
+    // track of the cluster before the current step (wraps below 0 before the
+    // first track; every in-range lane has at least one head at or before it)
+    uint32_t tb = s0 < j_begin ? t0 : t0 - 1u;
+    uint32_t st = 0;
+    for (uint32_t jb = j_begin; jb < j_end; jb += 8u * 32u) {
+      // head masks of the 8 steps (jb is a multiple of 32), then all loads
+      uint32_t mw = 0;
+      if (lane < 8 && jb + 32u * lane < j_end) mw = heads[(jb >> 5) + lane];
+      uint32_t M[8], er[8], es[8];
+      uint32_t tc = tb;
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint32_t j = jb + 256u * u + 8u * lane;
-      if (j + 8 <= j_end) {
-        const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-          const uint32_t k = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-          atomicAdd(&hist32[k >> 1], (k & 1u) ? 0x10000u : 1u);
+      for (int u = 0; u < 8; u++) {
+        M[u] = __shfl_sync(0xffffffffu, mw, u);
+        const uint32_t j = jb + 32u * u + lane;
+        const uint32_t tj = tc + __popc(M[u] & le_mask);
+        er[u] = 0;
+        es[u] = 0;
+        if (j < j_end) {
+          if ((M[u] >> lane) & 1u) {
+            er[u] = hrow[tj];
+            es[u] = hsec[tj] | 0x100u;  // marks a header sector (checked below)
+          } else {
+            const uint32_t d = j - tj - 1u;
+            er[u] = rd[d];
+            es[u] = sld[d];
+          }
         }
-      } else {
-        for (uint32_t q = j; q < j_end; q++) {
-          const uint32_t k = keys[q];
+        tc += __popc(M[u]);
+      }
+      tb = tc;
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const uint32_t j = jb + 32u * u + lane;
+        const bool in = j < j_end;
+        uint32_t sec_in;
+        if (es[u] & 0x100u) {  // a track's first cluster: its stored sector
+          sec_in = es[u] & 255u;
+          if (in && (sec_in >= (uint32_t)kNSec || er[u] >= (uint32_t)kNRow)) st |= kStRow;
+          if (sec_in >= (uint32_t)kNSec) sec_in = kNSec - 1;
+        } else {               // a sector difference (the leg part does not move the key)
+          sec_in = es[u] % (uint32_t)kNSec;
+        }
+        // inclusive warp scan of (row, sector); subtracting the prefix before
+        // the lane's last head restarts the sum at the track's first cluster
+        uint32_t S = er[u] | (sec_in << 16);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, S, o);
+          if (lane >= o) S += y;
+        }
+        const uint32_t hm = M[u] & le_mask;
+        const int hp = hm ? 31 - __clz(hm) : 0;
+        const uint32_t before = __shfl_sync(0xffffffffu, S, hp > 0 ? hp - 1 : 0);
+        const uint32_t seg = hm ? (hp > 0 ? S - before : S) : S + carry;
+        const uint32_t raw = seg & 255u;
+        const uint32_t sec = (seg >> 16) % (uint32_t)kNSec;
+        carry = __shfl_sync(0xffffffffu, raw | (sec << 16), 31);
+        if (in) {
+          uint32_t row = raw;
+          if (row >= (uint32_t)kNRow) {
+            st |= kStRow;
+            row = kNRow - 1;
+          }
+          const uint32_t k = sec * kNRow + row;
+          keys[j] = (uint16_t)k;
           atomicAdd(&hist32[k >> 1], (k & 1u) ? 0x10000u : 1u);
         }
       }
     }
+    st = __reduce_or_sync(0xffffffffu, st);
+    if (st && lane == 0) atomicOr(F.status, st);
   }
   __syncthreads();
   // per-warp exclusive offsets within the tile; tile histogram
@@ -89,8 +174,8 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
     tile_hist[(size_t)tile * kNBin + b] = (uint16_t)run;
   }
   __syncthreads();
-  // pass 2: stable ranks in stream order; the keys of the next 8 steps are
-  // loaded while the current 8 are ranked
+  // pass 2: stable ranks in stream order (keys written by this warp in pass
+  // 1); the keys of the next 8 steps are loaded while the current 8 are ranked
   uint32_t nk[8];
 #pragma unroll
   for (int u = 0; u < 8; u++) {
@@ -105,54 +190,22 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
       const uint32_t j = b0 + 256u + 32u * u + lane;
       nk[u] = j < j_end ? (uint32_t)keys[j] : 0xFFFFFFFFu;
     }
-    if constexpr (V == 2) {
-      // all 256 keys distinct: every rank is the bin's count so far, and the
-      // 8 steps' reads and writes of the counts are independent
-      uint32_t dup = 0;
-#pragma unroll
-      for (int u = 0; u < 8; u++)
-        if (kk[u] != 0xFFFFFFFFu) dup |= atomicOr(&bm[kk[u] >> 5], 1u << (kk[u] & 31)) & (1u << (kk[u] & 31));
-      const bool clash = __any_sync(0xffffffffu, dup != 0);
-      __syncwarp();
-#pragma unroll
-      for (int u = 0; u < 8; u++)
-        if (kk[u] != 0xFFFFFFFFu) bm[kk[u] >> 5] = 0u;  // every bit of the word was set here
-      __syncwarp();
-      if (!clash) {
-        uint32_t base[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) base[u] = kk[u] != 0xFFFFFFFFu ? hist[kk[u]] : 0u;
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-          const uint32_t j = b0 + 32u * u + lane;
-          if (kk[u] != 0xFFFFFFFFu) {
-            hist[kk[u]] = (uint16_t)(base[u] + 1);
-            rank[j] = (uint16_t)base[u];
-          }
-        }
-        __syncwarp();
-        continue;
-      }
-    }
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       const uint32_t j = b0 + 32u * u + lane;
       const bool in = j < j_end;
       const uint32_t k = kk[u];
-      bool slow = true;
-      if constexpr (V == 1) {
-        // a lane whose bit was already set shares its key with an earlier
-        // lane of the step; without such a lane every key is new to the step
-        uint32_t dup = 0;
-        if (in) dup = atomicOr(&bm[k >> 5], 1u << (k & 31)) & (1u << (k & 31));
-        slow = __any_sync(0xffffffffu, dup != 0);
-        if (!slow && in) {
+      // a lane whose bit was already set shares its key with an earlier
+      // lane of the step; without such a lane every key is new to the step
+      uint32_t dup = 0;
+      if (in) dup = atomicOr(&bm[k >> 5], 1u << (k & 31)) & (1u << (k & 31));
+      if (!__any_sync(0xffffffffu, dup != 0)) {
+        if (in) {
           const uint32_t base = hist[k];
           hist[k] = (uint16_t)(base + 1);
           rank[j] = (uint16_t)base;
         }
-      }
-      if (slow) {
+      } else {
         const uint32_t act = __ballot_sync(0xffffffffu, in);
         if (in) {
           const uint32_t peers = __match_any_sync(act, k);
@@ -164,34 +217,19 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
         }
       }
       __syncwarp();
-      if constexpr (V == 1) {
-        if (in) bm[k >> 5] = 0u;  // every bit of the word was set in this step
-        __syncwarp();
-      }
+      if (in) bm[k >> 5] = 0u;  // every bit of the word was set in this step
+      __syncwarp();
     }
   }
 }
 
-void launch_count_rank(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                       PlanDev plan) {
-  if (variant == 2)
-    k_count_rank<2><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
-  else if (variant == 1)
-    k_count_rank<1><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
-  else
-    k_count_rank<0><<<grid, 256, kCountRankSmem, st>>>(frames, plan);
+void launch_key_rank(uint32_t grid, cudaStream_t st, const FrameDev* frames, PlanDev plan) {
+  k_key_rank<<<grid, 256, kCountRankSmem, st>>>(frames, plan);
 }
 
-cudaError_t prepare_count_rank() {
-  cudaError_t e = cudaFuncSetAttribute(k_count_rank<0>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kCountRankSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_count_rank<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kCountRankSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_count_rank<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kCountRankSmem);
-  return e;
+cudaError_t prepare_key_rank() {
+  return cudaFuncSetAttribute(k_key_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kCountRankSmem);
 }
 
 }  // namespace tmd

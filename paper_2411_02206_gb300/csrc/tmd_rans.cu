@@ -17,9 +17,7 @@
 // Values are written by the lane at positions 32 k + l: a warp stores 32
 // consecutive values per step.  Three launches, one per value width, size
 // blocks and shared memory for their tables (16, 32, 64 KB); the 4-byte
-// streams run on the handle's second stream beside the others.  The word
-// refill has four forms with identical results (tuning key rans_variant);
-// the branch form is the default, the fastest measured.
+// streams run on the handle's second stream beside the others.
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -295,17 +293,9 @@ __device__ uint64_t check_entry(const Job& J, const JobField& F, uint32_t w) {
   return off;
 }
 
-// V selects how a lane takes its next word (identical results): V = 0
-// branches into the refill when the state falls below 2^16 (the warp runs the
-// refill path whenever any lane needs it); V = 1 refills with predicated
-// selects and checks the lane's word count once at the end of the stream;
-// V = 2 keeps up to 3 pending words in a 64-bit queue, takes a word with
-// predicated shifts, and tops the queue up from a prefetched pair once per
-// two symbols (a symbol takes at most one word, so the queue never runs dry);
-// V = 3 branches like V = 0 but keeps the next word in the low half of cur,
-// moves to the prefetched pair with selects and counts the words taken,
-// checked against the lane's words once at the end of the stream.
-template <int W, int THREADS, int MINB, int V>
+// A lane branches into the word refill when its state falls below 2^16 (the
+// warp runs the refill path whenever any lane needs it).
+template <int W, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_rans_decode(const __grid_constant__ Job J) {
   using T = typename ValueType<W>::T;
   extern __shared__ uint32_t s_tab[];  // W * 4096 slot entries: d | sym << 12 | (f - 1) << 20
@@ -384,131 +374,26 @@ __global__ void __launch_bounds__(THREADS, MINB) k_rans_decode(const __grid_cons
       uint32_t nxt = maxp > 1 ? __ldg(P + 32) : 0u;
       uint32_t j = 0;  // pair held in cur
       bool half = false;
-      if constexpr (V == 0) {
-        for (uint32_t k = 0; k < nk; k++) {
-          uint32_t v = 0;
+      for (uint32_t k = 0; k < nk; k++) {
+        uint32_t v = 0;
 #pragma unroll
-          for (int p = 0; p < W; p++) {
-            const uint32_t e = s_tab[p * kM + (x & (kM - 1))];
-            x = ((e >> 20) + 1) * (x >> 12) + (e & (kM - 1));
-            v |= ((e >> 12) & 0xFFu) << (8 * p);
-            if (x < kLower) {
-              if (j >= maxp) bad = true;
-              x = (x << 16) | (half ? cur >> 16 : cur & 0xFFFFu);
-              if (half) {
-                cur = nxt;
-                j++;
-                nxt = j + 1 < maxp ? __ldg(P + 32ull * (j + 1)) : 0u;
-              }
-              half = !half;
-              if (x < kLower) bad = true;
-            }
-          }
-          out[32ull * k] = (T)v;
-        }
-      } else if constexpr (V == 1) {
-        // cur holds the lane's next word in its low half (and the one after
-        // it in the high half while half is false); nxt the following pair
-        const uint32_t* np = P + 64;  // pair j + 2
-        for (uint32_t k = 0; k < nk; k++) {
-          uint32_t v = 0;
-#pragma unroll
-          for (int p = 0; p < W; p++) {
-            const uint32_t e = s_tab[p * kM + (x & (kM - 1))];
-            const uint32_t q = x >> 12;
-            x = (e >> 20) * q + (q + (e & (kM - 1)));
-            v |= ((e >> 12) & 0xFFu) << (8 * p);
-            const bool need = x < kLower;
-            x = need ? (x << 16) | (cur & 0xFFFFu) : x;
-            const bool adv = need && half;
-            cur = adv ? nxt : (need ? cur >> 16 : cur);
-            if (adv) {
-              j++;
-              nxt = j + 1 < maxp ? __ldg(np) : 0u;
-              np += 32;
-            }
-            half = half != need;
-            bad = bad || (need && x < kLower);
-          }
-          out[32ull * k] = (T)v;
-        }
-        if (2 * j + (half ? 1u : 0u) > 2 * maxp) bad = true;  // read past its words
-      } else if constexpr (V == 3) {
-        bool two = true;    // cur still holds two words
-        uint32_t used = 0;  // words taken
-        uint32_t jn = 2;    // next pair to prefetch
-        const uint32_t* np = P + 64;
-        for (uint32_t k = 0; k < nk; k++) {
-          uint32_t v = 0;
-#pragma unroll
-          for (int p = 0; p < W; p++) {
-            const uint32_t e = s_tab[p * kM + (x & (kM - 1))];
-            x = ((e >> 20) + 1) * (x >> 12) + (e & (kM - 1));
-            v |= ((e >> 12) & 0xFFu) << (8 * p);
-            if (x < kLower) {
-              x = (x << 16) | (cur & 0xFFFFu);
-              used++;
-              if (two) {
-                cur >>= 16;
-              } else {
-                cur = nxt;
-                nxt = jn < maxp ? __ldg(np) : 0u;
-                np += 32;
-                jn++;
-              }
-              two = !two;
-              if (x < kLower) bad = true;
-            }
-          }
-          out[32ull * k] = (T)v;
-        }
-        if (used > 2 * maxp) bad = true;  // read past its words
-      } else {
-        uint64_t q = 0;     // pending words, the next in bits 0-15
-        uint32_t c = 0;     // words in q
-        uint32_t added = 0; // pairs appended to q
-        uint32_t pre = maxp > 0 ? __ldg(P) : 0u;  // the pair to append next
-        const uint32_t* pn = P + 32;
-        auto top_up = [&]() {
-          if (c < 2) {
-            q |= (uint64_t)pre << (c ? 16 : 0);
-            c += 2;
-            added++;
-            pre = added < maxp ? __ldg(pn) : 0u;
-            pn += 32;
-          }
-        };
-        auto symbol = [&](int p) -> uint32_t {
+        for (int p = 0; p < W; p++) {
           const uint32_t e = s_tab[p * kM + (x & (kM - 1))];
-          const uint32_t qx = x >> 12;
-          x = (e >> 20) * qx + (qx + (e & (kM - 1)));
-          const bool need = x < kLower;
-          x = need ? (x << 16) | ((uint32_t)q & 0xFFFFu) : x;
-          q = need ? q >> 16 : q;
-          c -= need ? 1u : 0u;
-          bad = bad || (need && x < kLower);
-          return (e >> 12) & 0xFFu;
-        };
-        if constexpr (W == 1) {
-          for (uint32_t k = 0; k < nk; k += 2) {
-            top_up();
-            out[32ull * k] = (T)symbol(0);
-            if (k + 1 < nk) out[32ull * (k + 1)] = (T)symbol(0);
-          }
-        } else {
-          for (uint32_t k = 0; k < nk; k++) {
-            top_up();
-            uint32_t v = symbol(0);
-            v |= symbol(1) << 8;
-            if constexpr (W == 4) {
-              top_up();
-              v |= symbol(2) << 16;
-              v |= symbol(3) << 24;
+          x = ((e >> 20) + 1) * (x >> 12) + (e & (kM - 1));
+          v |= ((e >> 12) & 0xFFu) << (8 * p);
+          if (x < kLower) {
+            if (j >= maxp) bad = true;
+            x = (x << 16) | (half ? cur >> 16 : cur & 0xFFFFu);
+            if (half) {
+              cur = nxt;
+              j++;
+              nxt = j + 1 < maxp ? __ldg(P + 32ull * (j + 1)) : 0u;
             }
-            out[32ull * k] = (T)v;
+            half = !half;
+            if (x < kLower) bad = true;
           }
         }
-        if (2 * added - c > 2 * maxp) bad = true;  // read past its words
+        out[32ull * k] = (T)v;
       }
       if (x != kLower) bad = true;
     }
@@ -524,7 +409,7 @@ template <> struct Shape<4> { static constexpr int kThreads = 512, kMinBlocks = 
 
 template <int W>
 cudaError_t launch_width(const uint8_t* coded, uint64_t bytes, const tmd_frame_arrays& dst,
-                         uint32_t* status, cudaStream_t st, int variant) {
+                         uint32_t* status, cudaStream_t st) {
   constexpr int kT = Shape<W>::kThreads, kB = Shape<W>::kMinBlocks;
   void* const ptr[kFields] = {dst.qpt,     dst.row,         dst.slice,        dst.pad,
                               dst.time,    dst.ncl,         dst.qtot_a,       dst.qmax_a,
@@ -552,10 +437,7 @@ cudaError_t launch_width(const uint8_t* coded, uint64_t bytes, const tmd_frame_a
     blocks += std::max<uint32_t>(1, (F.nch + kT / 32 - 1) / (kT / 32));
   }
   const int smem = W * (int)kM * 4;
-  auto kern = variant == 3   ? k_rans_decode<W, kT, kB, 3>
-              : variant == 2 ? k_rans_decode<W, kT, kB, 2>
-              : variant == 1 ? k_rans_decode<W, kT, kB, 1>
-                             : k_rans_decode<W, kT, kB, 0>;
+  auto kern = k_rans_decode<W, kT, kB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<blocks, kT, smem, st>>>(J);
@@ -651,7 +533,6 @@ extern "C" int tmd_rans_decode(tmd_handle* h, const void* coded, uint64_t coded_
   if (rc != TMD_OK) return rc;
   const uint8_t* c = static_cast<const uint8_t*>(coded);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int var = h->tune_rans_variant;
   // the 4-byte streams (the fewest and longest lane streams) on the second
   // stream beside the 2- and 1-byte streams, joined back at the end
   const bool two = h->tune_rans_overlap && h->aux && h->fork && h->join;
@@ -660,16 +541,16 @@ extern "C" int tmd_rans_decode(tmd_handle* h, const void* coded, uint64_t coded_
     if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->aux, h->fork, 0), "cudaStreamWaitEvent");
     if (rc != TMD_OK) return rc;
   }
-  rc = tmd_cuda_check(h, launch_width<4>(c, coded_bytes, *dst, status, two ? h->aux : st, var),
+  rc = tmd_cuda_check(h, launch_width<4>(c, coded_bytes, *dst, status, two ? h->aux : st),
                       "k_rans_decode<4>");
   if (rc != TMD_OK) return rc;
   if (two) {
     rc = tmd_cuda_check(h, cudaEventRecord(h->join, h->aux), "cudaEventRecord");
     if (rc != TMD_OK) return rc;
   }
-  rc = tmd_cuda_check(h, launch_width<2>(c, coded_bytes, *dst, status, st, var), "k_rans_decode<2>");
+  rc = tmd_cuda_check(h, launch_width<2>(c, coded_bytes, *dst, status, st), "k_rans_decode<2>");
   if (rc != TMD_OK) return rc;
-  rc = tmd_cuda_check(h, launch_width<1>(c, coded_bytes, *dst, status, st, var), "k_rans_decode<1>");
+  rc = tmd_cuda_check(h, launch_width<1>(c, coded_bytes, *dst, status, st), "k_rans_decode<1>");
   if (rc != TMD_OK || !two) return rc;
   return tmd_cuda_check(h, cudaStreamWaitEvent(st, h->join, 0), "cudaStreamWaitEvent");
 }

@@ -200,10 +200,12 @@ __global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, Pla
     for (uint32_t b = tid; b < (uint32_t)kNBin; b += 1024) F.att_count[b] = 0u;
 }
 
-// trackStart and decode order.  A block first counts its tracks per length
-// bucket in shared memory and reserves each bucket's range of the order with
-// one global atomic per bucket; the order of tracks of equal length is
-// arbitrary (it only changes which warp decodes a track, not a result).
+// trackStart, the head bitmap (bit trackStart[t] of every track, for
+// k_key_rank) and the decode order.  A block first counts its tracks per
+// length bucket in shared memory and reserves each bucket's range of the
+// order with one global atomic per bucket; the order of tracks of equal
+// length is arbitrary (it only changes which warp decodes a track, not a
+// result).
 __global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, PlanDev plan) {
   __shared__ uint32_t s_cnt[kLenBuckets];
   uint32_t tot;
@@ -239,57 +241,11 @@ __global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, Pla
     const uint32_t t = t0 + k;
     if (t < nt) {
       track_start[t] = start;
+      if (F.heads) atomicOr(&F.heads[start >> 5], 1u << (start & 31));
       order[s_cnt[n[k] < kLenBuckets ? n[k] : kLenBuckets - 1] + slot[k]] = t;
       start += n[k];
       if (t == nt - 1) track_start[nt] = start;
     }
-  }
-}
-
-// Decode order in which the decoder can place records itself: tile by tile
-// (ranking tiles of kTile clusters), the tracks that start in the tile, longest
-// first (warps then get tracks of similar length, and all records of a tile
-// are written within a short time, so partly written lines of the native list
-// complete in L2).  One block per tile; tracks of equal length in any order.
-constexpr int kOrderBuckets = 256;
-__global__ void __launch_bounds__(256) k_chunk_order(const FrameDev* frames, PlanDev plan) {
-  __shared__ uint32_t s_cnt[kOrderBuckets];
-  __shared__ uint32_t s_lo, s_hi;
-  uint32_t tot;
-  const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, blockIdx.x);
-  const FrameDev& F = frames[f];
-  if (*F.status & kStCount) return;
-  const uint32_t c = blockIdx.x - plan.pre_tile[f];
-  const uint32_t nt = F.n_tracks;
-  const uint32_t* __restrict__ ts = F.track_start;
-  if (threadIdx.x < 2) {
-    // first track starting at or after J (track_start is non-decreasing)
-    const uint32_t J = (c + threadIdx.x) * (uint32_t)kTile;
-    uint32_t lo = 0, hi = nt;  // answer in [lo, hi]
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (ts[mid] < J) lo = mid + 1; else hi = mid;
-    }
-    if (threadIdx.x == 0) s_lo = lo; else s_hi = lo;
-  }
-  for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0u;
-  __syncthreads();
-  const uint32_t t_lo = s_lo, t_hi = s_hi;
-  // bucket kOrderBuckets - 1 - min(length, 255): longest first
-  for (uint32_t t = t_lo + threadIdx.x; t < t_hi; t += blockDim.x) {
-    const uint32_t n = F.ncl[t];
-    atomicAdd(&s_cnt[kOrderBuckets - 1 - (n < kOrderBuckets - 1 ? n : kOrderBuckets - 1)], 1u);
-  }
-  __syncthreads();
-  const uint32_t v = s_cnt[threadIdx.x];
-  const uint32_t e = block_excl_scan<256>(v, tot);
-  s_cnt[threadIdx.x] = e;
-  __syncthreads();
-  uint32_t* __restrict__ order = F.order;
-  for (uint32_t t = t_lo + threadIdx.x; t < t_hi; t += blockDim.x) {
-    const uint32_t n = F.ncl[t];
-    const uint32_t b = kOrderBuckets - 1 - (n < kOrderBuckets - 1 ? n : kOrderBuckets - 1);
-    order[t_lo + atomicAdd(&s_cnt[b], 1u)] = t;
   }
 }
 

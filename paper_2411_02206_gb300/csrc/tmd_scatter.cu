@@ -3,23 +3,13 @@
 //
 // Cluster j of ranking tile t with key b and rank r goes to native index
 //   tileBase[t][b] + r
-// (k_count_rank, k_tile_base).  The record is assembled from the decoded pad
+// (k_key_rank, k_tile_base).  The record is assembled from the decoded pad
 // and time codes (k_track_decode) and the charge streams.  The destinations of
 // consecutive clusters are unrelated (consecutive clusters of a track lie in
 // different rows), so writing records in input order costs two L2 write
-// requests per 12-byte record.  Variant 1 lets three lanes write the three
-// words of one record in the same store instruction; variant 2 regroups a
-// whole tile first: a
-// thread-block cluster of kScatCta CTAs loads the tile, and every record is
-// sent through distributed shared memory to the CTA that owns its place in the
-// tile's records ordered by (bin, rank); each CTA then writes its share in that
-// order, where a (tile, bin) run -- about six records for the Pb-Pb frame --
-// is contiguous in the native list.
-#include <cooperative_groups.h>
-
+// requests per 12-byte record; variant 1 lets three lanes write the three
+// words of one record in the same store instruction.
 #include "tmd_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace tmd {
 
@@ -117,149 +107,13 @@ __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev*
   if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(frames[f].status, kStLimit);
 }
 
-// Variant 2.  One cluster of kScatCta CTAs per ranking tile; CTA q loads
-// clusters [q, q + 1) * kTile / kScatCta of the tile (8 per thread, strided),
-// computes each record's place l = lbase[b] + r among the tile's records in
-// (bin, rank) order (lbase: the exclusive scan of the tile histogram), and
-// stores {record, b} into the shared memory of CTA l / chunk (chunk =
-// ceil(N / kScatCta), N records in the tile).  After the cluster barrier each
-// CTA writes its chunk in that order, record l to tileBase[t][b] + l -
-// lbase[b]: consecutive threads write adjacent records of a (tile, bin) run,
-// and the bin bases are read in bin order.
-__global__ void __cluster_dims__(kScatCta, 1, 1) __launch_bounds__(kScatThreads2, 2)
-    k_att_scatter_cluster(const FrameDev* frames, PlanDev plan) {
-  extern __shared__ uint4 s_dyn[];
-  uint4* s_buf = s_dyn;                                                   // kTile / kScatCta
-  uint16_t* s_lbase = reinterpret_cast<uint16_t*>(s_dyn + kTile / kScatCta);  // kNBin
-  __shared__ uint32_t s_part[kScatThreads2 / 32];
-  __shared__ uint32_t s_total;
-  cg::cluster_group cluster = cg::this_cluster();
-  const uint32_t q = cluster.block_rank();
-  const uint32_t gtile = blockIdx.x / kScatCta;
-  const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
-  const FrameDev& F = frames[f];
-  if (*F.status & kStCount) return;  // the same for every CTA of the cluster
-  const uint32_t tile = gtile - plan.pre_tile[f];
-  const uint32_t n_att = F.n_att, n_total = F.n_att + F.n_unatt;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint16_t* __restrict__ keys = F.keys;
-  const uint16_t* __restrict__ rank = F.rank;
-  const uint16_t* __restrict__ kpad = F.kf_pad;
-  const uint32_t* __restrict__ ktime = F.kf_time;
-  const uint16_t* __restrict__ qtot = F.qtot_a;
-  const uint16_t* __restrict__ qmax = F.qmax_a;
-  const uint8_t* __restrict__ flags = F.flags_a;
-  const uint8_t* __restrict__ sigp = F.sigp_a;
-  const uint8_t* __restrict__ sigt = F.sigt_a;
-  constexpr uint32_t kPerCta = kTile / kScatCta;
-  constexpr int kPerThread = kPerCta / kScatThreads2;
-  const uint32_t jb = tile * (uint32_t)kTile + q * kPerCta;
-  // the records of this CTA's slice, loaded before the histogram scan so
-  // that the loads are in flight while it runs
-  uint4 rec[kPerThread];  // record words, key | rank << 16 (all ones: no cluster)
-#pragma unroll
-  for (int u = 0; u < kPerThread; u++) {
-    const uint32_t j = jb + u * kScatThreads2 + tid;
-    rec[u].w = 0xFFFFFFFFu;
-    if (j < n_att) {
-      rec[u].x = (ktime[j] & 0xFFFFFFu) | ((uint32_t)flags[j] << 24);
-      rec[u].y = (uint32_t)kpad[j] | ((uint32_t)sigt[j] << 16) | ((uint32_t)sigp[j] << 24);
-      rec[u].z = (uint32_t)qmax[j] | ((uint32_t)qtot[j] << 16);
-      rec[u].w = (uint32_t)keys[j] | ((uint32_t)rank[j] << 16);
-    }
-  }
-  // lbase: exclusive scan of the tile's histogram over the bins
-  {
-    constexpr int kPer = (kNBin + kScatThreads2 - 1) / kScatThreads2;
-    const uint16_t* __restrict__ hist = F.tile_hist + (size_t)tile * kNBin;
-    uint32_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t b = tid * kPer + i;
-      sum += b < (uint32_t)kNBin ? hist[b] : 0u;
-    }
-    uint32_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_part[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      const uint32_t v = lane < kScatThreads2 / 32 ? s_part[lane] : 0u;
-      uint32_t z = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
-        if (lane >= o) z += y;
-      }
-      if (lane < kScatThreads2 / 32) s_part[lane] = z - v;
-      if (lane == 31) s_total = z;
-    }
-    __syncthreads();
-    uint32_t run = s_part[wid] + x - sum;
-#pragma unroll
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t b = tid * kPer + i;
-      if (b < (uint32_t)kNBin) {
-        s_lbase[b] = (uint16_t)run;
-        run += hist[b];
-      }
-    }
-  }
-  __syncthreads();
-  const uint32_t n_tile = s_total;
-  const uint32_t chunk = (n_tile + kScatCta - 1) / kScatCta;
-  cluster.sync();  // every CTA of the cluster is running before remote stores
-#pragma unroll
-  for (int u = 0; u < kPerThread; u++) {
-    if (rec[u].w != 0xFFFFFFFFu) {
-      const uint32_t l = (uint32_t)s_lbase[rec[u].w & 0xFFFFu] + (rec[u].w >> 16);  // (bin, rank) order
-      if (l < n_tile) {
-        const uint32_t owner = l / chunk;
-        uint4* remote = cluster.map_shared_rank(s_buf, owner);
-        remote[l - owner * chunk] = rec[u];
-      }
-    }
-  }
-  cluster.sync();  // all records are in place
-  const uint32_t lo = q * chunk;
-  const uint32_t n_own = n_tile > lo ? min(chunk, n_tile - lo) : 0u;
-  const uint32_t* __restrict__ tbase = F.tile_base + (size_t)tile * kNBin;
-  uint32_t* __restrict__ nat = reinterpret_cast<uint32_t*>(F.native);
-  uint32_t st = 0;
-  // word by word: consecutive threads write consecutive words of the sorted
-  // records, contiguous in the native list along each (tile, bin) run
-  for (uint32_t w = tid; w < 3 * n_own; w += kScatThreads2) {
-    const uint32_t l = w / 3, c = w - 3 * l;
-    const uint4 r = s_buf[l];
-    const uint32_t b = r.w & 0xFFFFu;
-    const uint32_t d = __ldg(tbase + b) + (lo + l - s_lbase[b]);
-    if (d < n_total) {
-      nat[(size_t)d * 3 + c] = c == 0 ? r.x : (c == 1 ? r.y : r.z);
-    } else {
-      st = kStLimit;
-    }
-  }
-  if (__syncthreads_or(st != 0) && tid == 0) atomicOr(frames[f].status, kStLimit);
-}
-
-cudaError_t prepare_att_scatter() {
-  return cudaFuncSetAttribute(k_att_scatter_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kScatClusterSmem);
-}
-
 void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan) {
-  switch (variant) {
-    case 1: k_att_scatter<1, 4><<<n_tiles * (kTile / (kScatThreads * 4)), kScatThreads, 0, st>>>(frames, plan); break;
-    case 2:
-      k_att_scatter_cluster<<<n_tiles * kScatCta, kScatThreads2, kScatClusterSmem, st>>>(frames, plan);
-      break;
-    case 3: k_att_scatter<1, 2><<<n_tiles * (kTile / (kScatThreads * 2)), kScatThreads, 0, st>>>(frames, plan); break;
-    default: k_att_scatter<0, 4><<<n_tiles * (kTile / (kScatThreads * 4)), kScatThreads, 0, st>>>(frames, plan); break;
-  }
+  const uint32_t grid = n_tiles * (kTile / (kScatThreads * 4));
+  if (variant == 0)
+    k_att_scatter<0, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);
+  else
+    k_att_scatter<1, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);
 }
 
 }  // namespace tmd

@@ -1,9 +1,9 @@
 // tmd_tune.cu -- tuning parameters and the autotuner.
 //
 // The parameters only change how the work is laid out (the staging-round
-// variant of the track decoder, the duplicate-key handling of the ranking
-// kernel, and how many blocks per SM the persistent decoders start); every
-// setting produces identical output.  tmd_autotune
+// variant of the track decoder, the store pattern of the record scatter, the
+// second stream of the unattached decode, and how many blocks per SM the
+// persistent decoders start); every setting produces identical output.  tmd_autotune
 // times the decode chain on the caller's frames for each candidate, keeps the
 // fastest, and stores it in the autotune cache (a small JSON file keyed by the
 // GPU name and SM count) when the handle was created with one.
@@ -22,16 +22,12 @@ struct Param {
   int lo, hi;
 };
 const Param kParams[] = {
-    {"decode_variant", &tmd_handle::tune_decode_variant, 0, 3},
-    {"rank_variant", &tmd_handle::tune_rank_variant, 0, 2},
-    {"scatter_variant", &tmd_handle::tune_scatter_variant, 0, 3},
-    {"overlap", &tmd_handle::tune_overlap, 0, 1},
-    {"place", &tmd_handle::tune_place, 0, 2},
-    {"prekey", &tmd_handle::tune_prekey, 0, 1},
+    {"decode_variant", &tmd_handle::tune_decode_variant, 0, 1},
+    {"scatter_variant", &tmd_handle::tune_scatter_variant, 0, 1},
+    {"overlap", &tmd_handle::tune_overlap, 0, 2},
     {"unatt_variant", &tmd_handle::tune_unatt_variant, 0, 1},
     {"decode_blocks_per_sm", &tmd_handle::tune_decode_bps, 0, 64},
     {"unatt_blocks_per_sm", &tmd_handle::tune_unatt_bps, 0, 64},
-    {"rans_variant", &tmd_handle::tune_rans_variant, 0, 3},
     {"rans_overlap", &tmd_handle::tune_rans_overlap, 0, 1},
 };
 
@@ -123,12 +119,9 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
     std::vector<int> values;
   };
   const Axis axes[] = {
-      {&tmd_handle::tune_place, {0, 1, 2}},
-      {&tmd_handle::tune_prekey, {0, 1}},
-      {&tmd_handle::tune_decode_variant, {0, 1, 2, 3}},
-      {&tmd_handle::tune_rank_variant, {0, 1, 2}},
-      {&tmd_handle::tune_scatter_variant, {0, 1, 2}},  // 3 differs from 1 within noise
-      {&tmd_handle::tune_overlap, {0, 1}},
+      {&tmd_handle::tune_decode_variant, {0, 1}},
+      {&tmd_handle::tune_scatter_variant, {0, 1}},
+      {&tmd_handle::tune_overlap, {0, 1, 2}},
       {&tmd_handle::tune_unatt_variant, {0, 1}},
       {&tmd_handle::tune_unatt_bps, {0, 1, 2, 3, 4}},
   };
@@ -152,15 +145,9 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
   if (!h->autotune_cache.empty()) {
     FILE* f = fopen(h->autotune_cache.c_str(), "w");
     if (f) {
-      fprintf(f, "{\"%s\": {\"decode_variant\": %d, \"rank_variant\": %d, "
-                 "\"scatter_variant\": %d, \"overlap\": %d, \"place\": %d, \"prekey\": %d, "
-                 "\"unatt_variant\": %d, "
-                 "\"decode_blocks_per_sm\": %d, \"unatt_blocks_per_sm\": %d, "
-                 "\"chain_ms\": %.4f}}\n",
-              device_key(h).c_str(), h->tune_decode_variant, h->tune_rank_variant,
-              h->tune_scatter_variant, h->tune_overlap, h->tune_place, h->tune_prekey,
-              h->tune_unatt_variant,
-              h->tune_decode_bps, h->tune_unatt_bps, best);
+      fprintf(f, "{\"%s\": {", device_key(h).c_str());
+      for (const Param& p : kParams) fprintf(f, "\"%s\": %d, ", p.name, h->*(p.field));
+      fprintf(f, "\"chain_ms\": %.4f}}\n", best);
       fclose(f);
     }
   }

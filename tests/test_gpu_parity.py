@@ -197,16 +197,15 @@ def test_full_size_pbpb_frame(dec):
 
 def test_every_tuning_setting_gives_the_oracle_result(dec):
     """Tuning parameters change only how work is laid out: every combination
-    of decoder, ranking and scatter variant must reproduce the oracle."""
-    from paper_2411_02206_gb300 import frames
+    of decoder staging, scatter stores, unattached write-out and second-stream
+    placement must reproduce the oracle."""
+    from paper_2411_02206_gb300 import frames, tmd
     truth = synth.make_truth(n_tracks=3000, n_unatt=60_000, seed=9, looper_frac=0.4,
                              max_legs=4, pt_mean=0.3)
     of = G.oracle_frame(truth)
     ora = O.decode(of)
     dev = frames.to_torch(of, "cuda:0")
-    saved = {k: dec.tmd_tune_get(k) for k in ("decode_variant", "rank_variant",
-                                               "scatter_variant", "overlap",
-                                               "unatt_variant", "place", "prekey")}
+    saved = {k: dec.tmd_tune_get(k) for k in tmd.tune_keys()}
 
     def check(what):
         native, rs, att, st = dec.decode(dev)
@@ -215,26 +214,19 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
         G.assert_same_decode(gpu, ora, what)
 
     try:
-        for pk in range(2):
-            dec.tmd_tune_set("prekey", pk)
-            for pl in range(3):
-                dec.tmd_tune_set("place", pl)
-                for uv in range(2):
-                    dec.tmd_tune_set("unatt_variant", uv)
-                    check(f"prekey {pk} place {pl} unatt {uv}")
-                for ov in range(2):
-                    dec.tmd_tune_set("overlap", ov)
-                    for dv in range(4):
-                        dec.tmd_tune_set("decode_variant", dv)
-                        what = f"prekey {pk} place {pl} overlap {ov} decode {dv}"
-                        if pl != 0:  # only the input-order scatter has ranking/scatter variants
-                            check(what)
-                            continue
-                        for rv in range(3):
-                            for sv in range(4):
-                                dec.tmd_tune_set("rank_variant", rv)
-                                dec.tmd_tune_set("scatter_variant", sv)
-                                check(f"{what} rank {rv} scatter {sv}")
+        for ov in range(3):
+            dec.tmd_tune_set("overlap", ov)
+            for dv in range(2):
+                dec.tmd_tune_set("decode_variant", dv)
+                for sv in range(2):
+                    dec.tmd_tune_set("scatter_variant", sv)
+                    for uv in range(2):
+                        dec.tmd_tune_set("unatt_variant", uv)
+                        check(f"overlap {ov} decode {dv} scatter {sv} unatt {uv}")
+        for bps in (1, 2):
+            dec.tmd_tune_set("decode_blocks_per_sm", bps)
+            dec.tmd_tune_set("unatt_blocks_per_sm", bps)
+            check(f"blocks per sm {bps}")
     finally:
         for k, v in saved.items():
             dec.tmd_tune_set(k, v)
@@ -257,19 +249,17 @@ def test_unaligned_caller_arrays(dec):
         buf = torch.zeros(t.numel() + 1, dtype=t.dtype, device=t.device)
         buf[1:] = t
         shifted[k] = buf[1:]
-    place = dec.tmd_tune_get("place")
-    for pl, sv in ((0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (2, 1)):
-        dec.tmd_tune_set("place", pl)
+    saved = {k: dec.tmd_tune_get(k) for k in ("scatter_variant", "decode_variant")}
+    for sv in range(2):
         dec.tmd_tune_set("scatter_variant", sv)
-        for dv in range(4):
+        for dv in range(2):
             dec.tmd_tune_set("decode_variant", dv)
             native, rs, att, st = dec.decode(shifted)
             gpu = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
                    frames.to_numpy(att, np.uint32), int(st.item()))
-            G.assert_same_decode(gpu, ora, f"unaligned, place {pl} scatter {sv} decode {dv}")
-    dec.tmd_tune_set("scatter_variant", 1)
-    dec.tmd_tune_set("decode_variant", 3)
-    dec.tmd_tune_set("place", place)
+            G.assert_same_decode(gpu, ora, f"unaligned, scatter {sv} decode {dv}")
+    for k, v in saved.items():
+        dec.tmd_tune_set(k, v)
 
 
 def test_host_stream_pipeline(dec):

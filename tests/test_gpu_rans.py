@@ -171,27 +171,24 @@ def test_full_size_pbpb_frame(dec):
         assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("overlap", [0, 1])
-def test_every_decoder_setting(dec, variant, overlap):
-    """Every word-refill variant, with and without the second stream, gives
-    the same streams (and the same corruption status)."""
+def test_every_decoder_setting(dec, overlap):
+    """With and without the second stream, the entropy decoder gives the same
+    streams (and the same corruption status)."""
     from paper_2411_02206_gb300 import tmd
-    dec.tmd_tune_set("rans_variant", variant)
     dec.tmd_tune_set("rans_overlap", overlap)
     try:
         counts = (300, 3 * CHUNK + 5, 2 * CHUNK - 3)
-        rng = np.random.default_rng(variant * 2 + overlap)
+        rng = np.random.default_rng(2 + overlap)
         fr = _random_frame(rng, *counts)
         blob = tmd.rans_encode(fr)
         got, status = dec.rans_decode(_upload(blob), *counts)
         assert int(status.item()) == 0
-        _same_streams(got, fr, f"variant {variant} overlap {overlap}")
+        _same_streams(got, fr, f"overlap {overlap}")
         for name, b, c in _corruptions(blob, counts):
             _, st = dec.rans_decode(_upload(b), *c)
             assert int(st.item()) & tmd.STATUS_CODED, name
     finally:
-        dec.tmd_tune_set("rans_variant", 0)
         dec.tmd_tune_set("rans_overlap", 1)
 
 
