@@ -141,10 +141,11 @@ __device__ __forceinline__ RoundBase issue_round(uint32_t* lb, uint32_t k0, uint
 
 }  // namespace
 
-// Writes the pad code and the time code of every attached cluster.
+// Writes the pad code and the time code of every attached cluster of the
+// tracks of one part (tasks of 32 tracks taken from counters[4 + part]).
 template <int R, int MINB>
 __global__ void __launch_bounds__(kDecodeThreads, MINB)
-    k_track_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
+    k_track_decode(const FrameDev* frames, PlanDev plan, uint32_t part) {
   static_assert(R == 8 || R == 16, "round length");
   using Lay = AsyncLayout<R>;
   constexpr int P = R + 1;   // pitch of the output rows
@@ -157,13 +158,17 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t sq = lane % R, sg = lane / R;
   AsyncStage<R>& S = stage[threadIdx.x >> 5];
+  const uint32_t nf = plan.n_frames;
+  const uint32_t* task_pre = plan.part_task_pre + (size_t)part * (nf + 1);
+  const uint32_t n_tasks = task_pre[nf];
   for (;;) {
-    const uint32_t task = next_task(&plan.counters[0]);
+    const uint32_t task = next_task(&plan.counters[4 + part]);
     if (task >= n_tasks) break;
-    const uint32_t f = find_frame(plan.pre_kt, plan.n_frames, task);
+    const uint32_t f = find_frame(task_pre, nf, task);
     const FrameDev& F = frames[f];
     if (*F.status & kStCount) continue;
-    const uint32_t idx = (task - plan.pre_kt[f]) * 32u + lane;
+    const uint32_t idx = plan.part_lo[(size_t)part * nf + f] + (task - task_pre[f]) * 32u + lane;
+    const uint32_t idx_end = plan.part_hi[(size_t)part * nf + f];
     const uint8_t* __restrict__ rd_s = F.row_diff;
     const uint8_t* __restrict__ sld_s = F.sld;
     const uint16_t* __restrict__ pr_s = F.pad_res;
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
     uint32_t* __restrict__ time_o = F.kf_time;
     uint32_t j0 = 0, n = 0, dm1 = 0, pad0 = 0, time0 = 0, st = 0;
     Track s;
-    if (idx < F.n_tracks) {
+    if (idx < idx_end) {
       const uint32_t t = F.order[idx];
       j0 = F.track_start[t];
       n = F.ncl[t];
@@ -250,11 +255,11 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
 // Variants: 0 -> rounds of 16 steps (4 blocks per SM), 1 -> rounds of 8
 // steps (6 blocks per SM).
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t n_tasks) {
+                         PlanDev plan, uint32_t part) {
   if (variant == 1)
-    k_track_decode<8, 6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks);
+    k_track_decode<8, 6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, part);
   else
-    k_track_decode<16, 4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks);
+    k_track_decode<16, 4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, part);
 }
 
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm) {

@@ -25,10 +25,10 @@ namespace tmd {
 //          32-byte sector) instead of two.
 template <int V, int U>
 __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev* frames,
-                                                                 PlanDev plan) {
+                                                                 PlanDev plan, uint32_t tile_lo) {
   constexpr uint32_t kPerBlock = kScatThreads * U;
   constexpr uint32_t kBlocksPerTile = kTile / kPerBlock;
-  const uint32_t gtile = blockIdx.x / kBlocksPerTile;
+  const uint32_t gtile = tile_lo + blockIdx.x / kBlocksPerTile;
   const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
   const FrameDev& F = frames[f];
   if (*F.status & kStCount) return;
@@ -107,13 +107,13 @@ __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev*
   if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(frames[f].status, kStLimit);
 }
 
-void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
-                        PlanDev plan) {
+void launch_att_scatter(int variant, uint32_t tile_lo, uint32_t n_tiles, cudaStream_t st,
+                        const FrameDev* frames, PlanDev plan) {
   const uint32_t grid = n_tiles * (kTile / (kScatThreads * 4));
   if (variant == 0)
-    k_att_scatter<0, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);
+    k_att_scatter<0, 4><<<grid, kScatThreads, 0, st>>>(frames, plan, tile_lo);
   else
-    k_att_scatter<1, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);
+    k_att_scatter<1, 4><<<grid, kScatThreads, 0, st>>>(frames, plan, tile_lo);
 }
 
 }  // namespace tmd

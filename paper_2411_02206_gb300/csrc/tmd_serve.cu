@@ -212,7 +212,7 @@ void TmdServer::run() {
       }
       if (rc == TMD_OK)
         rc = tmd_enqueue(h, (uint32_t)ins.size(), ins.data(), outs.data(), nullptr, nullptr,
-                         b->scratch, record[free_stream], b->dev_record, cs, false);
+                         b->scratch, record[free_stream], b->dev_record, cs, false, nullptr);
       cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
       cudaEventRecord(b->done, cs);
       if (b->scratch) cudaFreeAsync(b->scratch, cs);
