@@ -15,14 +15,17 @@
 //
 //   k_key_rank  tile = kTile consecutive clusters, one block, warp w =
 //               kTileSub consecutive clusters of the tile.  Pass 1 walks the
-//               warp's clusters in steps of 32 (one per lane): the track
-//               heads of a step come from the head bitmap (bit j set when
-//               cluster j starts a track, written by the track scan), a lane
-//               loads its header (a head) or its row and sector difference,
-//               and a warp scan with a carry from the previous step gives the
-//               row and sector of every cluster.  The loads of 8 steps are
-//               issued before their scans.  The keys are written and counted
-//               per warp (packed 16-bit shared-memory counters).  The block
+//               warp's clusters in blocks of 256, 8 consecutive clusters per
+//               lane: the track heads come from the head bitmap (bit j set
+//               when cluster j starts a track, written by the track scan); a
+//               lane's clusters after the first of their track use a
+//               contiguous range of row and sector differences, loaded as
+//               aligned words; each lane scans its 8 clusters sequentially
+//               and one segmented warp scan of the lanes' totals, with a
+//               carry from the previous block, gives every cluster its row
+//               and sector.  The keys are written (one 16-byte store per
+//               lane) and counted per warp (packed 16-bit shared-memory
+//               counters).  The block
 //               then turns the per-warp counts into per-warp exclusive
 //               offsets and writes the tile histogram; pass 2 reads the keys
 //               back in stream order and gives every cluster its rank among
@@ -55,9 +58,12 @@ __global__ void __launch_bounds__(256, 2) k_key_rank(const FrameDev* frames, Pla
   __syncwarp();
   const uint32_t j_begin = tile * (uint32_t)kTile + wid * (uint32_t)kTileSub;
   const uint32_t j_end = min(j_begin + (uint32_t)kTileSub, n_att);
-  const uint32_t le_mask = lanemask_le();
   // pass 1: keys (segmented scan of the row and sector differences) and
-  // per-warp counts
+  // per-warp counts.  Blocks of 256 clusters; lane l takes clusters
+  // [jb + 8 l, jb + 8 l + 8).  Its non-first clusters use the consecutive
+  // differences [D0, D0 + m) (a track's first cluster has none), which it
+  // loads as aligned words: an aligned word holding a byte of the array lies
+  // in the same page as that byte.
   if (j_begin < j_end) {
     const uint32_t* __restrict__ ts = F.track_start;
     const uint8_t* __restrict__ rd = F.row_diff;
@@ -73,8 +79,8 @@ __global__ void __launch_bounds__(256, 2) k_key_rank(const FrameDev* frames, Pla
       if (ts[mid] <= j_begin) lo = mid; else hi = mid - 1;
     }
     const uint32_t t0 = lo, s0 = ts[t0];
-    // carry = row and sector of cluster j_begin - 1 when it lies in the same
-    // track (row in bits 0-15, sector in bits 16-31)
+    // carry = row (bits 0-15) and sector (bits 16-31) of cluster j_begin - 1
+    // when it lies in the same track
     uint32_t carry = 0;
     if (s0 < j_begin) {
       const uint32_t hs = hsec[t0];
@@ -88,74 +94,127 @@ __global__ void __launch_bounds__(256, 2) k_key_rank(const FrameDev* frames, Pla
       carry = ((hrow[t0] + sr) & 255u) |
               (((hs < (uint32_t)kNSec ? hs : kNSec - 1u) + ss) % (uint32_t)kNSec) << 16;
     }
-    // track of the cluster before the current step (wraps below 0 before the
-    // first track; every in-range lane has at least one head at or before it)
+    // track of the cluster before the current block (wraps below 0 before the
+    // first track; every in-range cluster has a head at or before it)
     uint32_t tb = s0 < j_begin ? t0 : t0 - 1u;
     uint32_t st = 0;
-    for (uint32_t jb = j_begin; jb < j_end; jb += 8u * 32u) {
-      // head masks of the 8 steps (jb is a multiple of 32), then all loads
-      uint32_t mw = 0;
-      if (lane < 8 && jb + 32u * lane < j_end) mw = heads[(jb >> 5) + lane];
-      uint32_t M[8], er[8], es[8];
-      uint32_t tc = tb;
+    for (uint32_t jb = j_begin; jb < j_end; jb += 256u) {
+      const uint32_t c0 = jb + 8u * lane;
+      const uint32_t nin = c0 < j_end ? min(8u, j_end - c0) : 0u;  // clusters in range
+      uint32_t bits = 0;
+      if (nin) bits = (heads[(c0 >> 5)] >> (8u * (lane & 3u))) & ((1u << nin) - 1u);
+      // heads before this lane's clusters within the block
+      const uint32_t nh = __popc(bits);
+      uint32_t hb = nh;
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        M[u] = __shfl_sync(0xffffffffu, mw, u);
-        const uint32_t j = jb + 32u * u + lane;
-        const uint32_t tj = tc + __popc(M[u] & le_mask);
-        er[u] = 0;
-        es[u] = 0;
-        if (j < j_end) {
-          if ((M[u] >> lane) & 1u) {
-            er[u] = hrow[tj];
-            es[u] = hsec[tj] | 0x100u;  // marks a header sector (checked below)
-          } else {
-            const uint32_t d = j - tj - 1u;
-            er[u] = rd[d];
-            es[u] = sld[d];
-          }
-        }
-        tc += __popc(M[u]);
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, hb, o);
+        if (lane >= (uint32_t)o) hb += y;
       }
-      tb = tc;
+      const uint32_t heads_blk = __shfl_sync(0xffffffffu, hb, 31);
+      hb -= nh;
+      const uint32_t T0 = tb + hb;          // track before cluster c0
+      const uint32_t m = nin - nh;          // differences this lane needs
+      const uint32_t D0 = c0 - T0 - 1u;     // the first of them
+      // the lane's differences: aligned words covering [D0, D0 + m)
+      uint32_t wr[3] = {0, 0, 0}, ws[3] = {0, 0, 0};
+      if (m) {
+        const uint32_t* rw = reinterpret_cast<const uint32_t*>(
+            reinterpret_cast<uintptr_t>(rd + D0) & ~(uintptr_t)3);
+        const uint32_t* sw = reinterpret_cast<const uint32_t*>(
+            reinterpret_cast<uintptr_t>(sld + D0) & ~(uintptr_t)3);
+        const uint32_t offs = (uint32_t)(reinterpret_cast<uintptr_t>(sld + D0) & 3u);
+        const uint32_t offr = (uint32_t)(reinterpret_cast<uintptr_t>(rd + D0) & 3u);
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const uint32_t j = jb + 32u * u + lane;
-        const bool in = j < j_end;
-        uint32_t sec_in;
-        if (es[u] & 0x100u) {  // a track's first cluster: its stored sector
-          sec_in = es[u] & 255u;
-          if (in && (sec_in >= (uint32_t)kNSec || er[u] >= (uint32_t)kNRow)) st |= kStRow;
-          if (sec_in >= (uint32_t)kNSec) sec_in = kNSec - 1;
-        } else {               // a sector difference (the leg part does not move the key)
-          sec_in = es[u] % (uint32_t)kNSec;
+        for (int i = 0; i < 3; i++) {
+          if (4u * i < offr + m) wr[i] = __ldg(rw + i);
+          if (4u * i < offs + m) ws[i] = __ldg(sw + i);
         }
-        // inclusive warp scan of (row, sector); subtracting the prefix before
-        // the lane's last head restarts the sum at the track's first cluster
-        uint32_t S = er[u] | (sec_in << 16);
+        // bytes 0-7 of the lane's differences as two words per stream
+        const uint64_t r64 = ((uint64_t)wr[1] << 32 | wr[0]) >> (8 * offr);
+        const uint64_t s64 = ((uint64_t)ws[1] << 32 | ws[0]) >> (8 * offs);
+        const uint32_t r_lo = (uint32_t)r64;
+        const uint32_t r_hi = (uint32_t)(r64 >> 32) | (offr ? wr[2] << (32 - 8 * offr) : 0u);
+        const uint32_t s_lo = (uint32_t)s64;
+        const uint32_t s_hi = (uint32_t)(s64 >> 32) | (offs ? ws[2] << (32 - 8 * offs) : 0u);
+        wr[0] = r_lo; wr[1] = r_hi; ws[0] = s_lo; ws[1] = s_hi;
+      }
+      // sequential segmented prefix over the lane's clusters (zero carry in;
+      // a track's first cluster takes its stored row and sector), and the
+      // lane's aggregate since its last head
+      uint32_t pr[8], ps[8];
+      uint32_t ar = 0, as = 0, k_nh = 0;  // k_nh: differences consumed
+      uint32_t tc = T0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, S, o);
-          if (lane >= o) S += y;
+      for (int e = 0; e < 8; e++) {
+        uint32_t vr, vs;
+        if ((bits >> e) & 1u) {
+          tc++;
+          vr = hrow[tc];
+          const uint32_t hs = hsec[tc];
+          if (hs >= (uint32_t)kNSec || vr >= (uint32_t)kNRow) st |= kStRow;
+          vs = hs < (uint32_t)kNSec ? hs : kNSec - 1u;
+          ar = vr;
+          as = vs;
+        } else if ((uint32_t)e < nin) {
+          const uint32_t q = k_nh++;
+          vr = ((q < 4 ? wr[0] : wr[1]) >> (8 * (q & 3u))) & 255u;
+          vs = (((q < 4 ? ws[0] : ws[1]) >> (8 * (q & 3u))) & 255u) % (uint32_t)kNSec;
+          ar += vr;
+          as += vs;
         }
-        const uint32_t hm = M[u] & le_mask;
-        const int hp = hm ? 31 - __clz(hm) : 0;
-        const uint32_t before = __shfl_sync(0xffffffffu, S, hp > 0 ? hp - 1 : 0);
-        const uint32_t seg = hm ? (hp > 0 ? S - before : S) : S + carry;
-        const uint32_t raw = seg & 255u;
-        const uint32_t sec = (seg >> 16) % (uint32_t)kNSec;
-        carry = __shfl_sync(0xffffffffu, raw | (sec << 16), 31);
-        if (in) {
+        pr[e] = ar;
+        ps[e] = as;
+      }
+      // warp exclusive segmented scan of the lanes' aggregates: the value
+      // carried into each lane's first segment
+      const uint32_t hasf = bits != 0u;
+      uint32_t v = (ar & 255u) | ((as % (uint32_t)kNSec) << 16), fl = hasf;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        const uint32_t g = __shfl_up_sync(0xffffffffu, fl, o);
+        if (lane >= (uint32_t)o && !fl) {
+          v = ((v + y) & 255u) | ((((v >> 16) + (y >> 16)) % (uint32_t)kNSec) << 16);
+          fl = g;
+        }
+      }
+      // exclusive value for this lane: the inclusive value of lane - 1, or the
+      // block's carry when no earlier lane of the block has a head
+      uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
+      uint32_t exf = __shfl_up_sync(0xffffffffu, fl, 1);
+      if (lane == 0) { ex = 0; exf = 0; }
+      const uint32_t cin = exf ? ex
+                               : (((ex & 255u) + (carry & 255u)) & 255u) |
+                                     ((((ex >> 16) + (carry >> 16)) % (uint32_t)kNSec) << 16);
+      // keys of the lane's clusters
+      uint32_t kw[4] = {0, 0, 0, 0};
+      uint32_t seen = 0;  // a head at or before element e
+      uint32_t last = 0;
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        seen |= (bits >> e) & 1u;
+        const uint32_t raw = (seen ? pr[e] : (cin & 255u) + pr[e]) & 255u;
+        const uint32_t sec = (seen ? ps[e] : (cin >> 16) + ps[e]) % (uint32_t)kNSec;
+        last = raw | (sec << 16);
+        if ((uint32_t)e < nin) {
           uint32_t row = raw;
           if (row >= (uint32_t)kNRow) {
             st |= kStRow;
             row = kNRow - 1;
           }
           const uint32_t k = sec * kNRow + row;
-          keys[j] = (uint16_t)k;
+          kw[e >> 1] |= k << (16 * (e & 1));
           atomicAdd(&hist32[k >> 1], (k & 1u) ? 0x10000u : 1u);
         }
       }
+      if (nin == 8u) {
+        *reinterpret_cast<uint4*>(keys + c0) = make_uint4(kw[0], kw[1], kw[2], kw[3]);
+      } else {
+        for (uint32_t e = 0; e < nin; e++) keys[c0 + e] = (uint16_t)(kw[e >> 1] >> (16 * (e & 1)));
+      }
+      carry = __shfl_sync(0xffffffffu, last, 31);
+      tb += heads_blk;
     }
     st = __reduce_or_sync(0xffffffffu, st);
     if (st && lane == 0) atomicOr(F.status, st);
