@@ -264,6 +264,50 @@ int tmd_track_trace(tmd_handle* h, const tmd_frame_in* in, uint32_t n, const uin
 int tmd_encode_tracks(tmd_handle* h, const tmd_truth_in* in, const tmd_track_out* out,
                       void* stream);
 
+/* Unattached clusters as truth (any order), for tmd_encode_unattached.  All
+ * device pointers, n entries each. */
+typedef struct tmd_unatt_truth_in {
+  uint32_t n;
+  const uint8_t* row;    /* pad row, < 152 */
+  const uint8_t* sector; /* sector, < 36 */
+  const uint16_t* pad;   /* pad code */
+  const uint32_t* time;  /* time code */
+  const uint16_t* qtot;
+  const uint16_t* qmax;
+  const uint8_t* flags;
+  const uint8_t* sigma_pad;
+  const uint8_t* sigma_time;
+} tmd_unatt_truth_in;
+
+/* The unattached streams of a compressed frame (tmd_frame_in's n_unatt and
+ * per-unattached-cluster members), written by tmd_encode_unattached; device
+ * pointers; status is one u32. */
+typedef struct tmd_unatt_out {
+  uint32_t* n_unatt; /* 5472 */
+  uint16_t* pad_diff_u;
+  uint32_t* time_diff_u;
+  uint16_t* qtot_u;
+  uint16_t* qmax_u;
+  uint8_t* flags_u;
+  uint8_t* sigma_pad_u;
+  uint8_t* sigma_time_u;
+  uint32_t* status;
+} tmd_unatt_out;
+
+/* Unattached-cluster encoding (the synchronous side of Sec. 4: clusters not
+ * attached to a track are sorted by position and stored as differences to
+ * the preceding cluster).  Per (sector,row) bin, bins in order, the clusters
+ * sorted by (time, pad) ascending with ties in input order; pad_diff_u /
+ * time_diff_u = the cluster's pad / time minus those of the preceding
+ * cluster of its bin (the first of a bin minus 0), mod 2^16 / 2^32; charges,
+ * flags and sigmas in the same order; n_unatt = clusters per bin.  Stable
+ * LSD radix sort on the GPU, asynchronous on `stream`, handle scratch of
+ * about 24 bytes per cluster.  *status receives TMD_STATUS_ROW if a row >=
+ * 152 or a sector >= 36 (outputs then unspecified).  Errors: TMD_ERR_ARG
+ * (null or misaligned pointer), TMD_ERR_NOMEM, TMD_ERR_CUDA. */
+int tmd_encode_unattached(tmd_handle* h, const tmd_unatt_truth_in* in, const tmd_unatt_out* out,
+                          void* stream);
+
 /* Serving (continuous batching of frames as they arrive).  The paper has no
  * counterpart: its decoder runs several instances on streams to overlap the
  * transfers (Sec. 4, Fig. 2); admission by a memory budget and batching of

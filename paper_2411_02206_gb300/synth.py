@@ -65,6 +65,8 @@ TRUTH_ATT = ("qpt", "ncl", "row", "sector", "leg", "pad", "time", "qtot_a", "qma
              "flags_a", "sigma_pad_a", "sigma_time_a")
 UNATT = ("n_unatt", "pad_diff_u", "time_diff_u", "qtot_u", "qmax_u", "flags_u",
          "sigma_pad_u", "sigma_time_u")
+UNATT_TRUTH = ("row_u", "sector_u", "pad_u", "time_u", "qtot_u", "qmax_u", "flags_u",
+               "sigma_pad_u", "sigma_time_u")
 
 
 def _charges(rng, n):
@@ -250,6 +252,45 @@ def make_unattached(rng, n_unatt: int, empty_frac: float = 0.0, hot_frac: float 
     a = (rng.random(n_unatt) * npu).astype(np.int64)
     b = (rng.random(n_unatt) * npu).astype(np.int64)
     f["pad_diff_u"] = ((a - b) & 0xFFFF).astype(np.uint16)
+    (f["qtot_u"], f["qmax_u"], f["flags_u"], f["sigma_pad_u"], f["sigma_time_u"]) = \
+        _charges(rng, n_unatt)
+    return f
+
+
+def make_unattached_truth(rng, n_unatt: int, empty_frac: float = 0.0, hot_frac: float = 0.0,
+                          hot_share: float = 0.0, tie_frac: float = 0.0) -> dict:
+    """Unattached clusters as truth, for the unattached-cluster encoder: per
+    cluster its (sector, row), pad code (uniform over the row's pads) and time
+    code (uniform over the 4000-bin frame), in generation order (unsorted);
+    counts per (sector,row) as in make_unattached.  A fraction tie_frac of the
+    clusters repeat the (time, pad) of another cluster of their bin, so that
+    the encoder's tie rule (input order) is exercised.  Charges as for the
+    attached clusters."""
+    w = np.ones(NBIN)
+    if empty_frac > 0 or hot_frac > 0:
+        perm = rng.permutation(NBIN)
+        n_empty = int(round(empty_frac * NBIN))
+        n_hot = int(round(hot_frac * NBIN))
+        hot = perm[n_empty:n_empty + n_hot]
+        normal = perm[n_empty + n_hot:]
+        w = np.zeros(NBIN)
+        w[hot] = hot_share / max(1, n_hot)
+        w[normal] = (1.0 - hot_share) / max(1, len(normal))
+    w = w / w.sum()
+    binid = rng.choice(NBIN, size=n_unatt, p=w) if n_unatt else np.zeros(0, np.int64)
+    f = {}
+    f["row_u"] = (binid % NROW).astype(np.uint8)
+    f["sector_u"] = (binid // NROW).astype(np.uint8)
+    f["pad_u"] = (rng.random(n_unatt) * NPADS[binid % NROW] * 64).astype(np.uint16)
+    f["time_u"] = rng.integers(0, TIME_CODES, n_unatt).astype(np.uint32)
+    if tie_frac > 0 and n_unatt > 1:
+        # copy (time, pad) from the previous cluster of the same bin
+        order = np.argsort(binid, kind="stable")
+        same = np.nonzero(binid[order][1:] == binid[order][:-1])[0]
+        pick = same[rng.random(len(same)) < tie_frac]
+        dst, src = order[pick + 1], order[pick]
+        f["time_u"][dst] = f["time_u"][src]
+        f["pad_u"][dst] = f["pad_u"][src]
     (f["qtot_u"], f["qmax_u"], f["flags_u"], f["sigma_pad_u"], f["sigma_time_u"]) = \
         _charges(rng, n_unatt)
     return f

@@ -89,6 +89,20 @@ class tmd_track_out(ctypes.Structure):
     _fields_ = [(n, _P) for n in TRACK_OUT_FIELDS]
 
 
+UNATT_TRUTH_FIELDS = ["row_u", "sector_u", "pad_u", "time_u", "qtot_u", "qmax_u", "flags_u",
+                      "sigma_pad_u", "sigma_time_u"]
+UNATT_OUT_FIELDS = ["n_unatt", "pad_diff_u", "time_diff_u", "qtot_u", "qmax_u", "flags_u",
+                    "sigma_pad_u", "sigma_time_u", "status"]
+
+
+class tmd_unatt_truth_in(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32)] + [(n, _P) for n in UNATT_TRUTH_FIELDS]
+
+
+class tmd_unatt_out(ctypes.Structure):
+    _fields_ = [(n, _P) for n in UNATT_OUT_FIELDS]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -118,6 +132,8 @@ def lib():
                 "tmd_selftest_wait": [H, ctypes.POINTER(ctypes.c_uint32)],
                 "tmd_encode_tracks": [H, ctypes.POINTER(tmd_truth_in),
                                       ctypes.POINTER(tmd_track_out), _P],
+                "tmd_encode_unattached": [H, ctypes.POINTER(tmd_unatt_truth_in),
+                                          ctypes.POINTER(tmd_unatt_out), _P],
                 "tmd_submit": [H, ctypes.POINTER(tmd_frame_in), ctypes.POINTER(ctypes.c_uint64)],
                 "tmd_poll": [H, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(tmd_frame_out)],
                 "tmd_release": [H, ctypes.c_uint64],
@@ -347,6 +363,11 @@ class Decoder:
         return self._check(self._L.tmd_encode_tracks(self.h, ctypes.byref(tin), ctypes.byref(tout),
                                                      _P(_stream_ptr(stream))))
 
+    def tmd_encode_unattached(self, tin: tmd_unatt_truth_in, tout: tmd_unatt_out,
+                              stream=None) -> int:
+        return self._check(self._L.tmd_encode_unattached(
+            self.h, ctypes.byref(tin), ctypes.byref(tout), _P(_stream_ptr(stream))))
+
     def tmd_submit(self, fin: tmd_frame_in) -> int:
         rid = ctypes.c_uint64(0)
         self._check(self._L.tmd_submit(self.h, ctypes.byref(fin), ctypes.byref(rid)))
@@ -452,6 +473,28 @@ class Decoder:
                                     n_unattached, frame_out(native, row_start, att, status),
                                     stream)
         return native, row_start, att, status
+
+    def encode_unattached(self, truth: dict, stream=None) -> dict:
+        """GPU unattached-cluster encoding of device tensors row_u, sector_u,
+        pad_u, time_u and the charges; returns the unattached streams of a
+        compressed frame (n_unatt, pad_diff_u, ..., sigma_time_u) plus
+        'status'."""
+        import torch
+        n = int(truth["row_u"].numel())
+        dev = truth["row_u"].device
+        out = {"n_unatt": torch.empty(NBIN, dtype=torch.int32, device=dev),
+               "pad_diff_u": torch.empty(n, dtype=torch.int16, device=dev),
+               "time_diff_u": torch.empty(n, dtype=torch.int32, device=dev),
+               "qtot_u": torch.empty(n, dtype=torch.int16, device=dev),
+               "qmax_u": torch.empty(n, dtype=torch.int16, device=dev),
+               "flags_u": torch.empty(n, dtype=torch.uint8, device=dev),
+               "sigma_pad_u": torch.empty(n, dtype=torch.uint8, device=dev),
+               "sigma_time_u": torch.empty(n, dtype=torch.uint8, device=dev),
+               "status": torch.empty(1, dtype=torch.int32, device=dev)}
+        tin = tmd_unatt_truth_in(n, *[_ptr(truth[k]) for k in UNATT_TRUTH_FIELDS])
+        tout = tmd_unatt_out(*[_ptr(out[k]) for k in UNATT_OUT_FIELDS])
+        self.tmd_encode_unattached(tin, tout, stream)
+        return out
 
     def encode(self, truth: dict, stream=None) -> dict:
         """GPU track-model encoding of the attached truth (device tensors);
