@@ -152,19 +152,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(seed_offset: int = 0, scale: float = 1.0):
+def make_inputs(seed_offset: int = 0, scale: float = 1.0, unatt_truth: bool = True):
+    """Truth of the workload's frame: attached clusters as helix crossings and
+    (unatt_truth) the unattached clusters as unsorted truth, both encoded on
+    the GPU by the library's encoders."""
     from paper_2411_02206_gb300 import synth
     kw = dict(synth.SHAPES[WORKLOAD])
     kw["seed"] = kw["seed"] + seed_offset
     kw["n_tracks"] = int(round(kw["n_tracks"] * scale))
     kw["n_unatt"] = int(round(kw["n_unatt"] * scale))
+    kw["unatt_truth"] = unatt_truth
     return synth.make_truth(**kw), kw["seed"]
+
+
+def gpu_frame(dec, truth, device):
+    """The compressed frame of a truth, built on the GPU: the track-model
+    encoder for the attached clusters and, for unattached truth, the
+    unattached encoder.  Returns (frame, encoder outputs)."""
+    from paper_2411_02206_gb300 import frames, synth
+    dev = frames.to_torch(truth, device)
+    enc = dec.encode(dev)
+    un = dec.encode_unattached(dev) if "row_u" in truth else None
+    fr = frames.assemble(dev, enc, un)
+    if un is not None:
+        enc = dict(enc)
+        enc["unatt_status"] = un["status"]
+        for k in synth.UNATT_TRUTH:
+            del dev[k]
+    return fr, enc
 
 
 def oracle_frame(truth):
     """Compressed frame by the oracle encoder (CPU-baseline leg only)."""
     from oracle import oracle as O
     from paper_2411_02206_gb300 import synth
+    if "row_u" in truth:
+        return O.encode(truth)
     t = dict(truth)
     for k, dt, kind in O.TRUTH_FIELDS:
         if kind == "unatt":
@@ -226,7 +249,7 @@ def cpu_baseline_all_cores(frame, threads=None):
 UNIT_BYTES = {"attached": 27, "unattached": 25, "track": 11}
 # the units each decoder kernel processes
 KERNEL_UNITS = {"k_att_scatter": "attached", "k_track_decode": "attached",
-                "k_key_rank": "attached", "k_unatt_decode": "unattached"}
+                "k_count_rank": "attached", "k_unatt_decode": "unattached"}
 
 
 def kernel_bytes(name, nt, na, nu):
@@ -245,12 +268,10 @@ def moved_bytes(name, nt, na, nu):
       k_track_decode  per track a 19 B header (qpt, row, slice, pad, time,
                       ncl, track start, decode order), per cluster after the
                       first of its track 8 B of residual streams; per cluster
-                      6 B written (pad code, time code);
-      k_key_rank      per cluster after the first of its track 2 B of row and
-                      sector differences read, per cluster the 2 B key written
-                      and read back and the 2 B rank written, the head bitmap
-                      (1 bit per cluster), per ranking tile a 2 B count per
-                      bin written;
+                      8 B written (key, pad code, time code);
+      k_count_rank    per attached cluster the 2 B key read (twice) and the
+                      2 B rank written, per ranking tile a 2 B count per bin
+                      written;
       k_att_scatter   per attached cluster 17 B read (key, rank, pad code,
                       time code, 7 B of charges, sigmas and flags) and the
                       12 B native record written;
@@ -258,9 +279,9 @@ def moved_bytes(name, nt, na, nu):
                       per-bin counts read."""
     n_tiles = -(-na // 32768)
     table = {
-        "k_track_decode": 8 * (na - nt) + 19 * nt + 6 * na,
+        "k_track_decode": 8 * (na - nt) + 19 * nt + 8 * na,
         "k_att_scatter": 29 * na,
-        "k_key_rank": 2 * (na - nt) + 6 * na + na // 8 + 2 * 5472 * n_tiles,
+        "k_count_rank": 6 * na + 2 * 5472 * n_tiles,
         "k_unatt_decode": 25 * nu + 4 * 5472,
     }
     return table.get(name)
@@ -277,7 +298,7 @@ def path_bytes(nt, na, nu):
 
 KERNEL_SOURCES = {"k_track_decode": ("tmd_decode.cu", "tmd_model.cuh"),
                   "k_att_scatter": ("tmd_scatter.cu",),
-                  "k_key_rank": ("tmd_rank.cu",), "k_unatt_decode": ("tmd_unatt.cu",)}
+                  "k_count_rank": ("tmd_rank.cu",), "k_unatt_decode": ("tmd_unatt.cu",)}
 
 
 def source_sha(kernel):
@@ -397,9 +418,7 @@ def run(args):
         if legs and not args.no_serve else None
     dec = tmd.Decoder(local)
     truth, seed = make_inputs(seed_offset=rank, scale=args.scale)
-    dev_truth = frames.to_torch(truth, f"cuda:{local}")
-    enc = dec.encode(dev_truth)
-    frame = frames.assemble(dev_truth, enc)
+    frame, enc = gpu_frame(dec, truth, f"cuda:{local}")
     nt, na, nu = tmd.counts(frame)
     stream = torch.cuda.current_stream()
     native = torch.empty((na + nu, 12), dtype=torch.uint8, device=frame["ncl"].device)
@@ -410,6 +429,7 @@ def run(args):
     fout = tmd.frame_out(native, row_start, att, status)
     torch.cuda.synchronize()
     assert int(enc["status"].item()) == 0, "encoder status"
+    assert int(enc.get("unatt_status", enc["status"]).item()) == 0, "unattached encoder status"
     if not args.no_autotune:
         dec.tmd_autotune([fin], [fout], stream)
     _apply_tune(dec, args.tune)
@@ -465,13 +485,7 @@ def run(args):
     xyz_ms = start.elapsed_time(stop) / reps
     xyz_gbs = 24.0 * (na + nu) / (xyz_ms * 1e-3) / 1e9
     # end to end through the host-buffer entry point
-    host = frames.to_torch({k: truth[k] for k in truth if k not in ("sector", "leg")}, None,
-                           pin=True)
-    henc = {k: enc[k].cpu().pin_memory() for k in ("qpt", "row", "slice", "pad", "time", "ncl",
-                                                   "row_diff", "slice_leg_diff", "pad_res",
-                                                   "time_res")}
-    hframe = dict(host)
-    hframe.update(henc)
+    hframe = {n: frame[n].cpu().pin_memory() for n, _, _ in tmd.FRAME_FIELDS}
     h_native = torch.empty((na + nu, 12), dtype=torch.uint8).pin_memory()
     h_rs = torch.empty(5473, dtype=torch.int32).pin_memory()
     h_att = torch.empty(5472, dtype=torch.int32).pin_memory()
@@ -630,8 +644,8 @@ def _gen(kw):
 class FramePool:
     """Truths of many frames generated in a spawn-started process pool (the
     generator is plain numpy, one frame per task), started before the GPU work
-    so that generation overlaps it; `frames()` encodes them on the GPU as they
-    arrive and keeps only the device frames."""
+    so that generation overlaps it; `frames()` encodes them on the GPU (track
+    and unattached encoders) as they arrive and keeps only the device frames."""
 
     def __init__(self, specs, workers=None):
         import concurrent.futures as cf
@@ -642,12 +656,9 @@ class FramePool:
         self.futs = [self.ex.submit(_gen, kw) for kw in specs]
 
     def frames(self, dec, device):
-        from paper_2411_02206_gb300 import frames
         out = []
         for fut in self.futs:
-            dev = frames.to_torch(fut.result(), device)
-            enc = dec.encode(dev)
-            out.append(frames.assemble(dev, enc))
+            out.append(gpu_frame(dec, fut.result(), device)[0])
         self.ex.shutdown()
         return out
 
@@ -799,12 +810,13 @@ def serve_leg(dec, frs, n_req, device, clock_index, load=0.8):
 
 def batch_specs_c2(n):
     from paper_2411_02206_gb300 import synth
-    return synth.batch_specs(n_frames=n)
+    return [dict(kw, unatt_truth=True) for kw in synth.batch_specs(n_frames=n)]
 
 
 def serve_specs_c3(n):
     from paper_2411_02206_gb300 import synth
-    return synth.batch_specs(n_frames=n, seed=5000, lo=1e5, hi=5e7)
+    return [dict(kw, unatt_truth=True)
+            for kw in synth.batch_specs(n_frames=n, seed=5000, lo=1e5, hi=5e7)]
 
 
 def run_batch(args):

@@ -345,15 +345,8 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *   "unatt_variant"       0..1  record write-out of the unattached decoder:
  *                               word by word (0) or one staged 16-byte
  *                               {record, index} entry per thread (1)
- *   "overlap"             0..2  where the unattached decoder runs: after the
- *                               track decoder on the caller's stream (0), on a
- *                               third stream from the row offsets on (1), on
- *                               the scatter stream before the first scatter (2)
- *   "parts"               0..16 the attached clusters are decoded in this many
- *                               parts (ranges of ranking tiles); the record
- *                               scatter of a part runs on a second stream while
- *                               the next part is decoded (0: one part per 16
- *                               ranking tiles, at most 16)
+ *   "overlap"             0..1  unattached decoder on a second stream beside
+ *                               the tile bases and the record scatter (1)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
  *   "rans_overlap"   0..1  4-byte streams entropy-decoded on a second stream (1)

@@ -7,7 +7,7 @@
 //   k_put_record: frame descriptors and prefix tables, scratch cleared
 //   k_zero_status -> k_track_scan1 -> k_frame_scan -> k_track_scan2   track prep
 //   k_track_decode: coordinates and (sector,row) keys                  track decode
-//   k_count_rank                                                       per-row counts
+//   k_count_rank: per-tile counts and stable ranks                     per-row counts
 //   k_group_sum -> k_row_offsets -> k_tile_base                        row offsets
 //   k_att_scatter: native records of the attached clusters             placement
 //   k_unatt_decode                                                     unattached clusters
@@ -111,8 +111,8 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
   L.n_chunks = ceil_div(nu, kChunk);
   auto z = [&](size_t bytes) { size_t o = zoff; zoff = align_up(zoff + bytes, 256); return o; };
   auto p = [&](size_t bytes) { size_t o = poff; poff = align_up(poff + bytes, 256); return o; };
+  L.z_len = z((size_t)kLenBuckets * 4);
   L.z_lb = z((size_t)L.n_chunks * 8 + 8);
-  L.z_heads = z(((size_t)na + 31) / 32 * 4 + 4);
   L.track_start = p(((size_t)nt + 1) * 4);
   L.order = p((size_t)nt * 4 + 4);
   L.keys = p((size_t)na * 2 + 16);
@@ -201,9 +201,6 @@ tmd_handle::~tmd_handle() {
   if (coded) cudaFree(coded);
   if (trace_status) cudaFree(trace_status);
   if (aux) cudaStreamDestroy(aux);
-  if (aux2) cudaStreamDestroy(aux2);
-  if (ev_part) cudaEventDestroy(ev_part);
-  if (join2) cudaEventDestroy(join2);
   if (fork) cudaEventDestroy(fork);
   if (scratch_done) cudaEventDestroy(scratch_done);
   if (join) cudaEventDestroy(join);
@@ -241,15 +238,9 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking),
-                           "stream")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->ev_part, cudaEventDisableTiming),
-                           "event")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->join2, cudaEventDisableTiming),
-                           "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->scratch_done, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, prepare_key_rank(), "smem attribute")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, prepare_count_rank(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(0, &h->occ_decode_v[0]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_unatt_decode(&h->occ_unatt), "occupancy")) != TMD_OK ||
@@ -285,8 +276,8 @@ extern "C" const char* tmd_last_error_string(const tmd_handle* h) {
 // ---------------------------------------------------------------------------
 static const char* kKernelNames[kKNum] = {
     "k_put_record", "k_zero_status", "k_track_scan1", "k_frame_scan", "k_track_scan2",
-    "k_part_scan", "k_track_place", "k_track_decode", "k_key_rank", "k_group_sum",
-    "k_row_offsets", "k_tile_base", "k_att_scatter", "k_unatt_decode", "k_track_encode"};
+    "k_track_decode", "k_count_rank", "k_group_sum", "k_row_offsets", "k_tile_base",
+    "k_att_scatter", "k_unatt_decode", "k_track_encode"};
 
 cudaEvent_t TmdProfile::get() {
   if (pool.empty()) {
@@ -364,30 +355,11 @@ struct RecordLayout {
 static RecordLayout record_layout(uint32_t n, bool enc) {
   RecordLayout r;
   r.pre = 0;
-  r.frames = align_up(5 * ((size_t)n + 1) * 4, 64);
+  r.frames = align_up(6 * ((size_t)n + 1) * 4, 64);
   r.enc = align_up(r.frames + (size_t)n * sizeof(FrameDev), 64);
   r.bytes = align_up(r.enc + (enc ? (size_t)n * sizeof(EncDev) : 0), 64);
   r.counters_unused = 0;
   return r;
-}
-
-// Parts of a call: at most kMaxParts, and at most 1024 (part, frame) groups.
-uint32_t max_parts(uint32_t nf) {
-  const uint32_t g = nf ? 1024u / nf : 1u;
-  return std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)kMaxParts, g));
-}
-
-CallLayout call_layout(uint32_t nf) {
-  CallLayout c;
-  const size_t K = max_parts(nf);
-  c.counters = 0;
-  c.zero_bins = 256;
-  c.part_cnt = c.zero_bins + align_up((size_t)kNBin * 4, 256);
-  c.part_lo = c.part_cnt + align_up(K * nf * kOrderBuckets * 4, 256);
-  c.part_hi = c.part_lo + align_up(K * nf * 4, 256);
-  c.part_task_pre = c.part_hi + align_up(K * nf * 4, 256);
-  c.end = c.part_task_pre + align_up(K * ((size_t)nf + 1) * 4, 256);
-  return c;
 }
 
 // Scratch and record sizes of a call (nf decode frames, or one encode frame).
@@ -395,7 +367,7 @@ static void plan_all(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* ti
                      std::vector<FrameLayout>& L, size_t& zbytes, size_t& pbytes) {
   const bool encode = tin != nullptr;
   L.resize(nf);
-  size_t zoff = call_layout(nf).end;
+  size_t zoff = 256 + align_up((size_t)kNBin * 4, 256);  // counters + zero bins
   size_t poff = 0;
   for (uint32_t f = 0; f < nf; f++) {
     const uint32_t nt = encode ? tin[f].n_tracks : in[f].n_tracks;
@@ -429,7 +401,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   tmd_handle::Slot& S = h->slots[slot];
   bool order = false;
   if ((rc = h->order_after_previous(st, &order)) != TMD_OK) return rc;
-  const ChainStreams cs{h->aux, h->aux2, h->fork, h->ev_part, h->join, h->join2};
+  const ChainStreams cs{h->aux, h->fork, h->join};
   rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on,
                    tin ? nullptr : &cs, trace);
   if (rc != TMD_OK) return rc;
@@ -457,12 +429,11 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   uint32_t* pre_grp = pre + 2 * (nf + 1);
   uint32_t* pre_warp = pre + 3 * (nf + 1);
   uint32_t* pre_chunk = pre + 4 * (nf + 1);
+  uint32_t* pre_kt = pre + 5 * (nf + 1);
   FrameDev* fd = reinterpret_cast<FrameDev*>(host + R.frames);
   EncDev* ed = reinterpret_cast<EncDev*>(host + R.enc);
-  pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = 0;
-  const CallLayout C = call_layout(nf);
-  uint32_t* zero_bins = reinterpret_cast<uint32_t*>(zb + C.zero_bins);
-  uint64_t n_tracks_all = 0;
+  pre_tblk[0] = pre_tile[0] = pre_grp[0] = pre_warp[0] = pre_chunk[0] = pre_kt[0] = 0;
+  uint32_t* zero_bins = reinterpret_cast<uint32_t*>(zb + 256);
   for (uint32_t f = 0; f < nf; f++) {
     FrameDev& F = fd[f];
     memset(&F, 0, sizeof F);
@@ -499,8 +470,8 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     }
     F.n_tblocks = l.n_tblocks; F.n_tiles = l.n_tiles; F.n_groups = l.n_groups;
     F.n_chunks = l.n_chunks;
+    F.len_cursor = reinterpret_cast<uint32_t*>(zb + l.z_len);
     F.lookback = reinterpret_cast<unsigned long long*>(zb + l.z_lb);
-    F.heads = encode ? nullptr : reinterpret_cast<uint32_t*>(zb + l.z_heads);
     F.track_start = reinterpret_cast<uint32_t*>(pb + l.track_start);
     F.order = reinterpret_cast<uint32_t*>(pb + l.order);
     F.keys = reinterpret_cast<uint16_t*>(pb + l.keys);
@@ -517,7 +488,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     pre_grp[f + 1] = pre_grp[f] + l.n_groups * kBinBlocks;
     pre_warp[f + 1] = pre_warp[f] + ceil_div(F.n_tracks, 32);  // encoder warp tasks
     pre_chunk[f + 1] = pre_chunk[f] + l.n_chunks;
-    n_tracks_all += F.n_tracks;
+    pre_kt[f + 1] = pre_kt[f] + ceil_div(F.n_tracks, 32);
   }
   PlanDev P;
   const uint32_t* dpre = reinterpret_cast<const uint32_t*>(dev + R.pre);
@@ -527,24 +498,8 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   P.pre_grp = dpre + 2 * (nf + 1);
   P.pre_warp = dpre + 3 * (nf + 1);
   P.pre_chunk = dpre + 4 * (nf + 1);
-  P.counters = reinterpret_cast<uint32_t*>(zb + C.counters);
-  // parts of the attached clusters: their record scatter runs on the second
-  // stream while the next part is decoded (decoding calls with a second
-  // stream; one part otherwise)
-  const uint32_t n_tile = pre_tile[nf];
-  const bool decode_call = !encode && !trace;
-  const bool streams = decode_call && cs && cs->aux && cs->fork && cs->part && cs->join;
-  uint32_t K = 1;
-  if (streams && n_tile) {
-    K = h->tune_parts > 0 ? (uint32_t)h->tune_parts : n_tile / kMinPartTiles;
-    K = std::max<uint32_t>(1u, std::min<uint32_t>(K, std::min<uint32_t>(n_tile, max_parts(nf))));
-  }
-  P.n_parts = K;
-  P.n_tiles = std::max<uint32_t>(n_tile, 1u);
-  P.part_cnt = reinterpret_cast<uint32_t*>(zb + C.part_cnt);
-  P.part_lo = reinterpret_cast<uint32_t*>(zb + C.part_lo);
-  P.part_hi = reinterpret_cast<uint32_t*>(zb + C.part_hi);
-  P.part_task_pre = reinterpret_cast<uint32_t*>(zb + C.part_task_pre);
+  P.pre_kt = dpre + 5 * (nf + 1);
+  P.counters = reinterpret_cast<uint32_t*>(zb);
   const FrameDev* dframes = reinterpret_cast<const FrameDev*>(dev + R.frames);
   const EncDev* denc = reinterpret_cast<const EncDev*>(dev + R.enc);
 
@@ -571,15 +526,11 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
   });
   CK(put_err);
   if (!zs) timed(kKZeroStatus, [&] { k_zero_status<<<1, 256, 0, st>>>(dframes, nf); });
-  const uint32_t n_tblk = pre_tblk[nf], n_grp = pre_grp[nf];
+  const uint32_t n_tblk = pre_tblk[nf], n_tile = pre_tile[nf], n_grp = pre_grp[nf];
   const uint32_t n_warp = pre_warp[nf], n_chunk = pre_chunk[nf];
   if (n_tblk) timed(kKTrackScan1, [&] { k_track_scan1<<<n_tblk, 256, 0, st>>>(dframes, P); });
   timed(kKFrameScan, [&] { k_frame_scan<<<nf, 1024, 0, st>>>(dframes, P); });
-  if (n_tblk) {
-    timed(kKTrackScan2, [&] { k_track_scan2<<<n_tblk, 256, 0, st>>>(dframes, P); });
-    timed(kKPartScan, [&] { k_part_scan<<<K * nf, kOrderBuckets, 0, st>>>(dframes, P); });
-    timed(kKTrackPlace, [&] { k_track_place<<<n_tblk + 1, 256, 0, st>>>(dframes, P); });
-  }
+  if (n_tblk) timed(kKTrackScan2, [&] { k_track_scan2<<<n_tblk, 256, 0, st>>>(dframes, P); });
   if (trace) {
     if (trace->n)
       k_track_trace<<<(trace->n + 127) / 128, 128, 0, st>>>(dframes, trace->ids, trace->n,
@@ -590,16 +541,24 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
       timed(kKTrackEncode, [&] { k_track_encode<<<grid, 256, 0, st>>>(denc, dframes, P, n_warp); });
     }
   } else {
-    // keys and ranks, row offsets, tile bases; then per part the track decode
-    // (main stream) and the record scatter (second stream, after the part's
-    // decode); the unattached decode (it needs only rowStart and the attached
-    // counts) on the main stream after the decode (overlap 0), on a third
-    // stream from the row offsets on (1), or on the second stream before the
-    // first scatter (2)
-    if (n_tile) timed(kKKeyRank, [&] { launch_key_rank(n_tile, st, dframes, P); });
+    // track decode (keys, pad and time codes), per-tile counts and ranks, row
+    // offsets; then the tile bases and the record scatter, with the
+    // unattached decode (it needs only rowStart and the attached counts)
+    // beside them on the second stream (overlap 1) or after them
+    const uint32_t n_kt = pre_kt[nf];
+    const bool two = cs && cs->aux && cs->fork && cs->join && h->tune_overlap && n_chunk;
+    if (n_kt) {
+      const int var = h->tune_decode_variant;
+      int bps = h->occ_decode_v[var];
+      if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
+      const uint32_t per_block = kDecodeThreads / 32;
+      const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(
+          (uint32_t)(h->sms * bps), (n_kt + per_block - 1) / per_block));
+      timed(kKTrackDecode, [&] { launch_track_decode(var, grid, st, dframes, P, n_kt); });
+    }
+    if (n_tile) timed(kKCountRank, [&] { launch_count_rank(n_tile, st, dframes, P); });
     if (n_grp) timed(kKGroupSum, [&] { k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
-    if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
     auto unatt = [&](cudaStream_t s_) {
       if (!n_chunk) return;
       int bps = h->occ_unatt;
@@ -609,42 +568,19 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
         launch_unatt_decode(h->tune_unatt_variant, grid, s_, dframes, P, n_chunk);
       });
     };
-    const bool third = streams && h->tune_overlap == 1 && cs->aux2 && cs->join2 && n_chunk;
-    const int ov = third ? 1 : (streams && h->tune_overlap == 2 ? 2 : 0);
-    if (streams) {
+    if (two) {
       CK(cudaEventRecord(cs->fork, st));
       CK(cudaStreamWaitEvent(cs->aux, cs->fork, 0));
-      if (third) {
-        CK(cudaStreamWaitEvent(cs->aux2, cs->fork, 0));
-        unatt(cs->aux2);
-        CK(cudaEventRecord(cs->join2, cs->aux2));
-      } else if (ov == 2) {
-        unatt(cs->aux);
-      }
+      unatt(cs->aux);
     }
-    const int var = h->tune_decode_variant;
-    int bps = h->occ_decode_v[var];
-    if (h->tune_decode_bps > 0 && h->tune_decode_bps < bps) bps = h->tune_decode_bps;
-    const uint32_t dgrid = (uint32_t)std::max<uint64_t>(1u, std::min<uint64_t>(
-        (uint64_t)h->sms * bps, (n_tracks_all + kDecodeThreads - 1) / kDecodeThreads));
-    cudaStream_t sst = streams ? cs->aux : st;
-    for (uint32_t k = 0; k < K && n_tile; k++) {
-      if (n_tracks_all)
-        timed(kKTrackDecode, [&] { launch_track_decode(var, dgrid, st, dframes, P, k); });
-      if (streams) {
-        CK(cudaEventRecord(cs->part, st));
-        CK(cudaStreamWaitEvent(cs->aux, cs->part, 0));
-      }
-      const uint32_t g0 = part_first_tile(k, K, n_tile), g1 = part_first_tile(k + 1, K, n_tile);
-      timed_on(sst, kKAttScatter, [&] {
-        launch_att_scatter(h->tune_scatter_variant, g0, g1 - g0, sst, dframes, P);
-      });
-    }
-    if (!streams || ov == 0) unatt(st);
-    if (streams) {
+    if (n_grp) timed(kKTileBase, [&] { k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframes, P); });
+    if (n_tile)
+      timed(kKAttScatter, [&] { launch_att_scatter(h->tune_scatter_variant, n_tile, st, dframes, P); });
+    if (two) {
       CK(cudaEventRecord(cs->join, cs->aux));
       CK(cudaStreamWaitEvent(st, cs->join, 0));
-      if (third) CK(cudaStreamWaitEvent(st, cs->join2, 0));
+    } else {
+      unatt(st);
     }
   }
   CK(cudaGetLastError());

@@ -16,18 +16,17 @@ struct TmdServer;  // serving state (tmd_serve.cu)
 
 // Kernel ids of the instrumentation.
 enum TmdKernel {
-  kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKPartScan, kKTrackPlace,
-  kKTrackDecode, kKKeyRank, kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode,
-  kKTrackEncode, kKNum
+  kKPutRecord, kKZeroStatus, kKTrackScan1, kKFrameScan, kKTrackScan2, kKTrackDecode,
+  kKCountRank, kKGroupSum, kKRowOffsets, kKTileBase, kKAttScatter, kKUnattDecode, kKTrackEncode,
+  kKNum
 };
 
-// Streams and events of a decode chain: the record scatter of the parts runs
-// on aux (each part after its decode, signalled through `part`), the
-// unattached decode on aux2 or aux (tuning key overlap); fork starts them,
-// join / join2 end them.
+// The second stream of a decode chain: the unattached decode runs on aux
+// beside the tile bases and the record scatter (tuning key overlap); fork
+// starts it, join ends it.
 struct ChainStreams {
-  cudaStream_t aux, aux2;
-  cudaEvent_t fork, part, join, join2;
+  cudaStream_t aux;
+  cudaEvent_t fork, join;
 };
 
 struct TmdProfile {
@@ -58,10 +57,7 @@ struct tmd_handle {
   int tune_decode_variant = 0;   // staging-round variant of the track decoder
   int tune_scatter_variant = 1;  // store pattern of the record scatter
   int tune_unatt_variant = 1;    // record write-out of the unattached decode
-  int tune_overlap = 1;          // unattached decode: 0 after the track decode on the main
-                                 // stream, 1 on a third stream from the row offsets on, 2 on
-                                 // the scatter stream before the first scatter
-  int tune_parts = 0;            // parts of the attached clusters (0: automatic)
+  int tune_overlap = 1;          // unattached decode on the second stream beside the scatter
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 1;        // unattached-decode blocks per SM (0: as many as fit)
   int tune_rans_overlap = 1;     // 4-byte streams entropy-decoded on the second stream
@@ -81,8 +77,7 @@ struct tmd_handle {
   TmdProfile prof;
   uint32_t* trace_status = nullptr;        // status word of tmd_track_trace calls
   cudaStream_t aux = nullptr;              // second stream of the plain decode chain
-  cudaStream_t aux2 = nullptr;             // third stream (the unattached decode)
-  cudaEvent_t fork = nullptr, join = nullptr, ev_part = nullptr, join2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   // host streaming pipeline (tmd_decode_host_stream): copy streams, device
   // slots and their events
   static constexpr int kPipeSlots = 3;
@@ -122,18 +117,10 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
 // Scratch layout of one frame.  The zeroed part of all frames is contiguous.
 struct FrameLayout {
   uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
-  size_t z_lb, z_heads;                           // offsets in the zeroed part
+  size_t z_len, z_lb;                             // offsets in the zeroed part
   size_t track_start, order, keys, kf_pad, kf_time, rank, tile_hist, group_sum, tile_base,
       unatt_start, blk_sum, att_count;            // offsets in the plain part
 };
-// Call-level scratch at the start of the zeroed part: the counters, 5472
-// zero bin counts (the unattached counts of an encoding call), and the part
-// tables of up to max_parts(nf) parts; the frames' scratch follows.
-struct CallLayout {
-  size_t counters, zero_bins, part_cnt, part_lo, part_hi, part_task_pre, end;
-};
-uint32_t max_parts(uint32_t nf);
-CallLayout call_layout(uint32_t nf);
 // Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts.
 void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,
                 FrameLayout& L);
@@ -144,11 +131,10 @@ void tmd_call_sizes(uint32_t nf, const tmd_frame_in* in, const tmd_truth_in* tin
 // Fill the launch record (host_record, pinned) for the given scratch and enqueue
 // the record upload and the kernel chain on st (with per-kernel events into
 // the handle's profile if `profile`; only the handle's own thread may ask).
-// With streams (a decoding call), the attached clusters are decoded in parts
-// whose record scatter runs on cs->aux beside the next part's track decode,
-// and the unattached decode runs where the overlap setting puts it; st waits
-// for all of it at the end.  The caller keeps scratch and both record buffers
-// alive until the stream has passed the chain.
+// With streams (a decoding call), the unattached decode runs on cs->aux
+// beside the tile bases and the record scatter, and st waits for it at the
+// end.  The caller keeps scratch and both record buffers alive until the
+// stream has passed the chain.
 int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_frame_out* out,
                 const tmd_truth_in* tin, const tmd_track_out* tout, void* scratch,
                 void* host_record, void* dev_record, cudaStream_t st, bool profile,

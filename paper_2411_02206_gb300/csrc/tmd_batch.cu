@@ -4,7 +4,7 @@
 // every kernel of the chain spans the work items of all frames (the persistent
 // decoders pull (frame, warp-task) and (frame, chunk) items from global
 // counters), and the chain -- record upload, scratch clear, the kernels on
-// their three streams with the event edges between them -- is captured once
+// their two streams with the event edges between them -- is captured once
 // and replayed with one cudaGraphLaunch.  Small frames therefore
 // share waves with large ones instead of each paying a launch sequence and a
 // tail of its own.
@@ -19,8 +19,8 @@ struct tmd_batch {
   void* host_record = nullptr;
   void* dev_record = nullptr;
   cudaStream_t cap = nullptr;
-  cudaStream_t aux = nullptr, aux2 = nullptr;  // second and third branches of the chain
-  cudaEvent_t fork = nullptr, part = nullptr, join = nullptr, join2 = nullptr;
+  cudaStream_t aux = nullptr;  // second branch of the captured chain
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~tmd_batch() {
@@ -28,8 +28,7 @@ struct tmd_batch {
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
     if (aux) cudaStreamDestroy(aux);
-    if (aux2) cudaStreamDestroy(aux2);
-    for (cudaEvent_t e : {fork, part, join, join2})
+    for (cudaEvent_t e : {fork, join})
       if (e) cudaEventDestroy(e);
     if (scratch) cudaFree(scratch);
     if (dev_record) cudaFree(dev_record);
@@ -66,16 +65,13 @@ extern "C" int tmd_batch_create(tmd_handle* h, uint32_t n, const tmd_frame_in* i
   if (rc == TMD_OK)
     rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
   if (rc == TMD_OK)
-    rc = tmd_cuda_check(h, cudaStreamCreateWithFlags(&b->aux2, cudaStreamNonBlocking), "stream");
-  for (cudaEvent_t* e : {&b->join, &b->part, &b->join2})
-    if (rc == TMD_OK)
-      rc = tmd_cuda_check(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
+    rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming), "event");
   if (rc != TMD_OK) { delete b; return rc; }
   rc = tmd_cuda_check(h, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal),
                       "begin capture");
   if (rc == TMD_OK) {
     // no timing events inside the graph; the fork/join events become edges
-    const ChainStreams cs{b->aux, b->aux2, b->fork, b->part, b->join, b->join2};
+    const ChainStreams cs{b->aux, b->fork, b->join};
     rc = tmd_enqueue(h, n, in, out, nullptr, nullptr, b->scratch, b->host_record, b->dev_record,
                      b->cap, false, &cs);
     const int rc2 = tmd_cuda_check(h, cudaStreamEndCapture(b->cap, &b->graph), "end capture");

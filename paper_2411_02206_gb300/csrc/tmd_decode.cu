@@ -5,9 +5,6 @@
 //
 // Decoding of the attached clusters runs in three kernels:
 //
-//   k_key_rank      (tmd_rank.cu) the (sector,row) key of every cluster, a
-//                   segmented scan of the row and sector differences, and
-//                   its stable rank within its (ranking tile, bin).
 //   k_track_decode  one lane per track, warps take 32 tracks at a time from
 //                   the length-sorted order (longest first, so lanes of a warp
 //                   run loops of similar length and the tail is short).  For
@@ -15,7 +12,10 @@
 //                   differences, propagates the model to the row, adds the
 //                   modular residuals to the quantised prediction and updates
 //                   the model with the decoded cluster.  It writes, in input
-//                   order j, the cluster's pad code and time code.
+//                   order j, the cluster's (sector,row) key, pad code and time
+//                   code.
+//   k_count_rank    (tmd_rank.cu) per-tile counts of the keys and the stable
+//                   rank of every cluster within its (ranking tile, bin).
 //   k_att_scatter   (tmd_scatter.cu) assembles the 12-byte native record of
 //                   every attached cluster from the decoded coordinates and
 //                   the charge streams and writes it at
@@ -141,11 +141,11 @@ __device__ __forceinline__ RoundBase issue_round(uint32_t* lb, uint32_t k0, uint
 
 }  // namespace
 
-// Writes the pad code and the time code of every attached cluster of the
-// tracks of one part (tasks of 32 tracks taken from counters[4 + part]).
+// Writes the (sector,row) key, the pad code and the time code of every
+// attached cluster.
 template <int R, int MINB>
 __global__ void __launch_bounds__(kDecodeThreads, MINB)
-    k_track_decode(const FrameDev* frames, PlanDev plan, uint32_t part) {
+    k_track_decode(const FrameDev* frames, PlanDev plan, uint32_t n_tasks) {
   static_assert(R == 8 || R == 16, "round length");
   using Lay = AsyncLayout<R>;
   constexpr int P = R + 1;   // pitch of the output rows
@@ -158,26 +158,23 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t sq = lane % R, sg = lane / R;
   AsyncStage<R>& S = stage[threadIdx.x >> 5];
-  const uint32_t nf = plan.n_frames;
-  const uint32_t* task_pre = plan.part_task_pre + (size_t)part * (nf + 1);
-  const uint32_t n_tasks = task_pre[nf];
   for (;;) {
-    const uint32_t task = next_task(&plan.counters[4 + part]);
+    const uint32_t task = next_task(&plan.counters[0]);
     if (task >= n_tasks) break;
-    const uint32_t f = find_frame(task_pre, nf, task);
+    const uint32_t f = find_frame(plan.pre_kt, plan.n_frames, task);
     const FrameDev& F = frames[f];
     if (*F.status & kStCount) continue;
-    const uint32_t idx = plan.part_lo[(size_t)part * nf + f] + (task - task_pre[f]) * 32u + lane;
-    const uint32_t idx_end = plan.part_hi[(size_t)part * nf + f];
+    const uint32_t idx = (task - plan.pre_kt[f]) * 32u + lane;
     const uint8_t* __restrict__ rd_s = F.row_diff;
     const uint8_t* __restrict__ sld_s = F.sld;
     const uint16_t* __restrict__ pr_s = F.pad_res;
     const uint32_t* __restrict__ tr_s = F.time_res;
+    uint16_t* __restrict__ key_o = F.keys;
     uint16_t* __restrict__ pad_o = F.kf_pad;
     uint32_t* __restrict__ time_o = F.kf_time;
     uint32_t j0 = 0, n = 0, dm1 = 0, pad0 = 0, time0 = 0, st = 0;
     Track s;
-    if (idx < idx_end) {
+    if (idx < F.n_tracks) {
       const uint32_t t = F.order[idx];
       j0 = F.track_start[t];
       n = F.ncl[t];
@@ -185,6 +182,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
       pad0 = F.pad[t];
       time0 = F.time[t];
       const uint32_t raw = F.row[t], sec = F.slice[t];
+      if (raw >= (uint32_t)kNRow || sec >= (uint32_t)kNSec) st |= kStRow;
       seed(geo, s, F.qpt[t], (int)raw, sec < (uint32_t)kNSec ? (int)sec : kNSec - 1, pad0,
            time0);
     }
@@ -218,7 +216,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
             const uint32_t rdv = (lb[prd >> 2] >> (8 * (prd & 3))) & 255u;
             const uint32_t slv = (lb[Lay::kRd + (psl >> 2)] >> (8 * (psl & 3))) & 255u;
             const uint32_t prv = (lb[2 * Lay::kRd + (ppr >> 1)] >> (16 * (ppr & 1))) & 0xFFFFu;
-            key_step(s, rdv, slv);  // a row outside the detector is flagged by k_key_rank
+            st |= key_step(s, rdv, slv);
             uint32_t ppad, ptime;
             const float4 G = geo->row[s.row];
             propagate_predict(G, s, ppad, ptime);
@@ -227,7 +225,7 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
             update(G, s, padq, timeq);
           }
           if (timeq > 0xFFFFFFu) st |= kStTime;
-          S.kp[lane * P + q] = padq;
+          S.kp[lane * P + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
           lb[Lay::kTr0 + q] = timeq;
         }
       }
@@ -239,7 +237,9 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
         const uint32_t i = i0 + sg;
         const uint32_t ni = __shfl_sync(kFull, n, i), ji = __shfl_sync(kFull, j0, i);
         if (k < ni) {
-          pad_o[ji + k] = (uint16_t)S.kp[i * P + sq];
+          const uint32_t a = S.kp[i * P + sq];
+          key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
+          pad_o[ji + k] = (uint16_t)(a >> 16);
           time_o[ji + k] = bb[i * Lay::kLane + Lay::kTr0 + sq];
         }
       }
@@ -255,11 +255,11 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
 // Variants: 0 -> rounds of 16 steps (4 blocks per SM), 1 -> rounds of 8
 // steps (6 blocks per SM).
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t part) {
+                         PlanDev plan, uint32_t n_tasks) {
   if (variant == 1)
-    k_track_decode<8, 6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, part);
+    k_track_decode<8, 6><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks);
   else
-    k_track_decode<16, 4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, part);
+    k_track_decode<16, 4><<<grid, kDecodeThreads, 0, st>>>(frames, plan, n_tasks);
 }
 
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm) {

@@ -17,10 +17,7 @@ constexpr int kGroup = 32;               // tiles per group of the tile scan
 constexpr int kBinBlk = 256;             // bins per block of the tile scan
 constexpr int kBinBlocks = (kNBin + kBinBlk - 1) / kBinBlk;
 constexpr int kChunk = 2048;             // unattached clusters per scan chunk
-constexpr int kOrderBuckets = 256;       // track-length buckets of the decode order
-constexpr int kMaxParts = 16;            // parts of the attached clusters (tile ranges) whose
-                                         // scatter overlaps the next part's track decode
-constexpr int kMinPartTiles = 16;        // ranking tiles per part at least (automatic count)
+constexpr int kLenBuckets = 1024;        // track-length buckets of the decode order
 constexpr int kDecodeThreads = 128;      // threads per block of the track decoder
 constexpr int kScatThreads = 256;        // threads per block of the record scatter
 
@@ -73,9 +70,8 @@ struct FrameDev {
   uint32_t* tile_base;     // n_tiles x kNBin: first native index of (tile, bin)
   uint32_t* unatt_start;   // kNBin + 1
   uint32_t* blk_sum;       // n_tblocks
+  uint32_t* len_cursor;    // kLenBuckets (zeroed)
   unsigned long long* lookback;  // n_chunks (zeroed)
-  uint32_t* heads;         // (n_att + 31) / 32 words, bit j set when cluster j is the
-                           // first of its track (zeroed; set by the track scan)
 };
 
 // Encoder view of a frame: attached truth in, compressed attached streams out.
@@ -102,13 +98,6 @@ struct EncDev {
 
 // Launch plan of a batch: for each kernel family the exclusive prefix over
 // frames of its work items, so that a block can find its frame.
-//
-// Parts: the ranking tiles of all frames (concatenated in frame order, T in
-// all) are cut into n_parts ranges, part k = global tiles
-// [floor(k T / K), floor((k + 1) T / K)); a track belongs to the part of the
-// tile of its first cluster.  The tracks of (part k, frame f) are a contiguous
-// range of the frame's track indices [part_lo, part_hi) and are decoded in the
-// order order[part_lo .. part_hi), longest first.
 struct PlanDev {
   uint32_t n_frames;
   const uint32_t* pre_tblk;   // track-scan blocks
@@ -116,29 +105,9 @@ struct PlanDev {
   const uint32_t* pre_grp;    // tile-group blocks (n_groups * kBinBlocks)
   const uint32_t* pre_warp;   // encoder: warp tasks of 32 tracks
   const uint32_t* pre_chunk;  // unattached chunks
-  uint32_t* counters;         // [0] encode task, [1] unattached ticket, [4 + k] decode
-                              // task of part k (zeroed)
-  uint32_t n_parts, n_tiles;  // K, T
-  uint32_t* part_cnt;         // [K][nf][kOrderBuckets] track counts (zeroed), then the
-                              // decode-order cursors of the buckets
-  uint32_t* part_lo;          // [K][nf] first track of (part, frame)
-  uint32_t* part_hi;          // [K][nf] one past its last track
-  uint32_t* part_task_pre;    // [K][nf + 1] exclusive prefix of the warp tasks over frames
+  const uint32_t* pre_kt;     // decoder: warp tasks of 32 tracks
+  uint32_t* counters;         // [0] decode/encode task, [1] unattached ticket (zeroed)
 };
-
-// Part of global ranking tile g (see PlanDev).
-__host__ __device__ __forceinline__ uint32_t part_of_tile(uint32_t g, uint32_t n_parts,
-                                                          uint32_t n_tiles) {
-  return (uint32_t)((((unsigned long long)g + 1) * n_parts - 1) / n_tiles);
-}
-__host__ __device__ __forceinline__ uint32_t part_first_tile(uint32_t k, uint32_t n_parts,
-                                                             uint32_t n_tiles) {
-  return (uint32_t)(((unsigned long long)k * n_tiles) / n_parts);
-}
-// Decode-order bucket of a track length: longest first.
-__host__ __device__ __forceinline__ uint32_t order_bucket(uint32_t n) {
-  return kOrderBuckets - 1 - (n < kOrderBuckets - 1 ? n : kOrderBuckets - 1);
-}
 
 // Largest f with pre[f] <= item (pre has n+1 entries, pre[0] = 0).
 __device__ __forceinline__ uint32_t find_frame(const uint32_t* pre, uint32_t n, uint32_t item) {
@@ -179,30 +148,25 @@ __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames);
 __global__ void k_track_scan1(const FrameDev* frames, PlanDev plan);
 __global__ void k_frame_scan(const FrameDev* frames, PlanDev plan);
 __global__ void k_track_scan2(const FrameDev* frames, PlanDev plan);
-// Decode-order ranges and bucket cursors of every (part, frame) (grid:
-// n_parts * n_frames blocks of kOrderBuckets threads), then the order itself
-// and the warp-task prefixes (grid: track-scan blocks, plus one block).
-__global__ void k_part_scan(const FrameDev* frames, PlanDev plan);
-__global__ void k_track_place(const FrameDev* frames, PlanDev plan);
-// Keys, tile histograms and stable ranks of the attached clusters (grid:
-// ranking tiles of all frames).
-void launch_key_rank(uint32_t grid, cudaStream_t st, const FrameDev* frames, PlanDev plan);
-cudaError_t prepare_key_rank();
+// Tile histograms and stable ranks of the attached clusters from their keys
+// (grid: ranking tiles of all frames).
+void launch_count_rank(uint32_t grid, cudaStream_t st, const FrameDev* frames, PlanDev plan);
+cudaError_t prepare_count_rank();
 __global__ void k_group_sum(const FrameDev* frames, PlanDev plan);
 __global__ void k_row_offsets(const FrameDev* frames, PlanDev plan);
 __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
 // The track decoder is instantiated in variants of its staging (a tuning
 // parameter, every instance computes identical results); host code launches
-// it through these two functions, once per part.  Its warps take tasks of 32
-// tracks of part k from counters[4 + k] and write the pad and time codes of
-// every attached cluster (the keys come from k_key_rank).
+// it through these two functions.  Its warps take tasks of 32 tracks (pre_kt
+// of the plan) from counters[0] and write the key, pad code and time code of
+// every attached cluster.
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
-                         PlanDev plan, uint32_t part);
+                         PlanDev plan, uint32_t n_tasks);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
 // Record scatter variants 0, 1 (identical results; see tmd_scatter.cu),
-// launched over the global ranking tiles [tile_lo, tile_lo + n_tiles).
-void launch_att_scatter(int variant, uint32_t tile_lo, uint32_t n_tiles, cudaStream_t st,
-                        const FrameDev* frames, PlanDev plan);
+// launched over n_tiles ranking tiles of all frames.
+void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
+                        PlanDev plan);
 // Unattached decode variants 0, 1 (record write-out word by word or one
 // record per thread; identical results), launched through these functions.
 void launch_unatt_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,

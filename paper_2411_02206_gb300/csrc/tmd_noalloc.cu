@@ -7,10 +7,10 @@
 // the same kernels as tmd_decode_frame but takes its working memory from one
 // fixed array in the library's device image, g_noalloc_scratch, instead of a
 // handle's scratch allocation.  The caller still provides the frame's inputs
-// and outputs.  The chain is the default one of tmd_decode_frame (key and rank
-// pass, track decoder variant 0, three-lane record scatter, unattached decode
-// with one staged record per thread), all on the caller's stream (no second
-// stream).
+// and outputs.  The chain is the default one of tmd_decode_frame (track
+// decoder variant 0, counts and ranks, three-lane record scatter, unattached
+// decode with one staged record per thread), all on the caller's stream (no
+// second stream).
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it until the process exits.  In host code its name is only a
@@ -54,12 +54,12 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kArrayBytes];
 // Writes the frame descriptor and the prefix tables of a one-frame plan into
 // the record area.
 __global__ void k_noalloc_record(FrameDev f, uint32_t n_tblk, uint32_t n_tile, uint32_t n_grp,
-                                 uint32_t n_warp, uint32_t n_chunk, FrameDev* dst_frame,
-                                 uint32_t* dst_pre) {
+                                 uint32_t n_warp, uint32_t n_chunk, uint32_t n_kt,
+                                 FrameDev* dst_frame, uint32_t* dst_pre) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *dst_frame = f;
-    const uint32_t v[5] = {n_tblk, n_tile, n_grp, n_warp, n_chunk};
-    for (int i = 0; i < 5; i++) {
+    const uint32_t v[6] = {n_tblk, n_tile, n_grp, n_warp, n_chunk, n_kt};
+    for (int i = 0; i < 6; i++) {
       dst_pre[2 * i] = 0;
       dst_pre[2 * i + 1] = v[i];
     }
@@ -74,8 +74,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     return TMD_ERR_ARG;
   }
   FrameLayout L;
-  const CallLayout C = call_layout(1);
-  size_t zoff = C.end;
+  size_t zoff = 256 + ((size_t)kNBin * 4 + 255) / 256 * 256;  // counters + zero bins
   size_t poff = 0;
   plan_frame(in->n_tracks, in->n_attached, in->n_unattached, zoff, poff, L);
   const size_t zbytes = (zoff + 255) / 256 * 256;
@@ -106,7 +105,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     if (!S->ready) {
       int sms = 0, od = 0, ou = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          prepare_key_rank() != cudaSuccess ||
+          prepare_count_rank() != cudaSuccess ||
           occupancy_track_decode(0, &od) != cudaSuccess ||
           occupancy_unatt_decode(&ou) != cudaSuccess) {
         set_err(err, err_len, "device set-up failed");
@@ -137,8 +136,8 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.att_count = out->att_count ? out->att_count : reinterpret_cast<uint32_t*>(pb + L.att_count);
   F.n_tblocks = L.n_tblocks; F.n_tiles = L.n_tiles; F.n_groups = L.n_groups;
   F.n_chunks = L.n_chunks;
+  F.len_cursor = reinterpret_cast<uint32_t*>(zb + L.z_len);
   F.lookback = reinterpret_cast<unsigned long long*>(zb + L.z_lb);
-  F.heads = reinterpret_cast<uint32_t*>(zb + L.z_heads);
   F.track_start = reinterpret_cast<uint32_t*>(pb + L.track_start);
   F.order = reinterpret_cast<uint32_t*>(pb + L.order);
   F.keys = reinterpret_cast<uint16_t*>(pb + L.keys);
@@ -151,7 +150,8 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.unatt_start = reinterpret_cast<uint32_t*>(pb + L.unatt_start);
   F.blk_sum = reinterpret_cast<uint32_t*>(pb + L.blk_sum);
   const uint32_t n_tblk = L.n_tblocks, n_tile = L.n_tiles, n_grp = L.n_groups * kBinBlocks;
-  const uint32_t n_warp = (in->n_tracks + 31) / 32;
+  const uint32_t n_kt = (in->n_tracks + 31) / 32;  // decoder warp tasks
+  const uint32_t n_warp = n_kt;
   const uint32_t n_chunk = L.n_chunks;
   FrameDev* dframe = reinterpret_cast<FrameDev*>(rec);
   uint32_t* dpre = reinterpret_cast<uint32_t*>(rec + 1024);
@@ -162,14 +162,10 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   P.pre_grp = dpre + 4;
   P.pre_warp = dpre + 6;
   P.pre_chunk = dpre + 8;
-  P.counters = reinterpret_cast<uint32_t*>(zb + C.counters);
-  P.n_parts = 1;  // one stream: the parts would not overlap
-  P.n_tiles = n_tile > 0 ? n_tile : 1u;
-  P.part_cnt = reinterpret_cast<uint32_t*>(zb + C.part_cnt);
-  P.part_lo = reinterpret_cast<uint32_t*>(zb + C.part_lo);
-  P.part_hi = reinterpret_cast<uint32_t*>(zb + C.part_hi);
-  P.part_task_pre = reinterpret_cast<uint32_t*>(zb + C.part_task_pre);
-  k_noalloc_record<<<1, 32, 0, st>>>(F, n_tblk, n_tile, n_grp, n_warp, n_chunk, dframe, dpre);
+  P.pre_kt = dpre + 10;
+  P.counters = reinterpret_cast<uint32_t*>(zb);
+  k_noalloc_record<<<1, 32, 0, st>>>(F, n_tblk, n_tile, n_grp, n_warp, n_chunk, n_kt, dframe,
+                                     dpre);
   if (put_record(nullptr, 0, nullptr, zb, zbytes, st) != cudaSuccess) {
     set_err(err, err_len, "scratch clear failed");
     return TMD_ERR_CUDA;
@@ -177,21 +173,17 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   k_zero_status<<<1, 256, 0, st>>>(dframe, 1);
   if (n_tblk) k_track_scan1<<<n_tblk, 256, 0, st>>>(dframe, P);
   k_frame_scan<<<1, 1024, 0, st>>>(dframe, P);
-  if (n_tblk) {
-    k_track_scan2<<<n_tblk, 256, 0, st>>>(dframe, P);
-    k_part_scan<<<1, kOrderBuckets, 0, st>>>(dframe, P);
-    k_track_place<<<n_tblk + 1, 256, 0, st>>>(dframe, P);
+  if (n_tblk) k_track_scan2<<<n_tblk, 256, 0, st>>>(dframe, P);
+  if (n_kt) {
+    const uint32_t cap = (uint32_t)(S->sms * S->occ_decode);
+    const uint32_t want = (n_kt + kDecodeThreads / 32 - 1) / (kDecodeThreads / 32);
+    launch_track_decode(0, want < cap ? want : cap, st, dframe, P, n_kt);
   }
-  if (n_tile) launch_key_rank(n_tile, st, dframe, P);
+  if (n_tile) launch_count_rank(n_tile, st, dframe, P);
   if (n_grp) k_group_sum<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
   k_row_offsets<<<1, 1024, 0, st>>>(dframe, P);
   if (n_grp) k_tile_base<<<n_grp, kBinBlk, 0, st>>>(dframe, P);
-  if (n_warp) {
-    const uint32_t cap = (uint32_t)(S->sms * S->occ_decode);
-    const uint32_t want = (n_warp + kDecodeThreads / 32 - 1) / (kDecodeThreads / 32);
-    launch_track_decode(0, want < cap ? want : cap, st, dframe, P, 0);
-  }
-  if (n_tile) launch_att_scatter(1, 0, n_tile, st, dframe, P);
+  if (n_tile) launch_att_scatter(1, n_tile, st, dframe, P);
   if (n_chunk) {
     const uint32_t cap = (uint32_t)(S->sms * S->occ_unatt);
     launch_unatt_decode(1, n_chunk < cap ? n_chunk : cap, st, dframe, P, n_chunk);

@@ -122,12 +122,15 @@ __global__ void k_zero_status(const FrameDev* frames, uint32_t n_frames) {
     *frames[f].status = 0u;
 }
 
-// Block totals of the track lengths, zero-length check.
+// Block totals of the track lengths, zero-length check, length histogram.
 __global__ void __launch_bounds__(256) k_track_scan1(const FrameDev* frames, PlanDev plan) {
+  __shared__ uint32_t hist[kLenBuckets];
   uint32_t tot;
   const uint32_t f = find_frame(plan.pre_tblk, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
   const uint32_t lb = blockIdx.x - plan.pre_tblk[f];
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
   const uint32_t t0 = lb * kTrackBlk + threadIdx.x * 8;
   uint32_t sum = 0;
   bool zero = false;
@@ -138,14 +141,18 @@ __global__ void __launch_bounds__(256) k_track_scan1(const FrameDev* frames, Pla
       const uint32_t n = F.ncl[t];
       sum += n;
       zero |= (n == 0);
+      atomicAdd(&hist[n < kLenBuckets ? n : kLenBuckets - 1], 1u);
     }
   }
   if (__syncthreads_or(zero) && threadIdx.x == 0) atomicOr(F.status, kStCount);
   block_excl_scan<256>(sum, tot);
   if (threadIdx.x == 0) F.blk_sum[lb] = tot;
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x)
+    if (hist[i]) atomicAdd(&F.len_cursor[i], hist[i]);
 }
 
-// Per frame: offsets of the track blocks, unattached bin starts, count checks.
+// Per frame: offsets of the track blocks, decode-order bucket offsets (longest
+// first), unattached bin starts, count checks.
 __global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, PlanDev plan) {
   uint32_t tot;
   const FrameDev& F = frames[blockIdx.x];
@@ -159,6 +166,12 @@ __global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, Pla
     carry += tot;
   }
   if (tid == 0 && carry != F.n_att) atomicOr(F.status, kStCount);
+  {
+    const uint32_t b = kLenBuckets - 1 - tid;  // descending length
+    const uint32_t v = F.len_cursor[b];
+    const uint32_t e = block_excl_scan<1024>(v, tot);
+    F.len_cursor[b] = e;
+  }
   {
     // unattached bin starts: kBinPerThread consecutive bins per thread, one scan
     constexpr int Q = (kNBin + 1023) / 1024;
@@ -181,33 +194,27 @@ __global__ void __launch_bounds__(1024) k_frame_scan(const FrameDev* frames, Pla
     F.unatt_start[kNBin] = (uint32_t)carry;
     if (carry != F.n_unatt) atomicOr(F.status, kStCount);
   }
-  // attached counts per bin: summed into by k_group_sum (an encoding call has
-  // none)
+  // attached counts per bin: summed into by k_group_sum (an encoding call
+  // has none)
   if (F.att_count)
     for (uint32_t b = tid; b < (uint32_t)kNBin; b += 1024) F.att_count[b] = 0u;
 }
 
-// Per-block counts of tracks per (part, length bucket): shared-memory
-// histogram of all parts, one global atomic per non-empty entry.
-struct PartHist {
-  uint32_t c[kMaxParts][kOrderBuckets];
-};
-
-// trackStart, the head bitmap (bit trackStart[t] of every track, for
-// k_key_rank) and the track counts per (part, frame, length bucket).
+// trackStart and decode order.  A block first counts its tracks per length
+// bucket in shared memory and reserves each bucket's range of the order with
+// one global atomic per bucket; the order of tracks of equal length is
+// arbitrary (it only changes which warp decodes a track, not a result).
 __global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, PlanDev plan) {
-  __shared__ PartHist s_h;
+  __shared__ uint32_t s_cnt[kLenBuckets];
   uint32_t tot;
   const uint32_t f = find_frame(plan.pre_tblk, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
   if (*F.status & kStCount) return;
-  uint32_t* hflat = &s_h.c[0][0];
-  for (int i = threadIdx.x; i < kMaxParts * kOrderBuckets; i += blockDim.x) hflat[i] = 0u;
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) s_cnt[i] = 0u;
   const uint32_t lb = blockIdx.x - plan.pre_tblk[f];
   const uint32_t t0 = lb * kTrackBlk + threadIdx.x * 8;
   const uint32_t nt = F.n_tracks;
-  const uint32_t tile0 = plan.pre_tile[f];
-  uint32_t n[8];
+  uint32_t n[8], slot[8];
   uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < 8; k++) {
@@ -215,134 +222,28 @@ __global__ void __launch_bounds__(256) k_track_scan2(const FrameDev* frames, Pla
     n[k] = t < nt ? (uint32_t)F.ncl[t] : 0u;
     sum += n[k];
   }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 8; k++)
+    if (t0 + k < nt) slot[k] = atomicAdd(&s_cnt[n[k] < kLenBuckets ? n[k] : kLenBuckets - 1], 1u);
   uint32_t start = F.blk_sum[lb] + block_excl_scan<256>(sum, tot);  // synchronises the block
+  for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) {
+    const uint32_t c = s_cnt[i];
+    if (c) s_cnt[i] = atomicAdd(&F.len_cursor[i], c);
+  }
+  __syncthreads();
   uint32_t* __restrict__ track_start = F.track_start;
+  uint32_t* __restrict__ order = F.order;
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     const uint32_t t = t0 + k;
     if (t < nt) {
       track_start[t] = start;
-      if (F.heads) atomicOr(&F.heads[start >> 5], 1u << (start & 31));
-      const uint32_t part = part_of_tile(tile0 + start / (uint32_t)kTile, plan.n_parts,
-                                         plan.n_tiles);
-      atomicAdd(&s_h.c[part][order_bucket(n[k])], 1u);
+      order[s_cnt[n[k] < kLenBuckets ? n[k] : kLenBuckets - 1] + slot[k]] = t;
       start += n[k];
       if (t == nt - 1) track_start[nt] = start;
     }
   }
-  __syncthreads();
-  const uint32_t nf = plan.n_frames;
-  for (uint32_t i = threadIdx.x; i < plan.n_parts * (uint32_t)kOrderBuckets; i += blockDim.x) {
-    const uint32_t c = hflat[i];
-    if (c) {
-      const uint32_t part = i / kOrderBuckets, b = i % kOrderBuckets;
-      atomicAdd(&plan.part_cnt[((size_t)part * nf + f) * kOrderBuckets + b], c);
-    }
-  }
-}
-
-// One block per (part, frame): the frame's tracks of the part are the range
-// [a, b) of its track indices (those whose first cluster lies in the part's
-// tiles); the decode-order cursor of length bucket i is a plus the tracks of
-// the longer buckets.
-__global__ void __launch_bounds__(kOrderBuckets) k_part_scan(const FrameDev* frames,
-                                                             PlanDev plan) {
-  __shared__ uint32_t s_ab[2];
-  uint32_t tot;
-  const uint32_t nf = plan.n_frames;
-  const uint32_t part = blockIdx.x / nf, f = blockIdx.x % nf;
-  const FrameDev& F = frames[f];
-  const bool live = !(*F.status & kStCount);
-  if (threadIdx.x < 2) {
-    uint32_t r = 0;
-    if (live) {
-      // frame-local tile bound of the part, clamped to the frame's tiles
-      const uint32_t g = part_first_tile(part + threadIdx.x, plan.n_parts, plan.n_tiles);
-      const uint32_t t_lo = plan.pre_tile[f], t_n = plan.pre_tile[f + 1] - t_lo;
-      const uint32_t lt = g <= t_lo ? 0u : (g - t_lo < t_n ? g - t_lo : t_n);
-      // first track whose first cluster is at or after tile lt
-      if (lt >= t_n) {
-        r = F.n_tracks;
-      } else {
-        const uint64_t j = (uint64_t)lt * kTile;
-        uint32_t lo = 0, hi = F.n_tracks;  // answer in [lo, hi]
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if ((uint64_t)F.track_start[mid] < j) lo = mid + 1; else hi = mid;
-        }
-        r = lo;
-      }
-    }
-    s_ab[threadIdx.x] = r;
-  }
-  __syncthreads();
-  const uint32_t a = s_ab[0], b = s_ab[1];
-  uint32_t* cnt = plan.part_cnt + ((size_t)part * nf + f) * kOrderBuckets;
-  const uint32_t c = live ? cnt[threadIdx.x] : 0u;
-  const uint32_t e = block_excl_scan<kOrderBuckets>(c, tot);
-  cnt[threadIdx.x] = a + e;
-  if (threadIdx.x == 0) {
-    plan.part_lo[(size_t)part * nf + f] = a;
-    plan.part_hi[(size_t)part * nf + f] = live ? b : a;
-  }
-}
-
-// The decode order: every track at its bucket's cursor (a block reserves each
-// bucket's range with one global atomic; tracks of equal length in any order,
-// which changes only which warp decodes a track, not a result).  The last
-// block (blockIdx.x == number of track-scan blocks) computes the warp-task
-// prefixes over frames of every part instead.
-__global__ void __launch_bounds__(256) k_track_place(const FrameDev* frames, PlanDev plan) {
-  __shared__ PartHist s_h;
-  const uint32_t nf = plan.n_frames;
-  if (blockIdx.x == plan.pre_tblk[nf]) {
-    if (threadIdx.x < plan.n_parts) {
-      const uint32_t part = threadIdx.x;
-      uint32_t run = 0;
-      for (uint32_t f = 0; f < nf; f++) {
-        plan.part_task_pre[(size_t)part * (nf + 1) + f] = run;
-        const size_t i = (size_t)part * nf + f;
-        run += (plan.part_hi[i] - plan.part_lo[i] + 31) / 32;
-      }
-      plan.part_task_pre[(size_t)part * (nf + 1) + nf] = run;
-    }
-    return;
-  }
-  const uint32_t f = find_frame(plan.pre_tblk, nf, blockIdx.x);
-  const FrameDev& F = frames[f];
-  if (*F.status & kStCount) return;
-  uint32_t* hflat = &s_h.c[0][0];
-  for (int i = threadIdx.x; i < kMaxParts * kOrderBuckets; i += blockDim.x) hflat[i] = 0u;
-  __syncthreads();
-  const uint32_t lb = blockIdx.x - plan.pre_tblk[f];
-  const uint32_t t0 = lb * kTrackBlk + threadIdx.x * 8;
-  const uint32_t nt = F.n_tracks;
-  const uint32_t tile0 = plan.pre_tile[f];
-  uint32_t key[8], slot[8];
-#pragma unroll
-  for (int k = 0; k < 8; k++) {
-    const uint32_t t = t0 + k;
-    key[k] = 0xFFFFFFFFu;
-    if (t < nt) {
-      const uint32_t part = part_of_tile(tile0 + F.track_start[t] / (uint32_t)kTile,
-                                         plan.n_parts, plan.n_tiles);
-      key[k] = part * kOrderBuckets + order_bucket(F.ncl[t]);
-      slot[k] = atomicAdd(&hflat[key[k]], 1u);
-    }
-  }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < plan.n_parts * (uint32_t)kOrderBuckets; i += blockDim.x) {
-    const uint32_t c = hflat[i];
-    if (c) {
-      const uint32_t part = i / kOrderBuckets, b = i % kOrderBuckets;
-      hflat[i] = atomicAdd(&plan.part_cnt[((size_t)part * nf + f) * kOrderBuckets + b], c);
-    }
-  }
-  __syncthreads();
-  uint32_t* __restrict__ order = F.order;
-#pragma unroll
-  for (int k = 0; k < 8; k++)
-    if (key[k] != 0xFFFFFFFFu) order[hflat[key[k]] + slot[k]] = t0 + k;
 }
 
 // Sum of the tile histograms over groups of kGroup tiles, per bin; the group

@@ -3,7 +3,7 @@
 //
 // Cluster j of ranking tile t with key b and rank r goes to native index
 //   tileBase[t][b] + r
-// (k_key_rank, k_tile_base).  The record is assembled from the decoded pad
+// (k_count_rank, k_tile_base).  The record is assembled from the decoded pad
 // and time codes (k_track_decode) and the charge streams.  The destinations of
 // consecutive clusters are unrelated (consecutive clusters of a track lie in
 // different rows), so writing records in input order costs two L2 write
@@ -25,10 +25,10 @@ namespace tmd {
 //          32-byte sector) instead of two.
 template <int V, int U>
 __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev* frames,
-                                                                 PlanDev plan, uint32_t tile_lo) {
+                                                                 PlanDev plan) {
   constexpr uint32_t kPerBlock = kScatThreads * U;
   constexpr uint32_t kBlocksPerTile = kTile / kPerBlock;
-  const uint32_t gtile = tile_lo + blockIdx.x / kBlocksPerTile;
+  const uint32_t gtile = blockIdx.x / kBlocksPerTile;
   const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
   const FrameDev& F = frames[f];
   if (*F.status & kStCount) return;
@@ -107,13 +107,13 @@ __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev*
   if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(frames[f].status, kStLimit);
 }
 
-void launch_att_scatter(int variant, uint32_t tile_lo, uint32_t n_tiles, cudaStream_t st,
-                        const FrameDev* frames, PlanDev plan) {
+void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
+                        PlanDev plan) {
   const uint32_t grid = n_tiles * (kTile / (kScatThreads * 4));
   if (variant == 0)
-    k_att_scatter<0, 4><<<grid, kScatThreads, 0, st>>>(frames, plan, tile_lo);
+    k_att_scatter<0, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);
   else
-    k_att_scatter<1, 4><<<grid, kScatThreads, 0, st>>>(frames, plan, tile_lo);
+    k_att_scatter<1, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);
 }
 
 }  // namespace tmd

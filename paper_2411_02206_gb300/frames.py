@@ -43,17 +43,20 @@ def truth_attached(truth: dict) -> dict:
     return {k: truth[k] for k in ("qpt", "ncl", "row", "sector", "leg", "pad", "time")}
 
 
-def assemble(truth_dev: dict, enc_dev: dict) -> dict:
+def assemble(truth_dev: dict, enc_dev: dict, unatt_dev: dict | None = None) -> dict:
     """Compressed frame (device tensors) from the device truth and the
-    encoder's output: headers and residual streams from the encoder, charge
-    streams from the truth (already in compressed form), unattached streams
-    from the generator."""
+    encoder's output: headers and residual streams from the track encoder,
+    charge streams of the attached clusters from the truth (already in
+    compressed form), unattached streams from the unattached encoder
+    (unatt_dev) or, without it, from the generator."""
     f = {}
     for k in ("qpt", "row", "slice", "pad", "time", "ncl", "row_diff", "slice_leg_diff",
               "pad_res", "time_res"):
         f[k] = enc_dev[k]
-    for k in ("qtot_a", "qmax_a", "flags_a", "sigma_pad_a", "sigma_time_a") + synth.UNATT:
+    for k in ("qtot_a", "qmax_a", "flags_a", "sigma_pad_a", "sigma_time_a"):
         f[k] = truth_dev[k]
+    for k in synth.UNATT:
+        f[k] = (unatt_dev if unatt_dev is not None else truth_dev)[k]
     return f
 
 

@@ -162,7 +162,7 @@ def _helix_chunk(rng, pt, q, phi0, sinh_eta, t0, r_first, max_legs, drop, smear)
 def make_truth(n_tracks: int, n_unatt: int, seed: int, *, looper_frac: float = 0.17,
                secondary_frac: float = 0.65, pt_mean: float = 0.5, max_legs: int = 3,
                min_clusters: int = 20, max_clusters: int = 65535, empty_frac: float = 0.0, hot_frac: float = 0.0,
-               hot_share: float = 0.0, chunk: int = 16384) -> dict:
+               hot_share: float = 0.0, chunk: int = 16384, unatt_truth: bool = False) -> dict:
     """Attached-cluster truth of a frame (the encoder's input) plus the
     unattached part of the compressed frame.
 
@@ -175,7 +175,8 @@ def make_truth(n_tracks: int, n_unatt: int, seed: int, *, looper_frac: float = 0
 
     Keys: qpt, ncl (per track); row, sector, leg, pad, time, qtot_a, qmax_a,
     flags_a, sigma_pad_a, sigma_time_a (per attached cluster); and the
-    unattached fields of FIELDS."""
+    unattached fields of FIELDS (compressed form), or with unatt_truth the
+    unattached clusters as truth (UNATT_TRUTH, for the unattached encoder)."""
     rng = np.random.default_rng(seed)
     parts = []
     qcodes = []
@@ -222,7 +223,10 @@ def make_truth(n_tracks: int, n_unatt: int, seed: int, *, looper_frac: float = 0
     na = int(f["ncl"].astype(np.int64).sum())
     (f["qtot_a"], f["qmax_a"], f["flags_a"], f["sigma_pad_a"], f["sigma_time_a"]) = \
         _charges(rng, na)
-    f.update(make_unattached(rng, n_unatt, empty_frac, hot_frac, hot_share))
+    if unatt_truth:
+        f.update(make_unattached_truth(rng, n_unatt, empty_frac, hot_frac, hot_share))
+    else:
+        f.update(make_unattached(rng, n_unatt, empty_frac, hot_frac, hot_share))
     return f
 
 
