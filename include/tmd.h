@@ -339,12 +339,9 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *   "decode_variant"      0..1  staging of the track decoder: rounds of 16 (0)
  *                               or 8 (1) model steps, each lane's next round
  *                               copied asynchronously while it runs the current
- *   "scatter_variant"     0..2  stores of the record scatter: in input order,
- *                               one record per thread (0) or three lanes per
- *                               record in one store instruction (1); or each
- *                               ranking tile regrouped into native order
- *                               through the distributed shared memory of a
- *                               cluster of 8 CTAs, then written in order (2)
+ *   "scatter_variant"     0..1  stores of the record scatter: one record per
+ *                               thread (0), or three lanes per record in one
+ *                               store instruction (1)
  *   "unatt_variant"       0..1  record write-out of the unattached decoder:
  *                               word by word (0) or one staged 16-byte
  *                               {record, index} entry per thread (1)

@@ -118,9 +118,8 @@ void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& pof
   L.keys = p((size_t)na * 2 + 16);
   L.kf_pad = p((size_t)na * 2 + 16);
   L.kf_time = p((size_t)na * 4 + 16);
-  L.tpos = p((size_t)na * 2 + 4);
+  L.rank = p((size_t)na * 2 + 4);
   L.tile_hist = p((size_t)L.n_tiles * kNBin * 2 + 4);
-  L.tile_lbase = p((size_t)L.n_tiles * kNBin * 2 + 4);
   L.group_sum = p((size_t)L.n_groups * kNBin * 4 + 4);
   L.tile_base = p((size_t)L.n_tiles * kNBin * 4 + 4);
   L.unatt_start = p(((size_t)kNBin + 1) * 4);
@@ -242,7 +241,6 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->scratch_done, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, prepare_count_rank(), "smem attribute")) != TMD_OK ||
-      (rc = tmd_cuda_check(h, prepare_att_scatter(), "smem attribute")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(0, &h->occ_decode_v[0]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_track_decode(1, &h->occ_decode_v[1]), "occupancy")) != TMD_OK ||
       (rc = tmd_cuda_check(h, occupancy_unatt_decode(&h->occ_unatt), "occupancy")) != TMD_OK ||
@@ -479,9 +477,8 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     F.keys = reinterpret_cast<uint16_t*>(pb + l.keys);
     F.kf_pad = reinterpret_cast<uint16_t*>(pb + l.kf_pad);
     F.kf_time = reinterpret_cast<uint32_t*>(pb + l.kf_time);
-    F.tpos = reinterpret_cast<uint16_t*>(pb + l.tpos);
+    F.rank = reinterpret_cast<uint16_t*>(pb + l.rank);
     F.tile_hist = reinterpret_cast<uint16_t*>(pb + l.tile_hist);
-    F.tile_lbase = reinterpret_cast<uint16_t*>(pb + l.tile_lbase);
     F.group_sum = reinterpret_cast<uint32_t*>(pb + l.group_sum);
     F.tile_base = reinterpret_cast<uint32_t*>(pb + l.tile_base);
     F.unatt_start = reinterpret_cast<uint32_t*>(pb + l.unatt_start);

@@ -118,8 +118,8 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
 struct FrameLayout {
   uint32_t n_tblocks, n_tiles, n_groups, n_chunks;
   size_t z_len, z_lb;                             // offsets in the zeroed part
-  size_t track_start, order, keys, kf_pad, kf_time, tpos, tile_hist, tile_lbase, group_sum,
-      tile_base, unatt_start, blk_sum, att_count; // offsets in the plain part
+  size_t track_start, order, keys, kf_pad, kf_time, rank, tile_hist, group_sum, tile_base,
+      unatt_start, blk_sum, att_count;            // offsets in the plain part
 };
 // Append the scratch of one frame to the zeroed (zoff) and plain (poff) parts.
 void plan_frame(uint32_t nt, uint32_t na, uint32_t nu, size_t& zoff, size_t& poff,

@@ -64,13 +64,10 @@ struct FrameDev {
   uint16_t* keys;          // n_att: (sector,row) bin of every attached cluster
   uint16_t* kf_pad;        // n_att: decoded pad code of every attached cluster
   uint32_t* kf_time;       // n_att: decoded time code of every attached cluster
-  uint16_t* tpos;          // n_att: place of a cluster among its tile's clusters ordered by
-                           // (bin, input order)
+  uint16_t* rank;          // n_att: rank of a cluster within its (tile, bin)
   uint16_t* tile_hist;     // n_tiles x kNBin
-  uint16_t* tile_lbase;    // n_tiles x kNBin: first place of bin b among the tile's clusters
   uint32_t* group_sum;     // n_groups x kNBin
-  uint32_t* tile_base;     // n_tiles x kNBin: native index of the tile's place 0 for bin b
-                           // (first native index of (tile, b) minus tile_lbase, mod 2^32)
+  uint32_t* tile_base;     // n_tiles x kNBin: first native index of (tile, bin)
   uint32_t* unatt_start;   // kNBin + 1
   uint32_t* blk_sum;       // n_tblocks
   uint32_t* len_cursor;    // kLenBuckets (zeroed)
@@ -166,11 +163,10 @@ __global__ void k_tile_base(const FrameDev* frames, PlanDev plan);
 void launch_track_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
                          PlanDev plan, uint32_t n_tasks);
 cudaError_t occupancy_track_decode(int variant, int* blocks_per_sm);
-// Record scatter variants 0, 1, 2 (identical results; see tmd_scatter.cu),
+// Record scatter variants 0, 1 (identical results; see tmd_scatter.cu),
 // launched over n_tiles ranking tiles of all frames.
 void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan);
-cudaError_t prepare_att_scatter();
 // Unattached decode variants 0, 1 (record write-out word by word or one
 // record per thread; identical results), launched through these functions.
 void launch_unatt_decode(int variant, uint32_t grid, cudaStream_t st, const FrameDev* frames,
@@ -183,12 +179,6 @@ __global__ void k_track_trace(const FrameDev* frames, const uint32_t* ids, uint3
                               float* state);
 
 constexpr int kRankBitmapWords = (kNBin + 31) / 32;
-constexpr int kCountRankSmem =
-    kTileWarps * kNBin * 2 + kTileWarps * kRankBitmapWords * 4 + ((kNBin * 2 + 15) / 16) * 16;
-// Regrouping record scatter: a thread-block cluster of kRgCta CTAs per ranking
-// tile, each holding kTile / kRgCta places of the tile as 16-byte entries.
-constexpr int kRgCta = 8;
-constexpr int kRgThreads = 512;
-constexpr int kRgSmem = (kTile / kRgCta) * 16;
+constexpr int kCountRankSmem = kTileWarps * kNBin * 2 + kTileWarps * kRankBitmapWords * 4;
 
 }  // namespace tmd

@@ -105,7 +105,7 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
     if (!S->ready) {
       int sms = 0, od = 0, ou = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          prepare_count_rank() != cudaSuccess || prepare_att_scatter() != cudaSuccess ||
+          prepare_count_rank() != cudaSuccess ||
           occupancy_track_decode(0, &od) != cudaSuccess ||
           occupancy_unatt_decode(&ou) != cudaSuccess) {
         set_err(err, err_len, "device set-up failed");
@@ -143,9 +143,8 @@ extern "C" int tmd_decode_frame_noalloc(const tmd_frame_in* in, const tmd_frame_
   F.keys = reinterpret_cast<uint16_t*>(pb + L.keys);
   F.kf_pad = reinterpret_cast<uint16_t*>(pb + L.kf_pad);
   F.kf_time = reinterpret_cast<uint32_t*>(pb + L.kf_time);
-  F.tpos = reinterpret_cast<uint16_t*>(pb + L.tpos);
+  F.rank = reinterpret_cast<uint16_t*>(pb + L.rank);
   F.tile_hist = reinterpret_cast<uint16_t*>(pb + L.tile_hist);
-  F.tile_lbase = reinterpret_cast<uint16_t*>(pb + L.tile_lbase);
   F.group_sum = reinterpret_cast<uint32_t*>(pb + L.group_sum);
   F.tile_base = reinterpret_cast<uint32_t*>(pb + L.tile_base);
   F.unatt_start = reinterpret_cast<uint32_t*>(pb + L.unatt_start);

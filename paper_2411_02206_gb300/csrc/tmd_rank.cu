@@ -19,13 +19,7 @@
 //                 distinct rows, so most steps take this path.  A step with a
 //                 repeated key orders equal keys by lane with match.any.
 //
-// The kernel writes, instead of the rank, the cluster's place among the
-// tile's clusters ordered by (bin, input order): tpos[j] = lbase[key] + rank
-// with lbase the exclusive prefix of the tile histogram over the bins (also
-// written, per tile).  The native index of cluster j is then
-// tileBase[tile][key] + tpos[j], tileBase holding the first native index of
-// (tile, bin) minus lbase (k_tile_base): the input-order scatter needs no
-// lbase, and the regrouping scatter places records by tpos directly.
+// The native index of cluster j is then tileBase[tile][key] + rank[j].
 #include "tmd_internal.cuh"
 
 namespace tmd {
@@ -39,7 +33,7 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
   const uint32_t tile = blockIdx.x - plan.pre_tile[f];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint16_t* __restrict__ keys = F.keys;
-  uint16_t* __restrict__ tpos = F.tpos;
+  uint16_t* __restrict__ rank = F.rank;
   uint16_t* __restrict__ tile_hist = F.tile_hist;
   const uint32_t n_att = F.n_att;
   uint32_t* hist32 = s_mem + wid * (kNBin / 2);
@@ -78,52 +72,17 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
     }
   }
   __syncthreads();
-  // per-warp exclusive offsets within the tile; tile histogram; the tile's
-  // bin starts lbase (exclusive prefix over the bins, kept in shared memory
-  // behind the bitmaps), each thread a contiguous range of bins
+  // per-warp exclusive offsets within the tile; tile histogram
   uint16_t* hall = reinterpret_cast<uint16_t*>(s_mem);
-  uint16_t* s_lbase = reinterpret_cast<uint16_t*>(s_mem + kTileWarps * (kNBin / 2) +
-                                                  kTileWarps * kRankBitmapWords);
-  constexpr int kPer = (kNBin + 255) / 256;
-  uint32_t tot[kPer], sum = 0;
-  const uint32_t b0 = threadIdx.x * kPer;
-#pragma unroll
-  for (int i = 0; i < kPer; i++) {
-    const uint32_t b = b0 + i;
+  for (int b = threadIdx.x; b < kNBin; b += blockDim.x) {
     uint32_t run = 0;
-    if (b < (uint32_t)kNBin) {
 #pragma unroll
-      for (int ww = 0; ww < kTileWarps; ww++) {
-        const uint32_t c = hall[ww * kNBin + b];
-        hall[ww * kNBin + b] = (uint16_t)run;
-        run += c;
-      }
-      tile_hist[(size_t)tile * kNBin + b] = (uint16_t)run;
+    for (int ww = 0; ww < kTileWarps; ww++) {
+      const uint32_t c = hall[ww * kNBin + b];
+      hall[ww * kNBin + b] = (uint16_t)run;
+      run += c;
     }
-    tot[i] = run;
-    sum += run;
-  }
-  {
-    __shared__ uint32_t s_part[8];
-    uint32_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_part[wid] = x;
-    __syncthreads();
-    uint32_t base = x - sum;
-    for (int w = 0; w < wid; w++) base += s_part[w];
-#pragma unroll
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t b = b0 + i;
-      if (b < (uint32_t)kNBin) {
-        s_lbase[b] = (uint16_t)base;
-        F.tile_lbase[(size_t)tile * kNBin + b] = (uint16_t)base;
-      }
-      base += tot[i];
-    }
+    tile_hist[(size_t)tile * kNBin + b] = (uint16_t)run;
   }
   __syncthreads();
   // pass 2: stable ranks in stream order; the keys of the next 8 steps are
@@ -155,7 +114,7 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
         if (in) {
           const uint32_t base = hist[k];
           hist[k] = (uint16_t)(base + 1);
-          tpos[j] = (uint16_t)(s_lbase[k] + base);
+          rank[j] = (uint16_t)base;
         }
       } else {
         const uint32_t act = __ballot_sync(0xffffffffu, in);
@@ -165,7 +124,7 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
           const uint32_t r = base + __popc(peers & lanemask_lt());
           __syncwarp(act);
           if (lane == __ffs(peers) - 1) hist[k] = (uint16_t)(base + __popc(peers));
-          tpos[j] = (uint16_t)(s_lbase[k] + r);
+          rank[j] = (uint16_t)r;
         }
       }
       __syncwarp();

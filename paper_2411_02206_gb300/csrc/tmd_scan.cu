@@ -295,10 +295,8 @@ __global__ void __launch_bounds__(1024) k_row_offsets(const FrameDev* frames, Pl
   row_start_scan(F);
 }
 
-// Base of every (tile, bin): rowStart plus the counts of the bin in the groups
-// and tiles before, minus the tile's start of the bin among its own clusters
-// (tile_lbase), so that a cluster's native index is the base plus its place
-// in the tile (mod 2^32 arithmetic).
+// First native index of every (tile, bin): rowStart plus the counts of the
+// bin in the groups and tiles before.
 __global__ void __launch_bounds__(kBinBlk) k_tile_base(const FrameDev* frames, PlanDev plan) {
   const uint32_t f = find_frame(plan.pre_grp, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
@@ -311,20 +309,16 @@ __global__ void __launch_bounds__(kBinBlk) k_tile_base(const FrameDev* frames, P
   uint32_t* __restrict__ tbase = F.tile_base;
   const uint32_t t0 = g * kGroup, nt = min((uint32_t)kGroup, F.n_tiles - t0);
   const uint16_t* __restrict__ hist = F.tile_hist + (size_t)t0 * kNBin + b;
-  const uint16_t* __restrict__ lbase = F.tile_lbase + (size_t)t0 * kNBin + b;
-  // the group's tile counts and starts first (all loads in flight), then the bases
-  uint32_t c[kGroup], s[kGroup];
+  // the group's tile counts first (all loads in flight), then the bases
+  uint32_t c[kGroup];
 #pragma unroll
-  for (uint32_t k = 0; k < (uint32_t)kGroup; k++) {
-    c[k] = k < nt ? (uint32_t)hist[(size_t)k * kNBin] : 0u;
-    s[k] = k < nt ? (uint32_t)lbase[(size_t)k * kNBin] : 0u;
-  }
+  for (uint32_t k = 0; k < (uint32_t)kGroup; k++) c[k] = k < nt ? (uint32_t)hist[(size_t)k * kNBin] : 0u;
   uint32_t run = F.row_start[b];
 #pragma unroll 8
   for (uint32_t gg = 0; gg < g; gg++) run += gsum[(size_t)gg * kNBin + b];
 #pragma unroll
   for (uint32_t k = 0; k < (uint32_t)kGroup; k++) {
-    if (k < nt) tbase[(size_t)(t0 + k) * kNBin + b] = run - s[k];
+    if (k < nt) tbase[(size_t)(t0 + k) * kNBin + b] = run;
     run += c[k];
   }
 }

@@ -1,32 +1,15 @@
 // tmd_scatter.cu -- native records of the attached clusters (arXiv:2411.02206,
 // Sec. 4: the decoded clusters end up in the native per-(sector,row) list).
 //
-// Cluster j of ranking tile t with key b has the place tpos[j] among the
-// tile's clusters ordered by (bin, input order) and goes to native index
-//   tileBase[t][b] + tpos[j]
+// Cluster j of ranking tile t with key b and rank r goes to native index
+//   tileBase[t][b] + r
 // (k_count_rank, k_tile_base).  The record is assembled from the decoded pad
-// and time codes (k_track_decode) and the charge streams.
-//
-// Input order (variants 0, 1): the destinations of consecutive clusters are
-// unrelated (consecutive clusters of a track lie in different rows), so every
-// record is a partial write of its own sectors; variant 1 lets three lanes
-// write the three words of one record in the same store instruction.
-//
-// Regrouped (variant 2): the records of a (tile, bin) pair are contiguous in
-// the native list (a run of about six for the Pb-Pb frame), and written in
-// tile order, consecutive threads writing consecutive records, they go out as
-// whole sectors: a probe of the store patterns alone measured 0.21 ms for the
-// Pb-Pb frame's 37.8 M attached records in that order against 0.48 ms in
-// input order.  A tile is 32768 places, more than one CTA holds, so a
-// thread-block cluster of kRgCta CTAs takes it: each CTA loads its slice of
-// the tile's clusters, sends every record with its bin to the CTA that owns
-// its place (place / (kTile / kRgCta)) through distributed shared memory, and
-// after the cluster barrier writes its own places in order.
-#include <cooperative_groups.h>
-
+// and time codes (k_track_decode) and the charge streams.  The destinations of
+// consecutive clusters are unrelated (consecutive clusters of a track lie in
+// different rows), so writing records in input order costs two L2 write
+// requests per 12-byte record; variant 1 lets three lanes write the three
+// words of one record in the same store instruction.
 #include "tmd_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace tmd {
 
@@ -53,7 +36,7 @@ __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev*
   const uint32_t jb = tile * (uint32_t)kTile + (blockIdx.x % kBlocksPerTile) * kPerBlock;
   const uint32_t n_att = F.n_att, n_total = F.n_att + F.n_unatt;
   const uint16_t* __restrict__ keys = F.keys;
-  const uint16_t* __restrict__ tpos = F.tpos;
+  const uint16_t* __restrict__ rank = F.rank;
   const uint16_t* __restrict__ kpad = F.kf_pad;
   const uint32_t* __restrict__ ktime = F.kf_time;
   const uint16_t* __restrict__ qtot = F.qtot_a;
@@ -72,7 +55,7 @@ __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev*
     ky[u] = 0xFFFFu;
     if (j < n_att) {
       ky[u] = keys[j];
-      rk[u] = tpos[j];
+      rk[u] = rank[j];
       pd[u] = kpad[j];
       tm[u] = ktime[j];
       qm[u] = qmax[j];
@@ -124,113 +107,10 @@ __global__ void __launch_bounds__(kScatThreads, 4) k_att_scatter(const FrameDev*
   if (__syncthreads_or(st != 0) && threadIdx.x == 0) atomicOr(frames[f].status, kStLimit);
 }
 
-// Variant 2: one cluster of kRgCta CTAs per ranking tile.
-__global__ void __cluster_dims__(kRgCta, 1, 1) __launch_bounds__(kRgThreads, 2)
-    k_att_scatter_rg(const FrameDev* frames, PlanDev plan) {
-  extern __shared__ uint4 s_rec[];  // kTile / kRgCta places: {w0, w1, w2, bin}
-  constexpr uint32_t kPlaces = kTile / kRgCta;
-  constexpr int kPer = kPlaces / kRgThreads;
-  cg::cluster_group cluster = cg::this_cluster();
-  const uint32_t q = cluster.block_rank();
-  const uint32_t gtile = blockIdx.x / kRgCta;
-  const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, gtile);
-  const FrameDev& F = frames[f];
-  if (*F.status & kStCount) return;  // the same for every CTA of the cluster
-  const uint32_t tile = gtile - plan.pre_tile[f];
-  const uint32_t n_att = F.n_att, n_total = F.n_att + F.n_unatt;
-  const uint32_t tid = threadIdx.x;
-  const uint16_t* __restrict__ keys = F.keys;
-  const uint16_t* __restrict__ tpos = F.tpos;
-  const uint16_t* __restrict__ kpad = F.kf_pad;
-  const uint32_t* __restrict__ ktime = F.kf_time;
-  const uint16_t* __restrict__ qtot = F.qtot_a;
-  const uint16_t* __restrict__ qmax = F.qmax_a;
-  const uint8_t* __restrict__ flags = F.flags_a;
-  const uint8_t* __restrict__ sigp = F.sigp_a;
-  const uint8_t* __restrict__ sigt = F.sigt_a;
-  const uint32_t j_tile = tile * (uint32_t)kTile;
-  const uint32_t n_tile = min((uint32_t)kTile, n_att - j_tile);  // places of this tile
-  // this CTA's slice of the tile's clusters in kPer / kG groups of kG per
-  // thread: the next group's loads are in flight while the current group
-  // goes to its places
-  constexpr int kG = 2;
-  constexpr int kGroups = kPer / kG;
-  const uint32_t jb = j_tile + q * kPlaces;
-  uint32_t ky[kG], ps[kG], pd[kG], tm[kG], qm[kG], qt[kG], fl[kG], sg[kG], sp[kG];
-  auto load = [&](int g) {
-#pragma unroll
-    for (int u = 0; u < kG; u++) {
-      const uint32_t j = jb + (g * kG + u) * kRgThreads + tid;
-      ky[u] = 0xFFFFFFFFu;
-      if (j < n_att) {
-        ky[u] = keys[j];
-        ps[u] = tpos[j];
-        pd[u] = kpad[j];
-        tm[u] = ktime[j];
-        qm[u] = qmax[j];
-        qt[u] = qtot[j];
-        fl[u] = flags[j];
-        sg[u] = sigt[j];
-        sp[u] = sigp[j];
-      }
-    }
-  };
-  cluster.sync();  // every CTA of the cluster runs before the remote stores
-  load(0);
-#pragma unroll
-  for (int g = 0; g < kGroups; g++) {
-    uint4 rec[kG];
-    uint32_t place[kG];
-#pragma unroll
-    for (int u = 0; u < kG; u++) {
-      place[u] = ky[u] != 0xFFFFFFFFu && ps[u] < n_tile ? ps[u] : 0xFFFFFFFFu;
-      rec[u] = make_uint4((tm[u] & 0xFFFFFFu) | (fl[u] << 24), pd[u] | (sg[u] << 16) | (sp[u] << 24),
-                          qm[u] | (qt[u] << 16), ky[u]);
-    }
-    if (g + 1 < kGroups) load(g + 1);
-#pragma unroll
-    for (int u = 0; u < kG; u++) {
-      if (place[u] != 0xFFFFFFFFu) {
-        const uint32_t owner = place[u] / kPlaces;
-        uint4* remote = cluster.map_shared_rank(s_rec, owner);
-        remote[place[u] - owner * kPlaces] = rec[u];
-      }
-    }
-  }
-  cluster.sync();  // every record is at its place
-  // this CTA's places in order, one record per thread and step
-  const uint32_t lo = q * kPlaces;
-  const uint32_t n_own = n_tile > lo ? min(kPlaces, n_tile - lo) : 0u;
-  const uint32_t* __restrict__ tbase = F.tile_base + (size_t)tile * kNBin;
-  uint32_t* __restrict__ nat = reinterpret_cast<uint32_t*>(F.native);
-  uint32_t st = 0;
-#pragma unroll 4
-  for (uint32_t l = tid; l < n_own; l += kRgThreads) {
-    const uint4 r = s_rec[l];
-    const uint32_t d = __ldg(tbase + r.w) + lo + l;
-    if (d < n_total) {
-      uint32_t* dst = nat + (size_t)d * 3;
-      dst[0] = r.x;
-      dst[1] = r.y;
-      dst[2] = r.z;
-    } else {
-      st = kStLimit;
-    }
-  }
-  if (__syncthreads_or(st != 0) && tid == 0) atomicOr(frames[f].status, kStLimit);
-}
-
-cudaError_t prepare_att_scatter() {
-  return cudaFuncSetAttribute(k_att_scatter_rg, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kRgSmem);
-}
-
 void launch_att_scatter(int variant, uint32_t n_tiles, cudaStream_t st, const FrameDev* frames,
                         PlanDev plan) {
   const uint32_t grid = n_tiles * (kTile / (kScatThreads * 4));
-  if (variant == 2)
-    k_att_scatter_rg<<<n_tiles * kRgCta, kRgThreads, kRgSmem, st>>>(frames, plan);
-  else if (variant == 0)
+  if (variant == 0)
     k_att_scatter<0, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);
   else
     k_att_scatter<1, 4><<<grid, kScatThreads, 0, st>>>(frames, plan);

@@ -218,7 +218,7 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
             dec.tmd_tune_set("overlap", ov)
             for dv in range(2):
                 dec.tmd_tune_set("decode_variant", dv)
-                for sv in range(3):
+                for sv in range(2):
                     dec.tmd_tune_set("scatter_variant", sv)
                     for uv in range(2):
                         dec.tmd_tune_set("unatt_variant", uv)
@@ -250,7 +250,7 @@ def test_unaligned_caller_arrays(dec):
         buf[1:] = t
         shifted[k] = buf[1:]
     saved = {k: dec.tmd_tune_get(k) for k in ("scatter_variant", "decode_variant")}
-    for sv in range(3):
+    for sv in range(2):
         dec.tmd_tune_set("scatter_variant", sv)
         for dv in range(2):
             dec.tmd_tune_set("decode_variant", dv)
