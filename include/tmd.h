@@ -350,6 +350,9 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
  *   "rans_overlap"   0..1  4-byte streams entropy-decoded on a second stream (1)
+ *   "coded_overlap"  0..1  tmd_decode_coded_frame: the attached charges and the
+ *                          unattached streams entropy-decoded on a second stream
+ *                          while the track decoder runs (1)
  * tmd_autotune times the decode chain on the given frames (device buffers,
  * decoded several times) for each candidate setting, keeps the fastest, and
  * writes it to the handle's autotune cache if tmd_config.autotune_cache was
@@ -489,8 +492,10 @@ int tmd_rans_decode(tmd_handle* h, const void* coded, uint64_t coded_bytes,
 
 /* Entropy decoding followed by track-model decoding of one coded frame: the
  * streams are decoded into handle-owned device memory (grown on demand) and
- * the frame is then decoded as by tmd_decode_frame into `out`, all on
- * `stream`.  out->status receives TMD_STATUS_CODED as well as the decoder's
+ * the frame is then decoded as by tmd_decode_frame into `out`, on `stream`
+ * (the streams only the record scatter and the unattached decode read are
+ * entropy-decoded on the handle's second stream beside the track decoder,
+ * tuning key coded_overlap).  out->status receives TMD_STATUS_CODED as well as the decoder's
  * bits.  Errors as tmd_rans_decode and tmd_decode_frame, plus TMD_ERR_NOMEM. */
 int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t coded_bytes,
                            uint32_t n_tracks, uint32_t n_attached, uint32_t n_unattached,

@@ -202,6 +202,7 @@ tmd_handle::~tmd_handle() {
   if (trace_status) cudaFree(trace_status);
   if (aux) cudaStreamDestroy(aux);
   if (fork) cudaEventDestroy(fork);
+  if (coded_late) cudaEventDestroy(coded_late);
   if (scratch_done) cudaEventDestroy(scratch_done);
   if (join) cudaEventDestroy(join);
   if (h2d) cudaStreamSynchronize(h2d), cudaStreamDestroy(h2d);
@@ -237,6 +238,8 @@ extern "C" int tmd_create(const tmd_config* cfg, tmd_handle** out) {
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming),
+                           "event")) != TMD_OK ||
+      (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->coded_late, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
       (rc = tmd_cuda_check(h, cudaEventCreateWithFlags(&h->scratch_done, cudaEventDisableTiming),
                            "event")) != TMD_OK ||
@@ -401,7 +404,7 @@ int tmd_launch(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fra
   tmd_handle::Slot& S = h->slots[slot];
   bool order = false;
   if ((rc = h->order_after_previous(st, &order)) != TMD_OK) return rc;
-  const ChainStreams cs{h->aux, h->fork, h->join};
+  const ChainStreams cs{h->aux, h->fork, h->join, h->late_inputs};
   rc = tmd_enqueue(h, nf, in, out, tin, tout, h->scratch, S.host, S.dev, st, h->prof.on,
                    tin ? nullptr : &cs, trace);
   if (rc != TMD_OK) return rc;
@@ -568,6 +571,7 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
         launch_unatt_decode(h->tune_unatt_variant, grid, s_, dframes, P, n_chunk);
       });
     };
+    if (cs && cs->late) CK(cudaStreamWaitEvent(st, cs->late, 0));
     if (two) {
       CK(cudaEventRecord(cs->fork, st));
       CK(cudaStreamWaitEvent(cs->aux, cs->fork, 0));

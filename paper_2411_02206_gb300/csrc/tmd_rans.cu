@@ -18,6 +18,10 @@
 // consecutive values per step.  Three launches, one per value width, size
 // blocks and shared memory for their tables (16, 32, 64 KB); the 4-byte
 // streams run on the handle's second stream beside the others.
+// tmd_decode_coded_frame entropy-decodes the streams the track decoder and the
+// ranking read first and the attached charges and unattached streams on the
+// second stream while the track decoder runs; the decode chain waits for them
+// before its record scatter and unattached decode.
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -409,7 +413,7 @@ template <> struct Shape<4> { static constexpr int kThreads = 512, kMinBlocks = 
 
 template <int W>
 cudaError_t launch_width(const uint8_t* coded, uint64_t bytes, const tmd_frame_arrays& dst,
-                         uint32_t* status, cudaStream_t st) {
+                         uint32_t* status, cudaStream_t st, uint32_t field_mask = ~0u) {
   constexpr int kT = Shape<W>::kThreads, kB = Shape<W>::kMinBlocks;
   void* const ptr[kFields] = {dst.qpt,     dst.row,         dst.slice,        dst.pad,
                               dst.time,    dst.ncl,         dst.qtot_a,       dst.qmax_a,
@@ -426,7 +430,7 @@ cudaError_t launch_width(const uint8_t* coded, uint64_t bytes, const tmd_frame_a
   J.status = status;
   uint32_t blocks = 0;
   for (int f = 0; f < kFields; f++) {
-    if (kWidth[f] != (uint32_t)W) continue;
+    if (kWidth[f] != (uint32_t)W || !((field_mask >> f) & 1u)) continue;
     JobField& F = J.f[J.nf++];
     F.dst = ptr[f];
     F.n = field_len(f, J.nt, J.na, J.nu);
@@ -436,6 +440,7 @@ cudaError_t launch_width(const uint8_t* coded, uint64_t bytes, const tmd_frame_a
     // at least one block per stream, so that every directory entry is checked
     blocks += std::max<uint32_t>(1, (F.nch + kT / 32 - 1) / (kT / 32));
   }
+  if (J.nf == 0) return cudaSuccess;
   const int smem = W * (int)kM * 4;
   auto kern = k_rans_decode<W, kT, kB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -562,6 +567,10 @@ extern "C" int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t
   if (!h) return TMD_ERR_ARG;
   if (!out || !out->status) return tmd_set_error(h, TMD_ERR_ARG, "null output");
   if (n_attached < n_tracks) return tmd_set_error(h, TMD_ERR_ARG, "n_attached < n_tracks");
+  if (!coded || (reinterpret_cast<uintptr_t>(coded) & 15))
+    return tmd_set_error(h, TMD_ERR_ARG, "coded frame must be 16-byte aligned");
+  if (coded_bytes < kHead)
+    return tmd_set_error(h, TMD_ERR_ARG, "coded frame shorter than its header");
   // handle-owned streams: each array 256-byte aligned, then the status word
   size_t off[kFields + 1], total = 0;
   for (int f = 0; f < kFields; f++) {
@@ -608,7 +617,35 @@ extern "C" int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t
   if ((rc = h->order_after_previous(st, &order)) != TMD_OK) return rc;
   rc = tmd_cuda_check(h, cudaMemsetAsync(cstatus, 0, 4, st), "cudaMemsetAsync");
   if (rc != TMD_OK) return rc;
-  rc = tmd_rans_decode(h, coded, coded_bytes, &a, cstatus, stream);
+  // The streams the track decoder and the ranking read (headers, differences,
+  // residuals, the per-bin unattached counts) are entropy-decoded first on
+  // `stream`; the charges of the attached clusters and the unattached streams,
+  // needed only by the record scatter and the unattached decode, on the
+  // handle's second stream while the track decoder runs.
+  const uint32_t first = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 3) | (1u << 4) | (1u << 5) |
+                         (1u << 11) | (1u << 12) | (1u << 13) | (1u << 14) | (1u << 15);
+  const uint32_t later = ((1u << kFields) - 1u) & ~first;
+  const bool two = h->tune_coded_overlap && h->aux && h->fork && h->coded_late;
+  if (two) {
+    rc = tmd_cuda_check(h, cudaEventRecord(h->fork, st), "cudaEventRecord");
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->aux, h->fork, 0), "cudaStreamWaitEvent");
+    if (rc != TMD_OK) return rc;
+  }
+  const uint8_t* c = static_cast<const uint8_t*>(coded);
+  cudaStream_t late_st = two ? h->aux : st;
+  rc = tmd_cuda_check(h, launch_width<4>(c, coded_bytes, a, cstatus, st, first), "k_rans_decode<4>");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, launch_width<2>(c, coded_bytes, a, cstatus, st, first), "k_rans_decode<2>");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, launch_width<1>(c, coded_bytes, a, cstatus, st, first), "k_rans_decode<1>");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, launch_width<4>(c, coded_bytes, a, cstatus, late_st, later), "k_rans_decode<4>");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, launch_width<2>(c, coded_bytes, a, cstatus, late_st, later), "k_rans_decode<2>");
+  if (rc == TMD_OK)
+    rc = tmd_cuda_check(h, launch_width<1>(c, coded_bytes, a, cstatus, late_st, later), "k_rans_decode<1>");
+  if (rc == TMD_OK && two)
+    rc = tmd_cuda_check(h, cudaEventRecord(h->coded_late, h->aux), "cudaEventRecord");
   if (rc != TMD_OK) return rc;
   tmd_frame_in in;
   in.n_tracks = n_tracks;
@@ -621,7 +658,11 @@ extern "C" int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t
   in.n_unatt = a.n_unatt; in.pad_diff_u = a.pad_diff_u; in.time_diff_u = a.time_diff_u;
   in.qtot_u = a.qtot_u; in.qmax_u = a.qmax_u; in.flags_u = a.flags_u;
   in.sigma_pad_u = a.sigma_pad_u; in.sigma_time_u = a.sigma_time_u;
+  // the decode chain waits for the later streams before its record scatter
+  // and unattached decode
+  h->late_inputs = two ? h->coded_late : nullptr;
   rc = tmd_decode_frame(h, &in, out, stream);
+  h->late_inputs = nullptr;
   if (rc != TMD_OK) return rc;
   k_status_or<<<1, 1, 0, st>>>(out->status, cstatus);
   rc = tmd_cuda_check(h, cudaGetLastError(), "k_status_or launch");

@@ -44,7 +44,7 @@ FRAME_FIELDS = [
 TRUTH_FIELDS = ["qpt", "ncl", "row", "sector", "leg", "pad", "time"]
 # tuning parameters of tmd_tune_set / tmd_tune_get (include/tmd.h)
 TUNE_KEYS = ("decode_variant", "scatter_variant", "overlap", "unatt_variant",
-             "decode_blocks_per_sm", "unatt_blocks_per_sm", "rans_overlap")
+             "decode_blocks_per_sm", "unatt_blocks_per_sm", "rans_overlap", "coded_overlap")
 
 
 def tune_keys() -> tuple:

@@ -84,14 +84,22 @@ def test_stream_lengths_around_chunk_boundaries(dec, counts):
     _same_streams(got, fr, f"counts {counts}")
 
 
-def test_coded_frame_decodes_to_the_oracle_native_list(dec):
+@pytest.mark.parametrize("coded_overlap", [0, 1])
+def test_coded_frame_decodes_to_the_oracle_native_list(dec, coded_overlap):
+    """Entropy decoding then track-model decoding equals the oracle's decode,
+    with the later streams (charges, unattached) entropy-decoded beside the
+    track decoder or before it."""
     from paper_2411_02206_gb300 import tmd
     truth = synth.make_truth(n_tracks=1500, n_unatt=60_000, seed=23, looper_frac=0.2)
     fr = G.oracle_frame(truth)
     blob = tmd.rans_encode(fr)
-    native, rs, att, st = dec.decode_coded(_upload(blob), *O.frame_counts(fr))
-    import torch
-    torch.cuda.synchronize()
+    dec.tmd_tune_set("coded_overlap", coded_overlap)
+    try:
+        native, rs, att, st = dec.decode_coded(_upload(blob), *O.frame_counts(fr))
+        import torch
+        torch.cuda.synchronize()
+    finally:
+        dec.tmd_tune_set("coded_overlap", 1)
     got = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32), frames.to_numpy(att, np.uint32),
            int(st.item()))
     G.assert_same_decode(got, O.decode(fr), "coded frame")
@@ -137,10 +145,17 @@ def test_malformed_coded_frames_set_the_status(dec):
         assert not O.rans_decode(b, *c)[1], name
         _, status = dec.rans_decode(_upload(b), *c)
         assert int(status.item()) & tmd.STATUS_CODED, name
-    # the chained decode reports it beside the decoder's own bits
-    b = _corruptions(blob, counts)[0][1]
-    *_, st = dec.decode_coded(_upload(b), *counts)
-    assert int(st.item()) & tmd.STATUS_CODED
+    # the chained decode reports it beside the decoder's own bits, for a
+    # stream the track decoder reads (time_res) and for one entropy-decoded
+    # beside it (qtot_u)
+    ent = {name: i for i, (name, _, _) in enumerate(O.FRAME_FIELDS)}
+    k = ent["qtot_u"]
+    off_u = int(np.frombuffer(blob[32 + 32 * k: 40 + 32 * k].tobytes(), "<u8")[0])
+    late = blob.copy()
+    late[off_u + 512 * 2 + 4 * 3] ^= 0x80  # a lane's start state of qtot_u
+    for bad in (_corruptions(blob, counts)[0][1], late):
+        *_, st = dec.decode_coded(_upload(bad), *counts)
+        assert int(st.item()) & tmd.STATUS_CODED
     with pytest.raises(tmd.TmdError):
         dec.rans_decode(_upload(blob[:700]), *counts)
 
