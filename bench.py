@@ -568,7 +568,7 @@ def run(args):
         torch.cuda.empty_cache()
     if bpool is not None:
         batch = batch_leg(dec, bpool.frames(dec, f"cuda:{local}"), args.steps, f"cuda:{local}",
-                          local)
+                          local, autotune=not args.no_autotune)
         torch.cuda.empty_cache()
     if spool is not None:
         serve = serve_leg(dec, spool.frames(dec, f"cuda:{local}"), args.requests, local, local)
@@ -671,7 +671,7 @@ def _alloc_out(tmd, torch, frame, device):
             torch.empty(1, dtype=torch.int32, device=device))
 
 
-def batch_leg(dec, frs, steps, device, clock_index):
+def batch_leg(dec, frs, steps, device, clock_index, autotune=True):
     """The multi-frame schedule (64 frames of log-uniform 0.5-40 M clusters,
     pp-like to Pb-Pb-like mixes, seeds 1000+i): 64 plain tmd_decode_frame
     calls vs one tmd_decode_batch call vs one graph launch of a planned batch,
@@ -685,6 +685,11 @@ def batch_leg(dec, frs, steps, device, clock_index):
     total = sum(sum(tmd.counts(f)[1:]) for f in frs)
     stream = torch.cuda.current_stream()
     reps = max(3, min(steps, 20))
+    # tuned on the batch's own frames (a sample of 8), not on the single frame
+    saved = {k: dec.tmd_tune_get(k) for k in tmd.tune_keys()}
+    if autotune:
+        dec.tmd_autotune(fins[:8], fouts[:8], stream)
+    tuned = {k: dec.tmd_tune_get(k) for k in tmd.tune_keys()}
 
     def timeit(fn):
         for _ in range(3):
@@ -711,6 +716,8 @@ def batch_leg(dec, frs, steps, device, clock_index):
     dec.tmd_batch_destroy(bh)
     ok = all(int(o[3].item()) == 0 for o in outs)
     del outs, ref
+    for k, v in saved.items():
+        dec.tmd_tune_set(k, v)
     return {"workload": f"batch of {len(frs)} frames, {total} clusters (log-uniform "
                         "0.5-40 M per frame, pp-like to Pb-Pb-like mixes, seeds 1000+i)",
             "frames": len(frs), "clusters": total, "reps": reps,
@@ -719,7 +726,7 @@ def batch_leg(dec, frs, steps, device, clock_index):
             "graph_launch": {"value": total / (t_graph * 1e-3), "ms": t_graph},
             "speedup_vs_plain": t_plain / min(t_batch, t_graph),
             "identical_to_plain": bool(same_b and same_g), "status_ok": ok,
-            "clocks": clk.summary()}
+            "tuning": tuned, "clocks": clk.summary()}
 
 
 def serve_leg(dec, frs, n_req, device, clock_index, load=0.8):

@@ -564,8 +564,11 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     timed(kKRowOffsets, [&] { k_row_offsets<<<nf, 1024, 0, st>>>(dframes, P); });
     auto unatt = [&](cudaStream_t s_) {
       if (!n_chunk) return;
+      // beside the scatter the tuned number of blocks per SM; alone, every
+      // block that fits (its chunks form a look-back chain, so more blocks
+      // in flight shorten it)
       int bps = h->occ_unatt;
-      if (h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;
+      if (s_ != st && h->tune_unatt_bps > 0 && h->tune_unatt_bps < bps) bps = h->tune_unatt_bps;
       const uint32_t grid = std::min<uint32_t>(n_chunk, (uint32_t)(h->sms * bps));
       timed_on(s_, kKUnattDecode, [&] {
         launch_unatt_decode(h->tune_unatt_variant, grid, s_, dframes, P, n_chunk);
