@@ -6,7 +6,10 @@ than its fixed capacity with a clear error.  Collected last on purpose."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2411_02206_gb300 import synth
+
+import gpu_helpers as G
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +49,11 @@ def test_noalloc_equals_decode_frame_on_two_calls():
         assert torch.equal(native, ref[0])
         assert torch.equal(rs, ref[1])
         assert torch.equal(att, ref[2])
+        # and directly against the oracle's decode of the same compressed frame
+        host = {name: frames.to_numpy(frame[name], dt) for name, dt, _ in O.FRAME_FIELDS}
+        G.assert_same_decode((native.cpu().numpy(), frames.to_numpy(rs, np.uint32),
+                              frames.to_numpy(att, np.uint32), int(st.item())),
+                             O.decode(host), f"allocation-free decode, seed {seed}")
     dec.close()
 
 
