@@ -867,7 +867,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune", action="append", metavar="KEY=VALUE",
-                    help="set a tuning parameter (after autotuning), e.g. decode_variant=2")
+                    help="set a tuning parameter (after autotuning), e.g. decode_variant=1")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling runs only; the bench line uses 1.0)")
     args = ap.parse_args()
