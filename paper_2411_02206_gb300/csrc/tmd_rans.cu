@@ -625,8 +625,10 @@ extern "C" int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t
   const uint32_t first = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 3) | (1u << 4) | (1u << 5) |
                          (1u << 11) | (1u << 12) | (1u << 13) | (1u << 14) | (1u << 15);
   const uint32_t later = ((1u << kFields) - 1u) & ~first;
+  // coded_overlap 1: the later streams start at once beside the first ones;
+  // 2: they start when the first ones are done (beside the track decoder only)
   const bool two = h->tune_coded_overlap && h->aux && h->fork && h->coded_late;
-  if (two) {
+  if (two && h->tune_coded_overlap == 1) {
     rc = tmd_cuda_check(h, cudaEventRecord(h->fork, st), "cudaEventRecord");
     if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->aux, h->fork, 0), "cudaStreamWaitEvent");
     if (rc != TMD_OK) return rc;
@@ -638,6 +640,10 @@ extern "C" int tmd_decode_coded_frame(tmd_handle* h, const void* coded, uint64_t
     rc = tmd_cuda_check(h, launch_width<2>(c, coded_bytes, a, cstatus, st, first), "k_rans_decode<2>");
   if (rc == TMD_OK)
     rc = tmd_cuda_check(h, launch_width<1>(c, coded_bytes, a, cstatus, st, first), "k_rans_decode<1>");
+  if (rc == TMD_OK && two && h->tune_coded_overlap == 2) {
+    rc = tmd_cuda_check(h, cudaEventRecord(h->fork, st), "cudaEventRecord");
+    if (rc == TMD_OK) rc = tmd_cuda_check(h, cudaStreamWaitEvent(h->aux, h->fork, 0), "cudaStreamWaitEvent");
+  }
   if (rc == TMD_OK)
     rc = tmd_cuda_check(h, launch_width<4>(c, coded_bytes, a, cstatus, late_st, later), "k_rans_decode<4>");
   if (rc == TMD_OK)

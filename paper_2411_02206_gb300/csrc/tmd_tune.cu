@@ -29,7 +29,7 @@ const Param kParams[] = {
     {"decode_blocks_per_sm", &tmd_handle::tune_decode_bps, 0, 64},
     {"unatt_blocks_per_sm", &tmd_handle::tune_unatt_bps, 0, 64},
     {"rans_overlap", &tmd_handle::tune_rans_overlap, 0, 1},
-    {"coded_overlap", &tmd_handle::tune_coded_overlap, 0, 1},
+    {"coded_overlap", &tmd_handle::tune_coded_overlap, 0, 2},
 };
 
 std::string device_key(const tmd_handle* h) {

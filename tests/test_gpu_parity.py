@@ -173,6 +173,45 @@ def test_batch_equals_single(dec):
                              O.decode(npf[i]), f"batch frame {i}")
 
 
+def test_many_tiles_and_a_batch_with_a_rejected_frame(dec):
+    """A frame of ~87 ranking tiles, and a batch whose frames differ in tile
+    count with one frame the decoder rejects (a track with no clusters): the
+    rejected frame's status equals the oracle's and the frames around it
+    decode to the oracle's lists."""
+    import torch
+    from paper_2411_02206_gb300 import frames, tmd
+    big = G.oracle_frame(synth.make_truth(n_tracks=24_000, n_unatt=50_000, seed=41,
+                                          min_clusters=60, max_clusters=160))
+    assert len(big["qtot_a"]) > 80 * 32768
+    G.assert_same_decode(G.gpu_decode_np(dec, big), O.decode(big), "87 tiles")
+    specs = synth.batch_specs(n_frames=6, seed=78, lo=2e4, hi=6e5)
+    npf = [G.oracle_frame(synth.make_truth(**s)) for s in specs]
+    bad = dict(npf[2])
+    bad["ncl"] = bad["ncl"].copy()
+    bad["ncl"][5] = 0
+    npf[2] = bad
+    devs = [frames.to_torch(f, "cuda:0") for f in npf]
+    outs, fins, fouts = [], [], []
+    for d in devs:
+        nt, na, nu = tmd.counts(d)
+        o = (torch.empty((na + nu, 12), dtype=torch.uint8, device="cuda:0"),
+             torch.empty(5473, dtype=torch.int32, device="cuda:0"),
+             torch.empty(5472, dtype=torch.int32, device="cuda:0"),
+             torch.empty(1, dtype=torch.int32, device="cuda:0"))
+        outs.append(o)
+        fins.append(tmd.frame_in(d))
+        fouts.append(tmd.frame_out(*o))
+    dec.tmd_decode_batch(fins, fouts)
+    torch.cuda.synchronize()
+    for i, o in enumerate(outs):
+        ora = O.decode(npf[i])
+        if i == 2:
+            assert ora[3] != 0
+        G.assert_same_decode((o[0].cpu().numpy(), frames.to_numpy(o[1], np.uint32),
+                              frames.to_numpy(o[2], np.uint32), int(o[3].item())),
+                             ora, f"batch frame {i}")
+
+
 def test_host_entry_point(dec):
     from paper_2411_02206_gb300 import frames, tmd
     truth = synth.make_truth(n_tracks=1500, n_unatt=40_000, seed=21)

@@ -84,22 +84,23 @@ def test_stream_lengths_around_chunk_boundaries(dec, counts):
     _same_streams(got, fr, f"counts {counts}")
 
 
-@pytest.mark.parametrize("coded_overlap", [0, 1])
+@pytest.mark.parametrize("coded_overlap", [0, 1, 2])
 def test_coded_frame_decodes_to_the_oracle_native_list(dec, coded_overlap):
     """Entropy decoding then track-model decoding equals the oracle's decode,
-    with the later streams (charges, unattached) entropy-decoded beside the
-    track decoder or before it."""
+    with the later streams (charges, unattached) entropy-decoded before the
+    track decoder, beside everything, or beside the track decoder."""
     from paper_2411_02206_gb300 import tmd
     truth = synth.make_truth(n_tracks=1500, n_unatt=60_000, seed=23, looper_frac=0.2)
     fr = G.oracle_frame(truth)
     blob = tmd.rans_encode(fr)
+    saved = dec.tmd_tune_get("coded_overlap")
     dec.tmd_tune_set("coded_overlap", coded_overlap)
     try:
         native, rs, att, st = dec.decode_coded(_upload(blob), *O.frame_counts(fr))
         import torch
         torch.cuda.synchronize()
     finally:
-        dec.tmd_tune_set("coded_overlap", 1)
+        dec.tmd_tune_set("coded_overlap", saved)
     got = (native.cpu().numpy(), frames.to_numpy(rs, np.uint32), frames.to_numpy(att, np.uint32),
            int(st.item()))
     G.assert_same_decode(got, O.decode(fr), "coded frame")
