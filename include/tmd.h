@@ -345,8 +345,11 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *   "unatt_variant"       0..1  record write-out of the unattached decoder:
  *                               word by word (0) or one staged 16-byte
  *                               {record, index} entry per thread (1)
- *   "overlap"             0..1  unattached decoder on a second stream beside
- *                               the tile bases and the record scatter (1)
+ *   "overlap"             0..2  unattached decoder after the record scatter
+ *                               (0), on a second stream beside the tile bases
+ *                               and the record scatter (1), or beside them only
+ *                               when the call's frames hold fewer than 3
+ *                               unattached clusters per 4 attached ones (2)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
  *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
  *   "rans_overlap"   0..1  4-byte streams entropy-decoded on a second stream (1)

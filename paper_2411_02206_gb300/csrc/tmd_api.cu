@@ -547,9 +547,24 @@ int tmd_enqueue(tmd_handle* h, uint32_t nf, const tmd_frame_in* in, const tmd_fr
     // track decode (keys, pad and time codes), per-tile counts and ranks, row
     // offsets; then the tile bases and the record scatter, with the
     // unattached decode (it needs only rowStart and the attached counts)
-    // beside them on the second stream (overlap 1) or after them
+    // beside them on the second stream (overlap 1) or after them (overlap 0).
+    // overlap 2 decides by the mix of the call's frames: beside the scatter
+    // the unattached decode runs at ~26 ps per cluster and slows the scatter
+    // (~14 ps per attached cluster) a little; alone it takes ~8 ps per
+    // cluster with every block that fits.  Beside pays while it ends within
+    // the scatter with margin, i.e. for fewer than 3 unattached clusters per
+    // 4 attached ones (the Pb-Pb frame has 2.1 per 4).
     const uint32_t n_kt = pre_kt[nf];
-    const bool two = cs && cs->aux && cs->fork && cs->join && h->tune_overlap && n_chunk;
+    bool beside = h->tune_overlap == 1;
+    if (h->tune_overlap == 2) {
+      uint64_t na = 0, nu = 0;
+      for (uint32_t f = 0; f < nf; f++) {
+        na += in[f].n_attached;
+        nu += in[f].n_unattached;
+      }
+      beside = 4 * nu < 3 * na;
+    }
+    const bool two = cs && cs->aux && cs->fork && cs->join && beside && n_chunk;
     if (n_kt) {
       const int var = h->tune_decode_variant;
       int bps = h->occ_decode_v[var];

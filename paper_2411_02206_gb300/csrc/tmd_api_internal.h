@@ -59,7 +59,8 @@ struct tmd_handle {
   int tune_decode_variant = 0;   // staging-round variant of the track decoder
   int tune_scatter_variant = 1;  // store pattern of the record scatter
   int tune_unatt_variant = 1;    // record write-out of the unattached decode
-  int tune_overlap = 1;          // unattached decode on the second stream beside the scatter
+  int tune_overlap = 2;          // unattached decode on the second stream beside the scatter
+                                 // (1), after it (0), or by the frames' mix (2)
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 1;        // unattached-decode blocks per SM (0: as many as fit)
   int tune_rans_overlap = 1;

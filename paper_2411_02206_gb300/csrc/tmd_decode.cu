@@ -204,6 +204,12 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
         cp_wait<0>();
       }
       const uint32_t rem = n > k0 ? n - k0 : 0u;
+      // the round's differences as byte and halfword loads from the lane's
+      // buffer (step q at element base + q of each stream; the base is -1 in
+      // round 0, whose step 0 reads none)
+      const uint8_t* rd_b = reinterpret_cast<const uint8_t*>(lb);
+      const uint8_t* sl_b = reinterpret_cast<const uint8_t*>(lb + Lay::kRd);
+      const uint16_t* pr_b = reinterpret_cast<const uint16_t*>(lb + 2 * Lay::kRd);
 #pragma unroll 1
       for (uint32_t q = 0; q < (uint32_t)R; q++) {
         if (q < rem) {
@@ -212,10 +218,8 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
             padq = pad0;
             timeq = time0;
           } else {
-            const int prd = cur.rd + (int)q, psl = cur.sl + (int)q, ppr = cur.pr + (int)q;
-            const uint32_t rdv = (lb[prd >> 2] >> (8 * (prd & 3))) & 255u;
-            const uint32_t slv = (lb[Lay::kRd + (psl >> 2)] >> (8 * (psl & 3))) & 255u;
-            const uint32_t prv = (lb[2 * Lay::kRd + (ppr >> 1)] >> (16 * (ppr & 1))) & 0xFFFFu;
+            const uint32_t rdv = rd_b[cur.rd + (int)q], slv = sl_b[cur.sl + (int)q],
+                           prv = pr_b[cur.pr + (int)q];
             st |= key_step(s, rdv, slv);
             uint32_t ppad, ptime;
             const float4 G = geo->row[s.row];

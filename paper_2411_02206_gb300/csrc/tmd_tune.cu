@@ -24,7 +24,7 @@ struct Param {
 const Param kParams[] = {
     {"decode_variant", &tmd_handle::tune_decode_variant, 0, 1},
     {"scatter_variant", &tmd_handle::tune_scatter_variant, 0, 1},
-    {"overlap", &tmd_handle::tune_overlap, 0, 1},
+    {"overlap", &tmd_handle::tune_overlap, 0, 2},
     {"unatt_variant", &tmd_handle::tune_unatt_variant, 0, 1},
     {"decode_blocks_per_sm", &tmd_handle::tune_decode_bps, 0, 64},
     {"unatt_blocks_per_sm", &tmd_handle::tune_unatt_bps, 0, 64},
@@ -122,7 +122,7 @@ extern "C" int tmd_autotune(tmd_handle* h, uint32_t n, const tmd_frame_in* in,
   const Axis axes[] = {
       {&tmd_handle::tune_decode_variant, {0, 1}},
       {&tmd_handle::tune_scatter_variant, {0, 1}},
-      {&tmd_handle::tune_overlap, {0, 1}},
+      {&tmd_handle::tune_overlap, {0, 1, 2}},
       {&tmd_handle::tune_unatt_variant, {0, 1}},
       {&tmd_handle::tune_unatt_bps, {0, 1, 2, 3, 4}},
   };

@@ -253,7 +253,7 @@ def test_every_tuning_setting_gives_the_oracle_result(dec):
         G.assert_same_decode(gpu, ora, what)
 
     try:
-        for ov in range(2):
+        for ov in range(3):
             dec.tmd_tune_set("overlap", ov)
             for dv in range(2):
                 dec.tmd_tune_set("decode_variant", dv)
