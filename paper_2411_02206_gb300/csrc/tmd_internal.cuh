@@ -178,7 +178,7 @@ __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDe
 __global__ void k_track_trace(const FrameDev* frames, const uint32_t* ids, uint32_t n_ids,
                               float* state);
 
-constexpr int kRankBitmapWords = (kNBin + 31) / 32;
-constexpr int kCountRankSmem = kTileWarps * kNBin * 2 + kTileWarps * kRankBitmapWords * 4;
+constexpr int kRankTags = 1024;  // per-warp duplicate-test slots of the ranking (bytes)
+constexpr int kCountRankSmem = kTileWarps * kNBin * 2 + kTileWarps * kRankTags;
 
 }  // namespace tmd

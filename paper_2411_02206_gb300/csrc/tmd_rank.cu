@@ -12,12 +12,18 @@
 //                 offsets and writes the tile histogram; pass 2 reads the keys
 //                 in stream order (32 consecutive clusters per step) and gives
 //                 every cluster its rank among the tile's clusters of the same
-//                 bin.  A step whose keys are all distinct (tested with a
-//                 per-warp bitmap: atom.or returns the bit's old value) ranks
-//                 with one shared-memory read and write per lane;
-//                 consecutive clusters mostly belong to one track and lie in
-//                 distinct rows, so most steps take this path.  A step with a
-//                 repeated key orders equal keys by lane with match.any.
+//                 bin.  A step whose keys are all distinct ranks with one
+//                 shared-memory read and write per lane; consecutive clusters
+//                 mostly belong to one track and lie in distinct rows, so most
+//                 steps take this path.  The test: every lane writes its lane
+//                 number to slot key mod kRankTags of a per-warp byte array
+//                 and reads it back; a lane that finds another number shares
+//                 its slot with a lane of the step (an equal key, or rarely
+//                 keys kRankTags apart).  Consecutive keys fill consecutive
+//                 bytes, so the test costs one conflict-free store and load
+//                 (a bitmap with atom.or serialised the up to 32 lanes whose
+//                 consecutive rows share a bitmap word).  A step with a shared
+//                 slot orders equal keys by lane with match.any.
 //
 // The native index of cluster j is then tileBase[tile][key] + rank[j].
 #include "tmd_internal.cuh"
@@ -25,7 +31,7 @@
 namespace tmd {
 
 __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, PlanDev plan) {
-  // [kTileWarps][kNBin/2] packed u16 counts, then [kTileWarps][kRankBitmapWords]
+  // [kTileWarps][kNBin/2] packed u16 counts, then [kTileWarps][kRankTags] byte slots
   extern __shared__ uint32_t s_mem[];
   const uint32_t f = find_frame(plan.pre_tile, plan.n_frames, blockIdx.x);
   const FrameDev& F = frames[f];
@@ -38,9 +44,8 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
   const uint32_t n_att = F.n_att;
   uint32_t* hist32 = s_mem + wid * (kNBin / 2);
   uint16_t* hist = reinterpret_cast<uint16_t*>(hist32);
-  uint32_t* bm = s_mem + kTileWarps * (kNBin / 2) + wid * kRankBitmapWords;
+  uint8_t* tag = reinterpret_cast<uint8_t*>(s_mem + kTileWarps * (kNBin / 2)) + wid * kRankTags;
   for (int i = lane; i < kNBin / 2; i += 32) hist32[i] = 0u;
-  for (int i = lane; i < kRankBitmapWords; i += 32) bm[i] = 0u;
   __syncwarp();
   const uint32_t j_begin = tile * (uint32_t)kTile + wid * (uint32_t)kTileSub;
   const uint32_t j_end = min(j_begin + (uint32_t)kTileSub, n_att);
@@ -106,11 +111,13 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
       const uint32_t j = b0 + 32u * u + lane;
       const bool in = j < j_end;
       const uint32_t k = kk[u];
-      // a lane whose bit was already set shares its key with an earlier
-      // lane of the step; without such a lane every key is new to the step
-      uint32_t dup = 0;
-      if (in) dup = atomicOr(&bm[k >> 5], 1u << (k & 31)) & (1u << (k & 31));
-      if (!__any_sync(0xffffffffu, dup != 0)) {
+      // a lane that reads back another lane's number shares its slot with
+      // a lane of the step; without such a lane every key is new to the step
+      const uint32_t slot = k & (kRankTags - 1);
+      if (in) tag[slot] = (uint8_t)lane;
+      __syncwarp();
+      const bool clash = in && tag[slot] != lane;
+      if (!__any_sync(0xffffffffu, clash)) {
         if (in) {
           const uint32_t base = hist[k];
           hist[k] = (uint16_t)(base + 1);
@@ -127,8 +134,6 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
           rank[j] = (uint16_t)r;
         }
       }
-      __syncwarp();
-      if (in) bm[k >> 5] = 0u;  // every bit of the word was set in this step
       __syncwarp();
     }
   }
