@@ -178,7 +178,8 @@ __global__ void k_track_encode(const EncDev* enc, const FrameDev* frames, PlanDe
 __global__ void k_track_trace(const FrameDev* frames, const uint32_t* ids, uint32_t n_ids,
                               float* state);
 
-constexpr int kRankTags = 1024;  // per-warp duplicate-test slots of the ranking (bytes)
+constexpr int kRankTags = 2048;  // per-warp duplicate-test slots of the ranking (bytes)
+constexpr int kRankGroup = 2;    // ranking steps tested for distinct keys at once
 constexpr int kCountRankSmem = kTileWarps * kNBin * 2 + kTileWarps * kRankTags;
 
 }  // namespace tmd

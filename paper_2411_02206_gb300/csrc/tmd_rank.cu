@@ -12,18 +12,21 @@
 //                 offsets and writes the tile histogram; pass 2 reads the keys
 //                 in stream order (32 consecutive clusters per step) and gives
 //                 every cluster its rank among the tile's clusters of the same
-//                 bin.  A step whose keys are all distinct ranks with one
-//                 shared-memory read and write per lane; consecutive clusters
+//                 bin.  A group of kRankGroup steps whose keys are all
+//                 distinct ranks with one shared-memory read and write per
+//                 key, the group's reads issued together; consecutive clusters
 //                 mostly belong to one track and lie in distinct rows, so most
-//                 steps take this path.  The test: every lane writes its lane
-//                 number to slot key mod kRankTags of a per-warp byte array
-//                 and reads it back; a lane that finds another number shares
-//                 its slot with a lane of the step (an equal key, or rarely
-//                 keys kRankTags apart).  Consecutive keys fill consecutive
-//                 bytes, so the test costs one conflict-free store and load
-//                 (a bitmap with atom.or serialised the up to 32 lanes whose
-//                 consecutive rows share a bitmap word).  A step with a shared
-//                 slot orders equal keys by lane with match.any.
+//                 groups take this path.  The test: every key writes its
+//                 number in the group (lane + 32 * step) to slot key mod
+//                 kRankTags of a per-warp byte array and reads it back; a key
+//                 that finds another number shares its slot with a key of the
+//                 group (an equal key, or rarely keys kRankTags apart).
+//                 Consecutive keys fill consecutive bytes, so the test costs
+//                 conflict-free stores and loads (a bitmap with atom.or
+//                 serialised the up to 32 lanes whose consecutive rows share
+//                 a bitmap word).  A group that fails the test is ranked step
+//                 by step with the same test per step, and a step with a
+//                 shared slot orders equal keys by lane with match.any.
 //
 // The native index of cluster j is then tileBase[tile][key] + rank[j].
 #include "tmd_internal.cuh"
@@ -106,35 +109,74 @@ __global__ void __launch_bounds__(256, 2) k_count_rank(const FrameDev* frames, P
       const uint32_t j = b0 + 256u + 32u * u + lane;
       nk[u] = j < j_end ? (uint32_t)keys[j] : 0xFFFFFFFFu;
     }
+    // groups of kRankGroup steps: when the group's keys are all distinct
+    // (one slot test for all of them) its shared-counter updates are
+    // independent and issue together; otherwise step by step
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint32_t j = b0 + 32u * u + lane;
-      const bool in = j < j_end;
-      const uint32_t k = kk[u];
-      // a lane that reads back another lane's number shares its slot with
-      // a lane of the step; without such a lane every key is new to the step
-      const uint32_t slot = k & (kRankTags - 1);
-      if (in) tag[slot] = (uint8_t)lane;
-      __syncwarp();
-      const bool clash = in && tag[slot] != lane;
-      if (!__any_sync(0xffffffffu, clash)) {
-        if (in) {
-          const uint32_t base = hist[k];
-          hist[k] = (uint16_t)(base + 1);
-          rank[j] = (uint16_t)base;
-        }
-      } else {
-        const uint32_t act = __ballot_sync(0xffffffffu, in);
-        if (in) {
-          const uint32_t peers = __match_any_sync(act, k);
-          const uint32_t base = hist[k];
-          const uint32_t r = base + __popc(peers & lanemask_lt());
-          __syncwarp(act);
-          if (lane == __ffs(peers) - 1) hist[k] = (uint16_t)(base + __popc(peers));
-          rank[j] = (uint16_t)r;
-        }
+    for (int g0 = 0; g0 < 8; g0 += kRankGroup) {
+      bool clash = false;
+#pragma unroll
+      for (int g = 0; g < kRankGroup; g++) {
+        const uint32_t j = b0 + 32u * (g0 + g) + lane;
+        if (j < j_end) tag[kk[g0 + g] & (kRankTags - 1)] = (uint8_t)(lane + 32 * g);
       }
       __syncwarp();
+#pragma unroll
+      for (int g = 0; g < kRankGroup; g++) {
+        const uint32_t j = b0 + 32u * (g0 + g) + lane;
+        if (j < j_end && tag[kk[g0 + g] & (kRankTags - 1)] != (uint8_t)(lane + 32 * g))
+          clash = true;
+      }
+      if (!__any_sync(0xffffffffu, clash)) {
+        uint32_t base[kRankGroup];
+#pragma unroll
+        for (int g = 0; g < kRankGroup; g++) {
+          const uint32_t j = b0 + 32u * (g0 + g) + lane;
+          base[g] = j < j_end ? hist[kk[g0 + g]] : 0u;
+        }
+#pragma unroll
+        for (int g = 0; g < kRankGroup; g++) {
+          const uint32_t j = b0 + 32u * (g0 + g) + lane;
+          if (j < j_end) {
+            hist[kk[g0 + g]] = (uint16_t)(base[g] + 1);
+            rank[j] = (uint16_t)base[g];
+          }
+        }
+        __syncwarp();
+        continue;
+      }
+#pragma unroll
+      for (int g = 0; g < kRankGroup; g++) {
+        const int u = g0 + g;
+        const uint32_t j = b0 + 32u * u + lane;
+        const bool in = j < j_end;
+        const uint32_t k = kk[u];
+        // a lane that reads back another lane's number shares its slot with
+        // a lane of the step; without such a lane every key is new to the step
+        const uint32_t slot = k & (kRankTags - 1);
+        __syncwarp();
+        if (in) tag[slot] = (uint8_t)lane;
+        __syncwarp();
+        const bool dup = in && tag[slot] != lane;
+        if (!__any_sync(0xffffffffu, dup)) {
+          if (in) {
+            const uint32_t base = hist[k];
+            hist[k] = (uint16_t)(base + 1);
+            rank[j] = (uint16_t)base;
+          }
+        } else {
+          const uint32_t act = __ballot_sync(0xffffffffu, in);
+          if (in) {
+            const uint32_t peers = __match_any_sync(act, k);
+            const uint32_t base = hist[k];
+            const uint32_t r = base + __popc(peers & lanemask_lt());
+            __syncwarp(act);
+            if (lane == __ffs(peers) - 1) hist[k] = (uint16_t)(base + __popc(peers));
+            rank[j] = (uint16_t)r;
+          }
+        }
+        __syncwarp();
+      }
     }
   }
 }
