@@ -83,6 +83,46 @@ def test_tile_boundaries(dec):
         _check_truth(dec, sub, f"tile boundary {target}")
 
 
+def _single_row_tracks(rng, keys_per_track, n_unatt=0):
+    """Truth of tracks whose clusters sit at the given (sector, row) lists
+    (one list per track, consecutive rows), with random pads, times, charges
+    and curvature; unattached part empty or small."""
+    sec = np.concatenate([np.array([k // 152 for k in ks], np.uint8) for ks in keys_per_track])
+    row = np.concatenate([np.array([k % 152 for k in ks], np.uint8) for ks in keys_per_track])
+    n = len(row)
+    t = {"ncl": np.array([len(ks) for ks in keys_per_track], np.uint16),
+         "qpt": rng.integers(0, 256, len(keys_per_track)).astype(np.uint8),
+         "row": row, "sector": sec, "leg": np.zeros(n, np.uint8),
+         "pad": rng.integers(0, 4000, n).astype(np.uint16),
+         "time": rng.integers(0, 128000, n).astype(np.uint32),
+         "qtot_a": rng.integers(0, 1024, n).astype(np.uint16),
+         "qmax_a": rng.integers(0, 256, n).astype(np.uint16),
+         "flags_a": rng.integers(0, 4, n).astype(np.uint8),
+         "sigma_pad_a": rng.integers(0, 256, n).astype(np.uint8),
+         "sigma_time_a": rng.integers(0, 256, n).astype(np.uint8)}
+    t.update(synth.make_unattached(rng, n_unatt))
+    return t
+
+
+def test_ranking_repeated_and_aliased_keys(dec):
+    """Inputs that drive the ranking's duplicate tests: steps of 32 clusters
+    full of equal keys (short tracks crossing the same rows of one sector),
+    distinct keys 2048 apart that share a slot (rows 8 of sector 2 and 80 of
+    sector 15), and a lane whose keys in two consecutive steps are equal
+    (keys repeating with period 32), each over two ranking tiles."""
+    rng = np.random.default_rng(17)
+    cases = {
+        "repeated keys": [[5 * 152 + 10 + r for r in range(int(rng.integers(1, 4)))]
+                          for _ in range(20000)],
+        "aliased slots": [[2 * 152 + 8] if i % 3 else [15 * 152 + 80] for i in range(40000)],
+        "period 32": [[7 * 152 + (i % 32) * 4] for i in range(40000)],
+    }
+    for what, kpt in cases.items():
+        truth = _single_row_tracks(rng, kpt, n_unatt=3000)
+        assert len(truth["row"]) > 32768
+        _check_truth(dec, truth, what)
+
+
 def test_hot_bin_spans_many_chunks(dec):
     rng = np.random.default_rng(3)
     truth = synth.make_truth(n_tracks=100, n_unatt=0, seed=9)
