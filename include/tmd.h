@@ -351,13 +351,18 @@ int tmd_release(tmd_handle* h, uint64_t req_id);
  *                               when the call's frames hold fewer than 3
  *                               unattached clusters per 4 attached ones (2)
  *   "decode_blocks_per_sm" 0..64 persistent track-decoder blocks per SM (0: all that fit)
- *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM (0: all that fit)
+ *   "unatt_blocks_per_sm"  0..64 persistent unattached-decoder blocks per SM while it
+ *                               runs beside the scatter (0: all that fit; after
+ *                               the scatter it always takes all that fit)
  *   "rans_overlap"   0..1  4-byte streams entropy-decoded on a second stream (1)
  *   "coded_overlap"  0..2  tmd_decode_coded_frame: the attached charges and the
  *                          unattached streams entropy-decoded on `stream` after
  *                          the others (0), on a second stream from the start (1),
  *                          or on a second stream once the streams the track
  *                          decoder reads are done, beside the track decoder (2)
+ * Defaults of a new handle: decode_variant 0, scatter_variant 1, unatt_variant 1,
+ * overlap 2, decode_blocks_per_sm 0, unatt_blocks_per_sm 1, rans_overlap 1,
+ * coded_overlap 2 (unless its autotune cache holds other values).
  * tmd_autotune times the decode chain on the given frames (device buffers,
  * decoded several times) for each candidate setting, keeps the fastest, and
  * writes it to the handle's autotune cache if tmd_config.autotune_cache was
