@@ -109,13 +109,16 @@ def test_ranking_repeated_and_aliased_keys(dec):
     full of equal keys (short tracks crossing the same rows of one sector),
     distinct keys 2048 apart that share a slot (rows 8 of sector 2 and 80 of
     sector 15), and a lane whose keys in two consecutive steps are equal
-    (keys repeating with period 32), each over two ranking tiles."""
+    (keys repeating with period 32), each over two ranking tiles, and every
+    cluster of three tiles in one bin."""
     rng = np.random.default_rng(17)
     cases = {
         "repeated keys": [[5 * 152 + 10 + r for r in range(int(rng.integers(1, 4)))]
                           for _ in range(20000)],
         "aliased slots": [[2 * 152 + 8] if i % 3 else [15 * 152 + 80] for i in range(40000)],
         "period 32": [[7 * 152 + (i % 32) * 4] for i in range(40000)],
+        # every cluster in one bin: a whole tile (32768 places) of one key
+        "one bin": [[11 * 152 + 40] for _ in range(70000)],
     }
     for what, kpt in cases.items():
         truth = _single_row_tracks(rng, kpt, n_unatt=3000)
