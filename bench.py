@@ -868,8 +868,10 @@ def run_batch(args):
     build.build()
     pool = FramePool(batch_specs_c2(args.frames))
     dec = tmd.Decoder(0)
+    _apply_tune(dec, args.tune)
     frs = pool.frames(dec, "cuda:0")
-    print(json.dumps(batch_leg(dec, frs, args.steps, "cuda:0", 0)), flush=True)
+    print(json.dumps(batch_leg(dec, frs, args.steps, "cuda:0", 0,
+                               autotune=not args.no_autotune)), flush=True)
     dec.close()
     return 0
 
