@@ -63,11 +63,11 @@ struct tmd_handle {
                                  // (1), after it (0), or by the frames' mix (2)
   int tune_decode_bps = 0;       // decode blocks per SM (0: as many as fit)
   int tune_unatt_bps = 1;        // unattached-decode blocks per SM (0: as many as fit)
-  int tune_rans_overlap = 1;
+  int tune_rans_overlap = 1;      // 4-byte streams entropy-decoded on the second stream
   int tune_coded_overlap = 2;    // coded frames: charges and unattached streams entropy-
                                  // decoded on the second stream beside the track decoder
   cudaEvent_t coded_late = nullptr;   // recorded after those streams are decoded
-  cudaEvent_t late_inputs = nullptr;  // set for the chain of a coded frame     // 4-byte streams entropy-decoded on the second stream
+  cudaEvent_t late_inputs = nullptr;  // set for the chain of a coded frame
   uint64_t mem_budget = 0;
   uint32_t max_slots = 0;
   std::string autotune_cache;
