@@ -210,28 +210,39 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
       const uint8_t* rd_b = reinterpret_cast<const uint8_t*>(lb);
       const uint8_t* sl_b = reinterpret_cast<const uint8_t*>(lb + Lay::kRd);
       const uint16_t* pr_b = reinterpret_cast<const uint16_t*>(lb + 2 * Lay::kRd);
-#pragma unroll 1
-      for (uint32_t q = 0; q < (uint32_t)R; q++) {
-        if (q < rem) {
-          uint32_t padq, timeq;
-          if (k0 + q == 0) {
-            padq = pad0;
-            timeq = time0;
-          } else {
-            const uint32_t rdv = rd_b[cur.rd + (int)q], slv = sl_b[cur.sl + (int)q],
-                           prv = pr_b[cur.pr + (int)q];
-            st |= key_step(s, rdv, slv);
-            uint32_t ppad, ptime;
-            const float4 G = geo->row[s.row];
-            propagate_predict(G, s, ppad, ptime);
-            padq = (ppad + prv) & 0xFFFFu;
-            timeq = ptime + lb[Lay::kTr0 + q];
-            update(G, s, padq, timeq);
-          }
-          if (timeq > 0xFFFFFFu) st |= kStTime;
-          S.kp[lane * P + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
-          lb[Lay::kTr0 + q] = timeq;
+      // one model step: cluster k0 + q >= 1 of the lane's track
+      auto step = [&](uint32_t q) {
+        const uint32_t rdv = rd_b[cur.rd + (int)q], slv = sl_b[cur.sl + (int)q],
+                       prv = pr_b[cur.pr + (int)q];
+        st |= key_step(s, rdv, slv);
+        uint32_t ppad, ptime;
+        const float4 G = geo->row[s.row];
+        propagate_predict(G, s, ppad, ptime);
+        const uint32_t padq = (ppad + prv) & 0xFFFFu;
+        const uint32_t timeq = ptime + lb[Lay::kTr0 + q];
+        update(G, s, padq, timeq);
+        if (timeq > 0xFFFFFFu) st |= kStTime;
+        S.kp[lane * P + q] = (uint32_t)(s.sec * kNRow + s.row) | (padq << 16);
+        lb[Lay::kTr0 + q] = timeq;
+      };
+      uint32_t q0 = 0;
+      if (k0 == 0) {  // the track's first cluster, stored absolute
+        if (rem > 0) {
+          if (time0 > 0xFFFFFFu) st |= kStTime;
+          S.kp[lane * P] = (uint32_t)(s.sec * kNRow + s.row) | (pad0 << 16);
+          lb[Lay::kTr0] = time0;
         }
+        q0 = 1;
+      }
+      // rounds in which every lane has all R steps left run without the
+      // per-step bound test (the common case for the long tracks decoded first)
+      if (__all_sync(kFull, rem >= (uint32_t)R)) {
+#pragma unroll 1
+        for (uint32_t q = q0; q < (uint32_t)R; q++) step(q);
+      } else {
+#pragma unroll 1
+        for (uint32_t q = q0; q < (uint32_t)R; q++)
+          if (q < rem) step(q);
       }
       __syncwarp();
       const uint32_t k = k0 + sq;
