@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
       }
       // rounds in which every lane has all R steps left run without the
       // per-step bound test (the common case for the long tracks decoded first)
-      if (__all_sync(kFull, rem >= (uint32_t)R)) {
+      const bool full = __all_sync(kFull, rem >= (uint32_t)R);
+      if (full) {
 #pragma unroll 1
         for (uint32_t q = q0; q < (uint32_t)R; q++) step(q);
       } else {
@@ -250,7 +251,9 @@ __global__ void __launch_bounds__(kDecodeThreads, MINB)
 #pragma unroll
       for (int i0 = 0; i0 < 32; i0 += G) {
         const uint32_t i = i0 + sg;
-        const uint32_t ni = __shfl_sync(kFull, n, i), ji = __shfl_sync(kFull, j0, i);
+        const uint32_t ji = __shfl_sync(kFull, j0, i);
+        // in a full round every track has step k; otherwise test its length
+        const uint32_t ni = full ? 0xFFFFFFFFu : __shfl_sync(kFull, n, i);
         if (k < ni) {
           const uint32_t a = S.kp[i * P + sq];
           key_o[ji + k] = (uint16_t)(a & 0xFFFFu);
